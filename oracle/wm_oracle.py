@@ -1,0 +1,261 @@
+"""FP64 CPU oracle of the WeatherMesh-3 processor and its latent rollout.
+
+TEST INFRASTRUCTURE ONLY. This module is the slow, plain reference that the GPU
+library is checked against. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it; the library never calls it and
+has no CPU fallback.
+
+Everything is float64 numpy. Matrix products use ``@`` (a BLAS call serving as
+one step of a definition); everything else is written as the definition reads.
+The oracle shares no code with the CUDA path.
+
+What the paper fixes, and the readings taken where it is silent:
+
+* Section 2.1, "Encoder-processor-decoder architecture" and "latent rollout":
+  the processor acts on the latent any number of times; one call advances 6 h
+  (six-hour processor) or 1 h (one-hour processor); a lead time T is reached
+  by a simple greedy schedule. Reading: greedy coin change, largest coin
+  first -- floor(T/6) six-hour calls, then T mod 6 one-hour calls. T = 0 is
+  the identity; T < 0 is an error.
+* Section 2.1, "NATTEN" and Appendix A.2: each processor is a stack of
+  neighborhood-attention transformer blocks over the (level, latitude,
+  longitude) token grid. Reading of the block (the paper only says "NATTEN
+  blocks"): pre-LayerNorm -> 3D neighborhood multi-head self-attention ->
+  output projection -> residual add; pre-LayerNorm -> MLP (ratio 4, GELU) ->
+  residual add. No final norm.
+* Appendix A.2: "circular padding" in longitude -> periodic (mod W) windows;
+  "bump" behaviour at the poles -> clamped windows that shift inward and keep
+  their full size (also used along the level axis).
+* Silent, read as PyTorch defaults: LayerNorm with biased variance, eps 1e-5,
+  affine; exact erf GELU; softmax scale 1/sqrt(d_head); all linear layers
+  carry a bias; no relative-position bias; dilation 1.
+* Appendix A.2 also names rotary position embeddings; the processor built
+  here does not use them (no axis split or frequencies are given).
+
+Parity status: every function below is pinned by ``tests/test_oracle_pins.py``
+(closed forms, library special cases, invariants, brute force on tiny grids,
+and the step counts printed in Section 2.2). Physical forecast skill is not
+reproducible without the paper's trained weights and data; that part is out
+of reach and is not claimed.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import erf
+
+
+# ---------------------------------------------------------------- schedule --
+
+def greedy_schedule(lead_hours: int) -> tuple[int, int]:
+    """(six-hour calls, one-hour calls) for an integer lead time (Section 2.1).
+
+    Greedy coin change with coins {6, 1}: as many six-hour steps as fit, the
+    remainder in one-hour steps, applied six-hour steps first.
+    """
+    if int(lead_hours) != lead_hours or lead_hours < 0:
+        raise ValueError("lead time must be a non-negative integer number of hours")
+    n6 = 0
+    rest = int(lead_hours)
+    while rest >= 6:
+        rest -= 6
+        n6 += 1
+    return n6, rest
+
+
+# ------------------------------------------------------------- primitives --
+
+def layer_norm(x, gamma, beta, eps=1e-5):
+    """LayerNorm over the last axis: (x - mean) / sqrt(biased var + eps) * gamma + beta."""
+    x = np.asarray(x, dtype=np.float64)
+    mean = x.mean(axis=-1, keepdims=True)
+    var = ((x - mean) ** 2).mean(axis=-1, keepdims=True)
+    return (x - mean) / np.sqrt(var + eps) * np.asarray(gamma, np.float64) + np.asarray(beta, np.float64)
+
+
+def linear(x, weight, bias):
+    """x @ weight^T + bias, weight stored [out_features, in_features]."""
+    return np.asarray(x, np.float64) @ np.asarray(weight, np.float64).T + np.asarray(bias, np.float64)
+
+
+def gelu(z):
+    """Exact GELU: z * Phi(z) = 0.5 z (1 + erf(z / sqrt 2))."""
+    z = np.asarray(z, np.float64)
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+# --------------------------------------------------- neighborhood windows --
+
+def axis_window(n: int, k: int, periodic: bool) -> np.ndarray:
+    """[n, k] indices of the window of every position along one axis.
+
+    Clamped ("bump", Appendix A.2): the window of position i starts at
+    clamp(i - k//2, 0, n - k) and covers k consecutive positions, so it
+    shifts inward at the edges and never shrinks. Requires k <= n.
+    Periodic ("circular padding", Appendix A.2): positions (i + o) mod n for
+    o in [-k//2, k//2]. Requires k <= n so that the k positions are distinct.
+    """
+    if k % 2 != 1 or k < 1 or k > n:
+        raise ValueError(f"window {k} must be odd and at most the axis length {n}")
+    r = k // 2
+    win = np.empty((n, k), dtype=np.int64)
+    for i in range(n):
+        if periodic:
+            for o in range(k):
+                win[i, o] = (i - r + o) % n
+        else:
+            start = min(max(i - r, 0), n - k)
+            for o in range(k):
+                win[i, o] = start + o
+    return win
+
+
+def neighbor_index(D, H, W, kd, kh, kw, lon_periodic=True) -> np.ndarray:
+    """[N, kd*kh*kw] token ids of every token's 3D neighborhood.
+
+    Token id n = (level * H + lat) * W + lon. Level and latitude windows are
+    clamped; longitude is periodic when ``lon_periodic`` (else clamped).
+    Neighbors are listed level-major, then latitude, then longitude.
+    """
+    wd = axis_window(D, kd, False)
+    wh = axis_window(H, kh, False)
+    ww = axis_window(W, kw, lon_periodic)
+    nbr = np.empty((D, H, W, kd, kh, kw), dtype=np.int64)
+    for a in range(kd):
+        for b in range(kh):
+            for c in range(kw):
+                nbr[:, :, :, a, b, c] = ((wd[:, a][:, None, None] * H
+                                          + wh[:, b][None, :, None]) * W
+                                         + ww[:, c][None, None, :])
+    return nbr.reshape(D * H * W, kd * kh * kw)
+
+
+def neighborhood_attention(q, k, v, heads, nbr, return_weights=False, chunk=1024):
+    """3D neighborhood multi-head attention (Section 2.1 "NATTEN").
+
+    q, k, v: [B, N, C] float64; head h owns channels [h*dh, (h+1)*dh).
+    nbr: [Nq, K] neighbor token ids for the queries q[:, :Nq] (normally all N).
+    For each query t and head h:
+        s(t') = q_h(t) . k_h(t') / sqrt(dh)  for t' in nbr[t]
+        a = exp(s - max s) / sum exp(s - max s)
+        o_h(t) = sum_t' a(t') v_h(t')
+    Queries are processed ``chunk`` at a time only to bound memory.
+    Returns o [B, Nq, C] (and the weights [B, Nq, heads, K] if asked).
+    """
+    q = np.asarray(q, np.float64)
+    k = np.asarray(k, np.float64)
+    v = np.asarray(v, np.float64)
+    B, _, C = q.shape
+    Nq, K = nbr.shape
+    dh = C // heads
+    scale = 1.0 / np.sqrt(dh)
+    o = np.empty((B, Nq, C), dtype=np.float64)
+    wts = np.empty((B, Nq, heads, K), dtype=np.float64) if return_weights else None
+    for b in range(B):
+        qb = q[b, :Nq].reshape(Nq, heads, dh)
+        kb = k[b].reshape(-1, heads, dh)
+        vb = v[b].reshape(-1, heads, dh)
+        for t0 in range(0, Nq, chunk):
+            t1 = min(t0 + chunk, Nq)
+            idx = nbr[t0:t1]                        # [T, K]
+            kn = kb[idx]                            # [T, K, heads, dh]
+            vn = vb[idx]
+            s = np.einsum("thd,tkhd->thk", qb[t0:t1], kn) * scale
+            s = s - s.max(axis=-1, keepdims=True)
+            e = np.exp(s)
+            a = e / e.sum(axis=-1, keepdims=True)   # [T, heads, K]
+            o[b, t0:t1] = np.einsum("thk,tkhd->thd", a, vn).reshape(t1 - t0, C)
+            if return_weights:
+                wts[b, t0:t1] = a
+    return (o, wts) if return_weights else o
+
+
+# ------------------------------------------------------ block / processor --
+
+def _f64(w):
+    return {name: np.asarray(val, dtype=np.float64) for name, val in w.items()}
+
+
+def block(x, w, shape):
+    """One neighborhood-attention transformer block on x [B, D, H, W, C] (reading A1 above)."""
+    w = _f64(w)
+    x = np.asarray(x, np.float64)
+    B = x.shape[0]
+    C = shape.C
+    N = shape.D * shape.H * shape.W
+    xf = x.reshape(B, N, C)
+    nbr = neighbor_index(shape.D, shape.H, shape.W, shape.kd, shape.kh, shape.kw, shape.lon_periodic)
+    # attention half
+    u = layer_norm(xf, w["ln1_g"], w["ln1_b"], shape.ln_eps)
+    qkv = linear(u, w["wqkv"], w["bqkv"])
+    q, k, v = qkv[..., :C], qkv[..., C:2 * C], qkv[..., 2 * C:]
+    o = neighborhood_attention(q, k, v, shape.heads, nbr)
+    x1 = xf + linear(o, w["wo"], w["bo"])
+    # MLP half
+    u2 = layer_norm(x1, w["ln2_g"], w["ln2_b"], shape.ln_eps)
+    hid = gelu(linear(u2, w["w1"], w["b1"]))
+    x2 = x1 + linear(hid, w["w2"], w["b2"])
+    return x2.reshape(x.shape)
+
+
+def block_at_tokens(x, w, shape, tokens):
+    """The block's output at the listed token ids only: [B, len(tokens), C].
+
+    The same definition as ``block`` evaluated where asked: LayerNorm and the
+    QKV projection are taken on the union of the listed tokens' neighborhoods,
+    attention and the MLP on the listed tokens. Used for full-size latents,
+    where evaluating every token in float64 would take hours.
+    """
+    w = _f64(w)
+    x = np.asarray(x, np.float64)
+    B = x.shape[0]
+    C = shape.C
+    N = shape.D * shape.H * shape.W
+    xf = x.reshape(B, N, C)
+    tokens = np.asarray(tokens, dtype=np.int64)
+    nbr_all = neighbor_index(shape.D, shape.H, shape.W, shape.kd, shape.kh, shape.kw, shape.lon_periodic)
+    nbr = nbr_all[tokens]                                  # [S, K]
+    needed = np.unique(np.concatenate([nbr.ravel(), tokens]))
+    pos = {int(t): i for i, t in enumerate(needed)}
+    local_nbr = np.vectorize(pos.__getitem__)(nbr)         # [S, K] into `needed`
+    local_tok = np.array([pos[int(t)] for t in tokens], dtype=np.int64)
+    u = layer_norm(xf[:, needed], w["ln1_g"], w["ln1_b"], shape.ln_eps)
+    qkv = linear(u, w["wqkv"], w["bqkv"])
+    q = qkv[:, local_tok, :C]
+    k, v = qkv[..., C:2 * C], qkv[..., 2 * C:]
+    # queries first in a [B, S + ...] layout: neighborhood_attention reads q[:, :S]
+    o = neighborhood_attention(q, k, v, shape.heads, local_nbr)
+    x1 = xf[:, tokens] + linear(o, w["wo"], w["bo"])
+    u2 = layer_norm(x1, w["ln2_g"], w["ln2_b"], shape.ln_eps)
+    return x1 + linear(gelu(linear(u2, w["w1"], w["b1"])), w["w2"], w["b2"])
+
+
+def processor(x, blocks, shape):
+    """One processor call: its blocks in order, each with its own weights."""
+    for w in blocks:
+        x = block(x, w, shape)
+    return x
+
+
+def rollout(x, lead_hours, p6_blocks, p1_blocks, shape, per_step=None):
+    """Latent rollout to ``lead_hours`` (Section 2.1): greedy schedule, six-hour steps first.
+
+    If ``per_step`` is a list, the latent after every processor call is appended to it.
+    """
+    n6, n1 = greedy_schedule(lead_hours)
+    x = np.asarray(x, np.float64)
+    for _ in range(n6):
+        x = processor(x, p6_blocks, shape)
+        if per_step is not None:
+            per_step.append(x)
+    for _ in range(n1):
+        x = processor(x, p1_blocks, shape)
+        if per_step is not None:
+            per_step.append(x)
+    return x
+
+
+def rel_l2(y, y_ref) -> float:
+    """||y - y_ref||_2 / ||y_ref||_2 accumulated in float64."""
+    y = np.asarray(y, np.float64).ravel()
+    y_ref = np.asarray(y_ref, np.float64).ravel()
+    return float(np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref))

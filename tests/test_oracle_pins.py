@@ -1,0 +1,345 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test checks one definition against a value the paper prints, a closed
+form, a library routine that computes a special case, an invariant of the
+definition, or brute force on a tiny grid. A plausible slip in the oracle (a
+dropped bias, a wrong sign, a transposed weight, an off-by-one window) breaks
+at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+import synth
+from oracle import wm_oracle as orc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TINY = synth.Shape(D=3, H=5, W=7, C=8, heads=2, kd=3, kh=3, kw=5, blocks_p6=2, blocks_p1=1)
+
+
+# ------------------------------------------------------------ generator ---
+
+def test_splitmix64_published_first_output():
+    # SplitMix64 seeded with 0: first output 0xE220A8397B1DCDAF (Steele et al. 2014 reference code).
+    u = synth.uniform(np.uint64(0), 1)[0]
+    assert u == (0xE220A8397B1DCDAF >> 11) / 2.0 ** 53
+
+
+def test_generator_is_deterministic_and_normal():
+    a = synth.latent(TINY, 2, seed=1)
+    b = synth.latent(TINY, 2, seed=1)
+    assert np.array_equal(a, b)
+    z = synth.normal(synth.stream_key(7, 3), 200000)
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+
+
+# ------------------------------------------------------------- schedule ---
+
+def _golden_schedule():
+    rows = []
+    with open(os.path.join(GOLDEN, "schedule_paper.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                t, n6, n1 = line.split()[:3]
+                rows.append((int(t), int(n6), int(n1)))
+    return rows
+
+
+@pytest.mark.parametrize("T,n6,n1", _golden_schedule())
+def test_schedule_paper_values(T, n6, n1):
+    assert orc.greedy_schedule(T) == (n6, n1)
+
+
+def test_schedule_is_minimal_coin_change():
+    # dynamic-programming minimum number of {6 h, 1 h} calls for every T <= 1000
+    best = [0] + [10 ** 9] * 1000
+    for t in range(1, 1001):
+        best[t] = min(best[t - 1] + 1, best[t - 6] + 1 if t >= 6 else 10 ** 9)
+    for t in range(1001):
+        n6, n1 = orc.greedy_schedule(t)
+        assert 6 * n6 + n1 == t and 0 <= n1 < 6
+        assert n6 + n1 == best[t]
+
+
+@pytest.mark.parametrize("bad", [-1, -6, 2.5])
+def test_schedule_rejects_bad_lead(bad):
+    with pytest.raises(ValueError):
+        orc.greedy_schedule(bad)
+
+
+# ---------------------------------------------------- LN / linear / GELU ---
+
+def test_layer_norm_linear_gelu_match_torch_fp64():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((5, 16)) * 3 + 1.5
+    g = rng.standard_normal(16)
+    b = rng.standard_normal(16)
+    W = rng.standard_normal((24, 16))
+    bias = rng.standard_normal(24)
+    tx = torch.from_numpy(x)
+    ln_t = F.layer_norm(tx, (16,), torch.from_numpy(g), torch.from_numpy(b), eps=1e-5).numpy()
+    assert np.allclose(orc.layer_norm(x, g, b), ln_t, rtol=0, atol=1e-12)
+    lin_t = F.linear(tx, torch.from_numpy(W), torch.from_numpy(bias)).numpy()
+    assert np.allclose(orc.linear(x, W, bias), lin_t, rtol=0, atol=1e-12)
+    ge_t = F.gelu(tx, approximate="none").numpy()
+    assert np.allclose(orc.gelu(x), ge_t, rtol=0, atol=1e-14)
+
+
+def test_layer_norm_moments():
+    x = np.random.default_rng(1).standard_normal((7, 33)) * 5 - 2
+    y = orc.layer_norm(x, np.ones(33), np.zeros(33), eps=0.0)
+    assert np.allclose(y.mean(-1), 0, atol=1e-13)
+    assert np.allclose((y ** 2).mean(-1), 1, atol=1e-12)   # biased variance -> exactly 1
+
+
+def test_gelu_closed_form_points():
+    # Phi(1) = 0.841344746068542948..., Phi(-1) = 1 - Phi(1)
+    assert orc.gelu(0.0) == 0.0
+    assert abs(orc.gelu(1.0) - 0.8413447460685429) < 1e-15
+    assert abs(orc.gelu(-1.0) + (1 - 0.8413447460685429)) < 1e-15
+    assert abs(orc.gelu(10.0) - 10.0) < 1e-12 and abs(orc.gelu(-10.0)) < 1e-12
+
+
+# ------------------------------------------------------------- windows ---
+
+def _bump_window_bruteforce(i, n, k):
+    """The k consecutive positions inside [0, n) whose centre is nearest to i."""
+    r = k // 2
+    best = min(range(0, n - k + 1), key=lambda s: (abs(s + r - i), s))
+    return set(range(best, best + k))
+
+
+def _periodic_window_bruteforce(i, n, k):
+    r = k // 2
+    return {p for p in range(n) if min(abs(p - i), n - abs(p - i)) <= r}
+
+
+@pytest.mark.parametrize("n,k", [(5, 3), (7, 7), (24, 5), (9, 5), (4, 3), (1, 1), (90, 7)])
+def test_axis_window_clamped_matches_nearest_full_window(n, k):
+    win = orc.axis_window(n, k, periodic=False)
+    for i in range(n):
+        assert len(set(win[i])) == k
+        assert set(win[i]) == _bump_window_bruteforce(i, n, k)
+        assert i in win[i]
+
+
+@pytest.mark.parametrize("n,k", [(7, 5), (7, 7), (48, 5), (180, 7), (3, 3), (5, 1)])
+def test_axis_window_periodic_matches_circular_distance(n, k):
+    win = orc.axis_window(n, k, periodic=True)
+    for i in range(n):
+        assert len(set(win[i])) == k
+        assert set(win[i]) == _periodic_window_bruteforce(i, n, k)
+
+
+def test_axis_window_rejects_even_or_oversized():
+    with pytest.raises(ValueError):
+        orc.axis_window(8, 4, False)
+    with pytest.raises(ValueError):
+        orc.axis_window(4, 5, True)
+
+
+def test_neighbor_sets_have_full_size_and_contain_self():
+    nbr = orc.neighbor_index(4, 24, 48, 3, 5, 5, True)
+    assert nbr.shape == (4 * 24 * 48, 75)
+    for t in range(0, nbr.shape[0], 37):
+        assert len(set(nbr[t])) == 75 and t in nbr[t]
+
+
+# ------------------------------------------------ neighborhood attention ---
+
+def _mask_bruteforce(D, H, W, kd, kh, kw, periodic):
+    N = D * H * W
+    mask = np.zeros((N, N), dtype=bool)
+    for t in range(N):
+        l, i, j = t // (H * W), (t // W) % H, t % W
+        Ld = _bump_window_bruteforce(l, D, kd)
+        Li = _bump_window_bruteforce(i, H, kh)
+        Lj = _periodic_window_bruteforce(j, W, kw) if periodic else _bump_window_bruteforce(j, W, kw)
+        for l2 in Ld:
+            for i2 in Li:
+                for j2 in Lj:
+                    mask[t, (l2 * H + i2) * W + j2] = True
+    return mask
+
+
+def _sdpa_fp64(q, k, v, heads, mask=None):
+    B, N, C = q.shape
+    dh = C // heads
+    tq = torch.from_numpy(q).reshape(B, N, heads, dh).transpose(1, 2)
+    tk = torch.from_numpy(k).reshape(B, N, heads, dh).transpose(1, 2)
+    tv = torch.from_numpy(v).reshape(B, N, heads, dh).transpose(1, 2)
+    am = None if mask is None else torch.from_numpy(mask)
+    o = F.scaled_dot_product_attention(tq, tk, tv, attn_mask=am)
+    return o.transpose(1, 2).reshape(B, N, C).numpy()
+
+
+def _qkv(B, N, C, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((B, N, C)) * 1.5 for _ in range(3)]
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_whole_grid_window_equals_dense_attention(periodic):
+    D, H, W = 3, 5, 7   # odd W so a periodic kw = W window holds every column once
+    q, k, v = _qkv(2, D * H * W, 8, seed=3)
+    nbr = orc.neighbor_index(D, H, W, D, H, W, periodic)
+    o = orc.neighborhood_attention(q, k, v, 2, nbr)
+    ref = _sdpa_fp64(q, k, v, 2)
+    assert np.max(np.abs(o - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("periodic,win", [(True, (3, 3, 5)), (False, (1, 3, 3)), (True, (3, 5, 3))])
+def test_windowed_attention_equals_masked_dense_attention(periodic, win):
+    D, H, W = 3, 5, 7
+    q, k, v = _qkv(1, D * H * W, 12, seed=4)
+    nbr = orc.neighbor_index(D, H, W, *win, periodic)
+    o = orc.neighborhood_attention(q, k, v, 3, nbr)
+    ref = _sdpa_fp64(q, k, v, 3, _mask_bruteforce(D, H, W, *win, periodic))
+    assert np.max(np.abs(o - ref)) < 1e-12
+
+
+def test_attention_rows_sum_to_one():
+    D, H, W = 4, 6, 9
+    q, k, v = _qkv(1, D * H * W, 8, seed=5)
+    nbr = orc.neighbor_index(D, H, W, 3, 5, 5, True)
+    _, a = orc.neighborhood_attention(q * 4, k, v, 2, nbr, return_weights=True)
+    assert np.max(np.abs(a.sum(-1) - 1.0)) < 1e-12
+    assert a.min() >= 0
+
+
+def test_unit_window_returns_values():
+    q, k, v = _qkv(1, 3 * 5 * 7, 8, seed=6)
+    nbr = orc.neighbor_index(3, 5, 7, 1, 1, 1, True)
+    assert np.array_equal(orc.neighborhood_attention(q, k, v, 2, nbr), v)
+
+
+def test_zero_query_gives_window_mean():
+    D, H, W = 3, 5, 7
+    _, k, v = _qkv(1, D * H * W, 8, seed=7)
+    q = np.zeros_like(k)
+    mask = _mask_bruteforce(D, H, W, 3, 3, 5, True)
+    nbr = orc.neighbor_index(D, H, W, 3, 3, 5, True)
+    o = orc.neighborhood_attention(q, k, v, 2, nbr)
+    ref = (mask.astype(np.float64) @ v[0]) / mask.sum(1, keepdims=True)
+    assert np.max(np.abs(o[0] - ref)) < 1e-13
+
+
+def test_circular_padding_then_crop_equals_modular_longitude():
+    # Appendix A.2 "circular padding": pad r_w columns each side by wrap, run the
+    # clamped window on the padded grid, crop -- must equal mod-W windows.
+    D, H, W, win = 3, 5, 9, (3, 3, 5)
+    r = win[2] // 2
+    q, k, v = _qkv(1, D * H * W, 8, seed=8)
+    o_mod = orc.neighborhood_attention(q, k, v, 2, orc.neighbor_index(D, H, W, *win, True))
+
+    def pad(a):
+        g = a.reshape(1, D, H, W, 8)
+        return np.concatenate([g[:, :, :, W - r:], g, g[:, :, :, :r]], axis=3).reshape(1, -1, 8)
+
+    Wp = W + 2 * r
+    o_pad = orc.neighborhood_attention(pad(q), pad(k), pad(v), 2,
+                                       orc.neighbor_index(D, H, Wp, *win, False))
+    o_crop = o_pad.reshape(1, D, H, Wp, 8)[:, :, :, r:r + W].reshape(1, -1, 8)
+    assert np.max(np.abs(o_crop - o_mod)) < 1e-13
+
+
+# ------------------------------------------------------ block / rollout ---
+
+def _torch_block_dense(x, w, shape):
+    """Independent float64 formulation: torch functional ops + dense masked attention."""
+    t = {k: torch.from_numpy(np.asarray(v, np.float64)) for k, v in w.items()}
+    B = x.shape[0]
+    C = shape.C
+    xt = torch.from_numpy(np.asarray(x, np.float64)).reshape(B, -1, C)
+    mask = _mask_bruteforce(shape.D, shape.H, shape.W, shape.kd, shape.kh, shape.kw, shape.lon_periodic)
+    u = F.layer_norm(xt, (C,), t["ln1_g"], t["ln1_b"], eps=shape.ln_eps)
+    qkv = F.linear(u, t["wqkv"], t["bqkv"])
+    q, k, v = qkv.split(C, dim=-1)
+    o = torch.from_numpy(_sdpa_fp64(q.numpy(), k.numpy(), v.numpy(), shape.heads, mask))
+    x1 = xt + F.linear(o, t["wo"], t["bo"])
+    h = F.gelu(F.linear(F.layer_norm(x1, (C,), t["ln2_g"], t["ln2_b"], eps=shape.ln_eps),
+                        t["w1"], t["b1"]), approximate="none")
+    return (x1 + F.linear(h, t["w2"], t["b2"])).reshape(x.shape).numpy()
+
+
+@pytest.mark.parametrize("stress", [False, True])
+@pytest.mark.parametrize("periodic", [True, False])
+def test_block_equals_dense_torch_formulation(stress, periodic):
+    shape = synth.Shape(D=3, H=5, W=7, C=8, heads=2, kd=3, kh=3, kw=5, lon_periodic=periodic)
+    x = synth.latent(shape, 2, seed=1)
+    w = synth.block_weights(shape.C, 0, 0, 0, stress=stress)
+    y = orc.block(x, w, shape)
+    ref = _torch_block_dense(x, w, shape)
+    assert np.max(np.abs(y - ref)) < 1e-11
+
+
+def test_stress_weights_change_the_block():
+    # the pins above would miss a dropped bias only if biases were all zero
+    x = synth.latent(TINY, 1, seed=1)
+    w0 = synth.block_weights(TINY.C, 0, 0, 0, stress=False)
+    w1 = synth.block_weights(TINY.C, 0, 0, 0, stress=True)
+    assert orc.rel_l2(orc.block(x, w1, TINY), orc.block(x, w0, TINY)) > 1e-3
+
+
+def test_block_commutes_with_longitude_roll():
+    x = synth.latent(TINY, 1, seed=2)
+    w = synth.block_weights(TINY.C, 0, 0, 0, stress=True)
+    for s in (1, 3):
+        y1 = orc.block(np.roll(x, s, axis=3), w, TINY)
+        y2 = np.roll(orc.block(x, w, TINY), s, axis=3)
+        assert np.max(np.abs(y1 - y2)) < 1e-12
+
+
+@pytest.mark.parametrize("axis", [1, 2])
+def test_block_commutes_with_level_and_latitude_flip(axis):
+    x = synth.latent(TINY, 1, seed=3)
+    w = synth.block_weights(TINY.C, 0, 0, 0, stress=True)
+    y1 = orc.block(np.flip(x, axis=axis), w, TINY)
+    y2 = np.flip(orc.block(x, w, TINY), axis=axis)
+    assert np.max(np.abs(y1 - y2)) < 1e-12
+
+
+def test_block_output_is_not_flip_symmetric():
+    # the flip pin above is not trivially true: the output itself is not symmetric
+    x = synth.latent(TINY, 1, seed=3)
+    w = synth.block_weights(TINY.C, 0, 0, 0, stress=True)
+    y = orc.block(x, w, TINY)
+    assert orc.rel_l2(np.flip(y, axis=2), y) > 1e-2
+
+
+def test_block_at_tokens_matches_full_block():
+    shape = synth.Shape(D=4, H=6, W=9, C=16, heads=2, kd=3, kh=5, kw=5)
+    x = synth.latent(shape, 2, seed=4)
+    w = synth.block_weights(shape.C, 0, 1, 2, stress=True)
+    full = orc.block(x, w, shape).reshape(2, -1, shape.C)
+    toks = np.array([0, 5, 17, 100, shape.N - 1])
+    part = orc.block_at_tokens(x, w, shape, toks)
+    assert np.max(np.abs(part - full[:, toks])) < 1e-12
+
+
+def test_rollout_schedule_and_prefix_composition():
+    x = synth.latent(TINY, 1, seed=5)
+    p6, p1 = synth.processor_weights(TINY, seed=0, stress=True)
+    assert np.array_equal(orc.rollout(x, 0, p6, p1, TINY), x.astype(np.float64))
+    steps = []
+    y13 = orc.rollout(x, 13, p6, p1, TINY, per_step=steps)
+    assert len(steps) == 3                                 # 13 h = 2 x 6 h + 1 x 1 h
+    y12 = orc.rollout(x, 12, p6, p1, TINY)
+    assert np.max(np.abs(orc.processor(y12, p1, TINY) - y13)) < 1e-12
+    assert np.max(np.abs(orc.processor(orc.processor(x, p6, TINY), p6, TINY) - y12)) < 1e-12
+    # six-hour steps come first: P1(P6(x)) != P6(P1(x))
+    y7 = orc.rollout(x, 7, p6, p1, TINY)
+    other = orc.processor(orc.processor(x, p1, TINY), p6, TINY)
+    assert np.max(np.abs(y7 - orc.processor(orc.processor(x, p6, TINY), p1, TINY))) < 1e-12
+    assert orc.rel_l2(y7, other) > 1e-3
+
+
+def test_rel_l2():
+    a = np.array([3.0, 4.0])
+    assert orc.rel_l2(a, a) == 0.0
+    assert math.isclose(orc.rel_l2(np.array([3.0, 5.0]), a), 1.0 / 5.0)
