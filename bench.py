@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark: full-size six-hour latent rollout step of the WeatherMesh-3 processor.
+
+Workload (one "step" = one forecast): one six-hour processor call (8 blocks)
+on a 9 x 90 x 180 latent (145,800 tokens) with C = 768, 16 heads and a
+5 x 7 x 7 neighborhood window, BF16 tensor-core path with FP32 accumulation
+and FP32 residual stream; seeded synthetic latent ~ N(0,1) and Xavier-uniform
+random weights (the paper's trained weights and ERA-5 data are not available).
+Metric: forecasts/s (six-hour latent forecasts of the full-size latent).
+
+Also reported on the same line: the plain FP32 GPU path on the same step and
+its BF16-vs-FP32 error, an end-to-end number through the host-buffer C-ABI
+call, the dominant kernel's roofline fraction from per-launch CUDA events, the
+14-day rollout on the 4 x 24 x 48 x 128 latent, and the FP64 CPU oracle timed
+on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (replicas, weak scaling): torchrun --nproc-per-node N bench.py --gpus N ...
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "latent-rollout forecasts/s (full-size six-hour step)"
+UNIT = "forecasts/s"
+WORKLOAD = "six-hour processor step, 8 blocks, latent 9x90x180x768 (145,800 tokens), 16 heads, window 5x7x7"
+# bounded CPU-oracle sample: a latitude band of the same latent (all levels,
+# 7 latitudes, 80 longitudes); every token has the same per-token work
+# (full 5x7x7 bump window, C = 768) as in the full latent
+CPU_SAMPLE = dataclasses.replace(synth.FULL, H=7, W=80)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "bf16_tflops": d.get("bf16_tflops", 1900.0),
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", 1700.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_baseline(seconds_budget: float = 12.0, sample=CPU_SAMPLE):
+    """Time the FP64 oracle on a bounded band of the workload; scale to forecasts/s."""
+    from oracle import wm_oracle as orc
+    x = synth.latent(sample, 1, seed=1)
+    w = synth.block_weights(sample.C, 0, 0, 0)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        orc.block(x, w, sample)
+        reps += 1
+        if time.perf_counter() - t0 > seconds_budget or reps >= 8:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    per_token = dt / sample.N
+    sec_per_forecast = per_token * synth.FULL.N * synth.FULL.blocks_p6
+    return {"value": 1.0 / sec_per_forecast, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one block on a {sample.D}x{sample.H}x{sample.W}x{sample.C} latitude band of the latent "
+                       f"({sample.N} tokens, x{reps}), {dt:.2f} s per block, scaled by tokens to 8 blocks x "
+                       f"{synth.FULL.N} tokens; numpy float64, BLAS multi-threaded, gathers single-threaded"),
+            "seconds_per_forecast": sec_per_forecast}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    # each step: the oracle on a smaller band (same per-token work) so K + W steps end in minutes
+    sample = dataclasses.replace(synth.FULL, H=7, W=20)
+    from oracle import wm_oracle as orc
+    x = synth.latent(sample, 1, seed=1)
+    w = synth.block_weights(sample.C, 0, 0, 0)
+    for _ in range(args.warmup):
+        orc.block(x, w, sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.block(x, w, sample)
+    dt = (time.perf_counter() - t0) / args.steps
+    sec_per_forecast = dt / sample.N * synth.FULL.N * synth.FULL.blocks_p6
+    value = 1.0 / sec_per_forecast
+    desc = (f"per step one block on a {sample.D}x{sample.H}x{sample.W}x{sample.C} band ({sample.N} tokens), "
+            f"scaled by tokens to a full-size six-hour step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec_per_forecast * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "impl_note": "FP64 CPU oracle (numpy) on host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2503_22235_gb300 as wm
+    from paper_2503_22235_gb300 import build as wm_build
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wm_build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    shape = synth.FULL
+    p6, p1 = synth.processor_weights(shape, seed=0)
+    ctx = wm.wm_create_from_host(wm.make_config(shape, wm.WM_PREC_BF16), synth.pack_weights(p6, p1))
+    x0 = synth.latent(shape, 1, seed=1 + rank)
+    x = torch.from_numpy(x0).to(dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---------------- warm-up
+    for _ in range(args.warmup):
+        wm.wm_processor_step(ctx, x, wm.WM_P6)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K six-hour steps, per-launch events for the roofline
+    wm.wm_timing_begin(ctx, max_launches=7 * shape.blocks_p6 * args.steps + 16)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            wm.wm_processor_step(ctx, x, wm.WM_P6)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    kt = wm.wm_timing_end(ctx)
+    wm.wm_device_status()
+    total_ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * args.steps / (total_ms / 1e3)
+    launches = sum(c for _, c in kt.values())
+
+    # ---------------- roofline of the dominant kernel
+    peaks = _peaks()
+    M, C = shape.N, shape.C
+    flops = {"qkv": 2.0 * M * C * 3 * C, "proj": 2.0 * M * C * C, "fc1": 2.0 * M * C * 4 * C,
+             "fc2": 2.0 * M * 4 * C * C, "attn": 4.0 * M * shape.kd * shape.kh * shape.kw * C}
+    dom = max((k for k in flops if kt[k][1] > 0), key=lambda k: kt[k][0])
+    avg_ms = kt[dom][0] / kt[dom][1]
+    achieved = flops[dom] / (avg_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"], "traffic": None,
+                "peak_source": f"{peaks['source']} bf16 sustained (kernel timed inside a long step)",
+                "avg_launch_ms": avg_ms,
+                "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()}}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "batch_per_gpu": 1, "blocks": shape.blocks_p6,
+                      "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                      "l2": "working set larger than L2 (latent 448 MB fp32, activations ~2 GB bf16)"},
+           "gpu_launches": launches, "clocks": clk.summary(), "roofline": roofline}
+
+    # ---------------- FP32 plain path on the same step + BF16-vs-FP32 error
+    if not args.no_fp32:
+        xa = torch.from_numpy(x0).to(dev)
+        xb = torch.from_numpy(x0).to(dev)
+        wm.wm_processor_step(ctx, xa, wm.WM_P6)          # BF16
+        wm.wm_set_precision(ctx, wm.WM_PREC_FP32)
+        wm.wm_processor_step(ctx, xb, wm.WM_P6)          # FP32 (also warm-up)
+        torch.cuda.synchronize()
+        err = wm.wm_rel_l2(xa, xb)
+        xc = torch.from_numpy(x0).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wm.wm_processor_step(ctx, xc, wm.WM_P6)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp32_ms = e0.elapsed_time(e1)
+        wm.wm_set_precision(ctx, wm.WM_PREC_BF16)
+        out["fp32_plain"] = {"value": 1e3 / fp32_ms, "unit": UNIT, "ms_per_step": fp32_ms,
+                             "bf16_vs_fp32_rel_l2": err, "speedup_bf16": fp32_ms / ms_per_step}
+        del xa, xb, xc
+
+    # ---------------- end to end through the host-buffer C-ABI call
+    if not args.no_e2e:
+        hin = torch.from_numpy(x0).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            wm.wm_forecast_host(ctx, hin, hout, 6)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            wm.wm_forecast_host(ctx, hin, hout, 6)
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        nbytes = hin.numel() * 4
+        out["e2e"] = {"value": ws * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": nbytes, "call": "wm_forecast_host(lead 6 h)"}
+    wm.wm_destroy(ctx)
+
+    # ---------------- 14-day rollout on the small latent (whole rollout as one CUDA graph)
+    if not args.no_rollout:
+        out["rollout_14d_small"] = small_rollout(wm, torch, dev)
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_oracle_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def small_rollout(wm, torch, dev, reps=3):
+    s = synth.SMALL
+    p6, p1 = synth.processor_weights(s, seed=0)
+    ctx = wm.wm_create_from_host(wm.make_config(s, wm.WM_PREC_BF16), synth.pack_weights(p6, p1))
+    x0 = torch.from_numpy(synth.latent(s, 1, seed=1)).to(dev)
+    res = {"workload": "latent 4x24x48x128, window 3x5x5, P6 8 blocks + P1 4 blocks, greedy schedule"}
+    try:
+        finals = {}
+        for prec, name in ((wm.WM_PREC_BF16, "bf16"), (wm.WM_PREC_FP32, "fp32")):
+            wm.wm_set_precision(ctx, prec)
+            for T in (336, 337):
+                x = x0.clone()
+                wm.wm_latent_rollout(ctx, x, T)         # capture + first replay
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    x.copy_(x0)
+                    wm.wm_latent_rollout(ctx, x, T)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                res[f"{name}_T{T}_forecasts_per_s"] = 1e3 / ms
+                finals[(name, T)] = x.clone()
+        for T in (336, 337):
+            res[f"bf16_vs_fp32_final_rel_l2_T{T}"] = wm.wm_rel_l2(finals[("bf16", T)], finals[("fp32", T)])
+    finally:
+        wm.wm_destroy(ctx)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-rollout", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * wm.h -- C ABI of libwm, the GB300 (sm_103a) latent-rollout library for the
+ * WeatherMesh-3 processor (arXiv 2503.22235).
+ *
+ * What the library computes (paper Section 2.1 and Appendix A.2):
+ *   A forecast to an integer lead time T is a latent rollout: the six-hour
+ *   processor is applied floor(T/6) times, then the one-hour processor T mod 6
+ *   times (the "simple greedy schedule" of Section 2.1). Each processor is a
+ *   stack of neighborhood-attention transformer blocks. One block on a latent
+ *   x [B, D, H, W, C] (channel last; token n = (level*H + lat)*W + lon) is
+ *       u  = LN1(x);  q,k,v = u Wqkv^T + bqkv
+ *       o  = 3D neighborhood attention of q,k,v (per head, window kd x kh x kw,
+ *            clamped -- "bump" -- along level and latitude, periodic along
+ *            longitude -- "circular padding", Appendix A.2), softmax scale 1/sqrt(dh)
+ *       x1 = x + o Wo^T + bo
+ *       x2 = x1 + GELU(LN2(x1) W1^T + b1) W2^T + b2     (exact erf GELU)
+ *   LayerNorm: biased variance, eps from the config, affine.
+ *
+ * Conventions for every call:
+ *   - Status codes are returned, never aborts. On failure wm_last_error()
+ *     gives a message for the calling thread.
+ *   - "device" pointers are CUDA global memory of the current device, owned by
+ *     the caller unless stated otherwise; "host" pointers are CPU memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls taking a
+ *     stream are asynchronous on it unless stated otherwise.
+ *   - Latents at the boundary are always float32 [batch, D, H, W, C],
+ *     contiguous, whatever the internal precision.
+ *   - The library owns weights, workspace, CUDA graphs and server slots.
+ */
+#ifndef WM_H
+#define WM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WM_OK = 0,
+  WM_ERR_INVALID_ARG = 1,  /* bad shape, window, lead time, pointer or enum */
+  WM_ERR_OOM = 2,          /* a device or host allocation failed */
+  WM_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  WM_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out; the context stays usable */
+  WM_ERR_BUSY = 5,         /* server admission: the HBM budget or slot table is full */
+  WM_ERR_IO = 6,           /* weight file missing, short or malformed */
+  WM_ERR_NOT_FOUND = 7     /* unknown request id */
+} wm_status;
+
+typedef enum { WM_P6 = 0 /* six-hour processor */, WM_P1 = 1 /* one-hour processor */ } wm_processor;
+
+typedef enum {
+  WM_PREC_FP32 = 0,        /* plain path: FP32 FMA everywhere (no TF32), CUDA cores */
+  WM_PREC_BF16 = 1,        /* BF16 tcgen05 GEMMs + BF16 tensor-core attention, FP32 accumulate,
+                              FP32 residual stream, FP32 LayerNorm statistics and softmax normalisers */
+  WM_PREC_BF16_FP8MLP = 2  /* as BF16, with the MLP GEMMs in FP8 E4M3 (per-tensor scales) */
+} wm_precision;
+
+typedef struct {
+  int D, H, W, C;          /* latent levels, latitudes, longitudes, channels */
+  int heads;               /* attention heads; C % heads == 0 */
+  int kd, kh, kw;          /* odd window sizes; kd <= D, kh <= H, kw <= W */
+  int blocks_p6;           /* blocks in the six-hour processor (>= 1) */
+  int blocks_p1;           /* blocks in the one-hour processor (>= 1) */
+  int lon_periodic;        /* 1: periodic longitude windows; 0: clamped like the other axes */
+  float ln_eps;            /* LayerNorm epsilon (the processor uses 1e-5) */
+  int precision;           /* wm_precision used by the compute calls */
+  int max_batch;           /* initial workspace capacity in latents (grown on demand) */
+} wm_config;
+
+typedef struct wm_ctx wm_ctx;
+typedef struct wm_server wm_server;
+
+/* ----------------------------------------------------------- context ---- */
+
+/* Create a context on the current CUDA device and upload the weights.
+ * weights_path: weight file = 8-byte magic "WM3WGT1\0", int32 C, blocks_p6,
+ * blocks_p1, 0 (little endian), then float32 tensors: for the six-hour blocks
+ * then the one-hour blocks, per block in this order
+ *   ln1_g[C] ln1_b[C] wqkv[3C][C] bqkv[3C] wo[C][C] bo[C] ln2_g[C] ln2_b[C]
+ *   w1[4C][C] b1[4C] w2[C][4C] b2[C]
+ * (matrices [out][in], q/k/v row blocks of wqkv each head-major).
+ * Errors: WM_ERR_INVALID_ARG (config), WM_ERR_IO (file), WM_ERR_OOM, WM_ERR_CUDA. */
+wm_status wm_create(const wm_config* cfg, const char* weights_path, wm_ctx** out);
+
+/* As wm_create, with the float32 tensors (no header) in host memory; n_floats
+ * must equal (blocks_p6 + blocks_p1) * (12*C*C + 13*C). The buffer is copied. */
+wm_status wm_create_from_host(const wm_config* cfg, const float* weights, size_t n_floats, wm_ctx** out);
+
+/* Synchronises the device, frees everything the context owns. NULL is a no-op. */
+wm_status wm_destroy(wm_ctx* ctx);
+
+/* Switch the precision used by later compute calls (weights for all precisions are resident). */
+wm_status wm_set_precision(wm_ctx* ctx, int precision);
+
+/* ----------------------------------------------------------- compute ---- */
+
+/* One block (index `block` of processor `which`) applied in place to
+ * latent (device, float32 [batch, D, H, W, C]). */
+wm_status wm_block_forward(wm_ctx* ctx, float* latent, int batch, int which, int block, void* stream);
+
+/* One processor call (all of its blocks, in order) in place: a six-hour step
+ * (WM_P6) or a one-hour step (WM_P1), Section 2.1. */
+wm_status wm_processor_step(wm_ctx* ctx, float* latent, int batch, int which, void* stream);
+
+/* Latent rollout to lead_hours (Section 2.1) in place on a device latent:
+ * floor(T/6) six-hour steps then T mod 6 one-hour steps, replayed as one CUDA
+ * graph captured on first use for (latent, batch, T, precision) and cached.
+ * T = 0 is a no-op; T < 0 gives WM_ERR_INVALID_ARG. */
+wm_status wm_latent_rollout(wm_ctx* ctx, float* latent, int batch, int lead_hours, void* stream);
+
+/* End-to-end forecast from HOST memory: copies host_in (float32 [batch,D,H,W,C])
+ * to a library-owned device latent, runs wm_latent_rollout, copies the result
+ * to host_out (may equal host_in) and synchronises the stream before returning.
+ * Pinned host buffers make the copies asynchronous DMA. */
+wm_status wm_forecast_host(wm_ctx* ctx, const float* host_in, float* host_out, int batch,
+                           int lead_hours, void* stream);
+
+/* Batched uneven rollouts: latents[i] (device, one float32 latent each) is
+ * advanced in place to lead_hours[i]. All requests advance together one
+ * processor step per tick; the requests due for the same processor in a tick
+ * run as one batched step (row-independent kernels, so each result equals its
+ * single-request rollout bit for bit). n >= 1; leads >= 0. */
+wm_status wm_rollout_batch(wm_ctx* ctx, float* const* latents, const int* lead_hours, int n, void* stream);
+
+/* Greedy schedule of Section 2.1 (pure host): n6 = T div 6, n1 = T mod 6. */
+wm_status wm_schedule(int lead_hours, int* n6, int* n1);
+
+/* FP64 error reduction on the GPU: out[0] = sum (a-b)^2, out[1] = sum b^2 over n
+ * float32 elements (device pointers); out is HOST memory of 2 doubles, filled
+ * after an internal synchronisation of `stream`. rel-L2 = sqrt(out[0]/out[1]). */
+wm_status wm_rel_l2(const float* a, const float* b, size_t n, double* out, void* stream);
+
+/* Reads (and clears) the device status word that bounded device-side waits
+ * write; synchronises the device. WM_OK or WM_ERR_TIMEOUT. */
+wm_status wm_device_status(void);
+
+/* Self-test of the bounded-wait path: launches one kernel that waits on a
+ * device flag that nothing sets, for at most timeout_us microseconds, then
+ * returns. Expect WM_ERR_TIMEOUT, after which the context must stay usable. */
+wm_status wm_selftest_wait_timeout(int timeout_us);
+
+/* Per-launch kernel timing. Between wm_timing_begin and wm_timing_end every
+ * hot-path kernel launched by compute calls on this context is bracketed by a
+ * CUDA event pair on its stream (rollouts then run eagerly instead of from a
+ * graph). wm_timing_end synchronises the device and returns, per kernel kind
+ * (wm_kernel_kind), the summed device milliseconds and the launch count.
+ * At most max_launches launches are recorded; later ones are not timed. */
+typedef enum { WM_K_LN1 = 0, WM_K_QKV = 1, WM_K_ATTN = 2, WM_K_PROJ = 3, WM_K_LN2 = 4, WM_K_FC1 = 5,
+               WM_K_FC2 = 6, WM_KERNEL_KINDS = 7 } wm_kernel_kind;
+wm_status wm_timing_begin(wm_ctx* ctx, int max_launches);
+wm_status wm_timing_end(wm_ctx* ctx, double* ms_by_kind /* [WM_KERNEL_KINDS] */,
+                        int* launches_by_kind /* [WM_KERNEL_KINDS] */);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* wm_last_error(void);
+
+/* ---------------------------------------------------------- op level ---- */
+/* The individual hot-path kernels on caller device buffers, for parity tests
+ * of each step against the oracle. All synchronous-free; `stream` as above. */
+
+/* LayerNorm over C of M float32 rows of x; out is float32 (out_bf16 = 0) or
+ * bfloat16 (out_bf16 = 1) [M, C]. */
+wm_status wm_op_layernorm(const float* x, const float* gamma, const float* beta, void* out, int out_bf16,
+                          int M, int C, float eps, void* stream);
+
+/* Linear layer D = A W^T + bias on A [M, K], W [N, K] (row major, K contiguous).
+ * precision WM_PREC_FP32: A, W float32 (CUDA-core FP32 FMA);
+ * precision WM_PREC_BF16: A, W bfloat16 (tcgen05, FP32 accumulate), K % 8 == 0.
+ * epilogue 0: out = D (out float32 for FP32, bfloat16 for BF16)
+ * epilogue 1: out = GELU(D) (same out types)
+ * epilogue 2: out (float32 [M, N]) += D   (residual add)
+ * epilogue 3: out (float32) = D. bias may be NULL. */
+wm_status wm_op_linear(const void* A, const void* W, const float* bias, void* out, int M, int N, int K,
+                       int precision, int epilogue, void* stream);
+
+/* 3D neighborhood attention on qkv [batch*D*H*W, 3C] (q | k | v, each head-major)
+ * -> out [batch*D*H*W, C]. precision FP32: float32 in/out; BF16: bfloat16 in/out
+ * (BF16 requires dh = C/heads in {16, 32, 48, 64}). */
+wm_status wm_op_neighborhood_attention(const void* qkv, void* out, int batch, int D, int H, int W, int C,
+                                       int heads, int kd, int kh, int kw, int lon_periodic, int precision,
+                                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WM_H */

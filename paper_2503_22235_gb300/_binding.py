@@ -1,0 +1,227 @@
+"""ctypes binding of libwm (include/wm.h). Argument marshalling only.
+
+Every function here has the name of the C entry point it calls. Device
+buffers are passed as torch CUDA tensors (only their data pointers are used);
+streams default to torch's current stream. A missing library raises: there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "wm.h")
+
+WM_OK, WM_ERR_INVALID_ARG, WM_ERR_OOM, WM_ERR_CUDA, WM_ERR_TIMEOUT, WM_ERR_BUSY, WM_ERR_IO, WM_ERR_NOT_FOUND = range(8)
+WM_P6, WM_P1 = 0, 1
+WM_PREC_FP32, WM_PREC_BF16, WM_PREC_BF16_FP8MLP = 0, 1, 2
+EPI_STORE, EPI_GELU, EPI_RESID_F32, EPI_STORE_F32 = 0, 1, 2, 3
+
+_c_int, _c_float, _vp, _sz = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+
+
+class WmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libwm status {status}: {message}")
+        self.status = status
+
+
+class wm_config(ctypes.Structure):
+    _fields_ = [("D", _c_int), ("H", _c_int), ("W", _c_int), ("C", _c_int), ("heads", _c_int),
+                ("kd", _c_int), ("kh", _c_int), ("kw", _c_int), ("blocks_p6", _c_int), ("blocks_p1", _c_int),
+                ("lon_periodic", _c_int), ("ln_eps", _c_float), ("precision", _c_int), ("max_batch", _c_int)]
+
+
+_SIGS = {
+    "wm_create": (_c_int, [ctypes.POINTER(wm_config), ctypes.c_char_p, ctypes.POINTER(_vp)]),
+    "wm_create_from_host": (_c_int, [ctypes.POINTER(wm_config), _vp, _sz, ctypes.POINTER(_vp)]),
+    "wm_destroy": (_c_int, [_vp]),
+    "wm_set_precision": (_c_int, [_vp, _c_int]),
+    "wm_block_forward": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _vp]),
+    "wm_processor_step": (_c_int, [_vp, _vp, _c_int, _c_int, _vp]),
+    "wm_latent_rollout": (_c_int, [_vp, _vp, _c_int, _c_int, _vp]),
+    "wm_forecast_host": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
+    "wm_rollout_batch": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_c_int), _c_int, _vp]),
+    "wm_schedule": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "wm_rel_l2": (_c_int, [_vp, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp]),
+    "wm_device_status": (_c_int, []),
+    "wm_selftest_wait_timeout": (_c_int, [_c_int]),
+    "wm_last_error": (ctypes.c_char_p, []),
+    "wm_timing_begin": (_c_int, [_vp, _c_int]),
+    "wm_timing_end": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
+    "wm_op_layernorm": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _vp]),
+    "wm_op_linear": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _vp]),
+    "wm_op_neighborhood_attention": (_c_int, [_vp, _vp] + [_c_int] * 12 + [_vp]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libwm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise WmError(WM_ERR_IO, f"{LIB_PATH} is missing: build it with paper_2503_22235_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/wm.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wm_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(status: int):
+    if status != WM_OK:
+        msg = lib().wm_last_error()
+        raise WmError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):  # numpy
+        return t.ctypes.data
+    return int(t)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def make_config(shape, precision=WM_PREC_BF16, max_batch=1) -> wm_config:
+    """wm_config from an object with D, H, W, C, heads, kd, kh, kw, blocks_p6, blocks_p1, lon_periodic, ln_eps."""
+    return wm_config(shape.D, shape.H, shape.W, shape.C, shape.heads, shape.kd, shape.kh, shape.kw,
+                     shape.blocks_p6, shape.blocks_p1, int(bool(shape.lon_periodic)), float(shape.ln_eps),
+                     int(precision), int(max_batch))
+
+
+# ------------------------------------------------------------------ context ---
+
+def wm_create(cfg: wm_config, weights_path: str) -> int:
+    out = _vp()
+    _check(lib().wm_create(ctypes.byref(cfg), weights_path.encode(), ctypes.byref(out)))
+    return out.value
+
+
+def wm_create_from_host(cfg: wm_config, weights) -> int:
+    """weights: contiguous float32 numpy array (the packed weight blob)."""
+    import numpy as np
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    out = _vp()
+    _check(lib().wm_create_from_host(ctypes.byref(cfg), w.ctypes.data, w.size, ctypes.byref(out)))
+    return out.value
+
+
+def wm_destroy(ctx: int) -> None:
+    _check(lib().wm_destroy(ctx))
+
+
+def wm_set_precision(ctx: int, precision: int) -> None:
+    _check(lib().wm_set_precision(ctx, int(precision)))
+
+
+# ------------------------------------------------------------------ compute ---
+
+def wm_block_forward(ctx, latent, which, block, stream=None):
+    _check(lib().wm_block_forward(ctx, _ptr(latent), latent.shape[0], int(which), int(block), _stream(stream)))
+
+
+def wm_processor_step(ctx, latent, which, stream=None):
+    _check(lib().wm_processor_step(ctx, _ptr(latent), latent.shape[0], int(which), _stream(stream)))
+
+
+def wm_latent_rollout(ctx, latent, lead_hours, stream=None):
+    _check(lib().wm_latent_rollout(ctx, _ptr(latent), latent.shape[0], int(lead_hours), _stream(stream)))
+
+
+def wm_forecast_host(ctx, host_in, host_out, lead_hours, stream=None):
+    _check(lib().wm_forecast_host(ctx, _ptr(host_in), _ptr(host_out), host_in.shape[0], int(lead_hours),
+                                  _stream(stream)))
+
+
+def wm_rollout_batch(ctx, latents, lead_hours, stream=None):
+    n = len(latents)
+    ptrs = (_vp * n)(*[_ptr(t) for t in latents])
+    leads = (_c_int * n)(*[int(t) for t in lead_hours])
+    _check(lib().wm_rollout_batch(ctx, ptrs, leads, n, _stream(stream)))
+
+
+def wm_schedule(lead_hours: int) -> tuple[int, int]:
+    n6, n1 = _c_int(), _c_int()
+    _check(lib().wm_schedule(int(lead_hours), ctypes.byref(n6), ctypes.byref(n1)))
+    return n6.value, n1.value
+
+
+def wm_rel_l2(a, b, stream=None) -> float:
+    out = (ctypes.c_double * 2)()
+    _check(lib().wm_rel_l2(_ptr(a), _ptr(b), a.numel(), out, _stream(stream)))
+    return (out[0] / out[1]) ** 0.5 if out[1] > 0 else float(out[0] > 0)
+
+
+def wm_device_status() -> None:
+    _check(lib().wm_device_status())
+
+
+def wm_selftest_wait_timeout(timeout_us: int) -> int:
+    """Returns the status code (WM_ERR_TIMEOUT expected) instead of raising."""
+    return lib().wm_selftest_wait_timeout(int(timeout_us))
+
+
+KERNEL_KINDS = ("ln1", "qkv", "attn", "proj", "ln2", "fc1", "fc2")
+
+
+def wm_timing_begin(ctx, max_launches=4096):
+    _check(lib().wm_timing_begin(ctx, int(max_launches)))
+
+
+def wm_timing_end(ctx) -> dict:
+    """{kind: (total_ms, launches)} for the launches since wm_timing_begin."""
+    n = len(KERNEL_KINDS)
+    ms = (ctypes.c_double * n)()
+    cnt = (_c_int * n)()
+    _check(lib().wm_timing_end(ctx, ms, cnt))
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+# ----------------------------------------------------------------------- ops ---
+
+def wm_op_layernorm(x, gamma, beta, out, eps=1e-5, stream=None):
+    import torch
+    M, C = x.shape[0], x.shape[-1]
+    _check(lib().wm_op_layernorm(_ptr(x), _ptr(gamma), _ptr(beta), _ptr(out), int(out.dtype == torch.bfloat16),
+                                 M, C, float(eps), _stream(stream)))
+
+
+def wm_op_linear(A, W, bias, out, precision, epilogue, stream=None):
+    M, K = A.shape
+    N = W.shape[0]
+    _check(lib().wm_op_linear(_ptr(A), _ptr(W), _ptr(bias), _ptr(out), M, N, K, int(precision), int(epilogue),
+                              _stream(stream)))
+
+
+def wm_op_neighborhood_attention(qkv, out, batch, D, H, W, C, heads, kd, kh, kw, lon_periodic, precision,
+                                 stream=None):
+    _check(lib().wm_op_neighborhood_attention(_ptr(qkv), _ptr(out), batch, D, H, W, C, heads, kd, kh, kw,
+                                              int(bool(lon_periodic)), int(precision), _stream(stream)))

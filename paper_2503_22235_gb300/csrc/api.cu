@@ -1,0 +1,632 @@
+// libwm C ABI: context, weights, workspace, the block / processor / rollout
+// orchestration, CUDA-graph capture of rollouts, batched uneven rollouts and
+// the op-level entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "wm_internal.cuh"
+
+namespace wm {
+const char* last_error_cstr();
+}
+
+using wm::fail;
+using bf16 = __nv_bfloat16;
+
+#define WM_TRY(expr)                 \
+  do {                               \
+    wm_status st_ = (expr);          \
+    if (st_ != WM_OK) return st_;    \
+  } while (0)
+
+namespace {
+
+struct BlockW {
+  const float *ln1_g, *ln1_b, *wqkv, *bqkv, *wo, *bo, *ln2_g, *ln2_b, *w1, *b1, *w2, *b2;
+  bf16 *hqkv, *ho, *h1, *h2;
+  CUtensorMap tm_qkv[2], tm_o[2], tm_1[2], tm_2[2];  // [0]: box 128 rows, [1]: box 256 rows
+};
+
+}  // namespace
+
+struct wm_ctx {
+  wm_config cfg{};
+  int device = 0;
+  long N = 0;
+  float* d_w32 = nullptr;
+  bf16* d_wh = nullptr;
+  std::vector<BlockW> blk[2];
+  // workspace for cap32 (FP32 path) / cap16 (BF16 path) latents
+  int cap32 = 0, cap16 = 0;
+  float *f_u = nullptr, *f_qkv = nullptr, *f_o = nullptr, *f_h = nullptr;
+  bf16 *h_u = nullptr, *h_qkv = nullptr, *h_o = nullptr, *h_h = nullptr;
+  CUtensorMap tm_u{}, tm_o{}, tm_h{};
+  // staging
+  float* d_stage = nullptr;
+  size_t stage_cap = 0;  // floats
+  float* d_io = nullptr;
+  size_t io_cap = 0;     // floats
+  // graphs
+  std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
+  // optional per-launch timing (CUDA events around each hot-path kernel)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_marks;  // (kernel kind, index of the start event)
+  cudaStream_t cap_stream = nullptr;
+  std::recursive_mutex mu;
+};
+
+namespace {
+
+constexpr int kMaxGraphs = 64;
+
+bool is_odd_pos(int k) { return k >= 1 && (k % 2) == 1; }
+
+wm_status validate(const wm_config* c) {
+  if (!c) return fail(WM_ERR_INVALID_ARG, "config is NULL");
+  if (c->D <= 0 || c->H <= 0 || c->W <= 0 || c->C <= 0 || c->heads <= 0)
+    return fail(WM_ERR_INVALID_ARG, "D, H, W, C and heads must be positive");
+  if (c->C % c->heads != 0) return fail(WM_ERR_INVALID_ARG, "C must be a multiple of heads");
+  if (!is_odd_pos(c->kd) || !is_odd_pos(c->kh) || !is_odd_pos(c->kw))
+    return fail(WM_ERR_INVALID_ARG, "window sizes must be odd and positive");
+  if (c->kd > c->D || c->kh > c->H || c->kw > c->W)
+    return fail(WM_ERR_INVALID_ARG, "a window is larger than its axis");
+  if (c->blocks_p6 < 1 || c->blocks_p1 < 1) return fail(WM_ERR_INVALID_ARG, "each processor needs >= 1 block");
+  if (c->precision < WM_PREC_FP32 || c->precision > WM_PREC_BF16_FP8MLP)
+    return fail(WM_ERR_INVALID_ARG, "unknown precision");
+  if (!(c->ln_eps >= 0.f)) return fail(WM_ERR_INVALID_ARG, "ln_eps must be >= 0");
+  return WM_OK;
+}
+
+wm_status check_bf16_shape(const wm_config& c) {
+  const int dh = c.C / c.heads;
+  if (c.C % 64 != 0) return fail(WM_ERR_INVALID_ARG, "BF16 path needs C % 64 == 0");
+  if (dh != 16 && dh != 32 && dh != 48 && dh != 64)
+    return fail(WM_ERR_INVALID_ARG, "BF16 path needs head dim 16, 32, 48 or 64");
+  return WM_OK;
+}
+
+size_t block_floats(int C) { return 12ull * C * C + 13ull * C; }
+
+void destroy_graphs(wm_ctx* ctx) {
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+}
+
+void free_workspace(wm_ctx* ctx) {
+  cudaFree(ctx->f_u); cudaFree(ctx->f_qkv); cudaFree(ctx->f_o); cudaFree(ctx->f_h);
+  cudaFree(ctx->h_u); cudaFree(ctx->h_qkv); cudaFree(ctx->h_o); cudaFree(ctx->h_h);
+  ctx->f_u = ctx->f_qkv = ctx->f_o = ctx->f_h = nullptr;
+  ctx->h_u = ctx->h_qkv = ctx->h_o = ctx->h_h = nullptr;
+  ctx->cap32 = ctx->cap16 = 0;
+}
+
+// Grow the workspace of one precision family to hold `batch` latents. Never
+// called during capture; growing invalidates captured graphs (they hold
+// workspace addresses).
+wm_status ensure_workspace(wm_ctx* ctx, int batch, bool fp32) {
+  int& cap = fp32 ? ctx->cap32 : ctx->cap16;
+  if (batch <= cap) return WM_OK;
+  destroy_graphs(ctx);
+  const size_t M = (size_t)batch * ctx->N, C = ctx->cfg.C;
+  const size_t el = fp32 ? 4 : 2;
+  void** bufs[4];
+  if (fp32) {
+    bufs[0] = (void**)&ctx->f_u; bufs[1] = (void**)&ctx->f_qkv; bufs[2] = (void**)&ctx->f_o; bufs[3] = (void**)&ctx->f_h;
+  } else {
+    bufs[0] = (void**)&ctx->h_u; bufs[1] = (void**)&ctx->h_qkv; bufs[2] = (void**)&ctx->h_o; bufs[3] = (void**)&ctx->h_h;
+  }
+  const size_t widths[4] = {C, 3 * C, C, 4 * C};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 4; ++i) {
+    cudaFree(*bufs[i]);
+    *bufs[i] = nullptr;
+  }
+  cap = 0;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMalloc(bufs[i], M * widths[i] * el);
+  if (e != cudaSuccess) {
+    for (int i = 0; i < 4; ++i) {
+      cudaFree(*bufs[i]);
+      *bufs[i] = nullptr;
+    }
+    cudaGetLastError();
+    return fail(WM_ERR_OOM, "workspace allocation failed for batch " + std::to_string(batch));
+  }
+  cap = batch;
+  if (!fp32 && ctx->cfg.C % 8 == 0) {
+    if (!wm::make_tmap_bf16(&ctx->tm_u, ctx->h_u, M, C, 128) || !wm::make_tmap_bf16(&ctx->tm_o, ctx->h_o, M, C, 128) ||
+        !wm::make_tmap_bf16(&ctx->tm_h, ctx->h_h, M, 4 * C, 128))
+      return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspace");
+  }
+  return WM_OK;
+}
+
+wm_status ensure_workspace(wm_ctx* ctx, int batch) {
+  return ensure_workspace(ctx, batch, ctx->cfg.precision == WM_PREC_FP32);
+}
+
+wm_status ensure_buffer(float** p, size_t* cap, size_t floats) {
+  if (floats <= *cap) return WM_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, floats * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(WM_ERR_OOM, "staging allocation failed");
+  }
+  *cap = floats;
+  return WM_OK;
+}
+
+int pick_bn(long M, int N) {
+  // wide tiles only when they still fill every SM at least once
+  if (N % 256 == 0 && ((M + 127) / 128) * (N / 256) >= wm::num_sms()) return 256;
+  return 128;
+}
+
+wm_status gemm_bf16(const CUtensorMap& tmA, const CUtensorMap* tmB2, long M, int N, int K, const float* bias,
+                    void* out, int ldo, int epi, cudaStream_t s) {
+  wm::GemmArgs a;
+  a.bn = pick_bn(M, N);
+  a.tmA = tmA;
+  a.tmB = tmB2[a.bn == 256 ? 1 : 0];
+  a.M = (int)M; a.N = N; a.K = K;
+  a.bias = bias; a.out = out; a.ldo = ldo; a.epi = epi;
+  return wm::launch_gemm_tc(a, s);
+}
+
+// ---- optional per-launch timing: an event pair around each hot-path kernel
+struct TimedLaunch {
+  wm_ctx* ctx;
+  cudaStream_t s;
+  int idx = -1;
+  TimedLaunch(wm_ctx* c, int kind, cudaStream_t st) : ctx(c), s(st) {
+    if (!ctx->timing) return;
+    const size_t i = ctx->ev_marks.size() * 2;
+    if (i + 2 > ctx->ev_pool.size()) return;
+    if (cudaEventRecord(ctx->ev_pool[i], s) != cudaSuccess) return;
+    idx = (int)i;
+    ctx->ev_marks.push_back({kind, idx});
+  }
+  ~TimedLaunch() {
+    if (idx >= 0) cudaEventRecord(ctx->ev_pool[idx + 1], s);
+  }
+};
+
+wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, cudaStream_t s) {
+  const wm_config& c = ctx->cfg;
+  const BlockW& w = ctx->blk[which][b];
+  const long M = (long)batch * ctx->N;
+  const int C = c.C;
+  const bool per = c.lon_periodic != 0;
+  if (c.precision == WM_PREC_FP32) {
+    { TimedLaunch t(ctx, WM_K_LN1, s);
+      WM_TRY(wm::launch_layernorm(x, w.ln1_g, w.ln1_b, ctx->f_u, false, (int)M, C, c.ln_eps, s)); }
+    { TimedLaunch t(ctx, WM_K_QKV, s);
+      WM_TRY(wm::launch_sgemm(ctx->f_u, w.wqkv, w.bqkv, ctx->f_qkv, (int)M, 3 * C, C, wm::EPI_STORE_F32, s)); }
+    { TimedLaunch t(ctx, WM_K_ATTN, s);
+      WM_TRY(wm::launch_na_f32(ctx->f_qkv, ctx->f_o, batch, c.D, c.H, c.W, C, c.heads, c.kd, c.kh, c.kw, per, s)); }
+    { TimedLaunch t(ctx, WM_K_PROJ, s);
+      WM_TRY(wm::launch_sgemm(ctx->f_o, w.wo, w.bo, x, (int)M, C, C, wm::EPI_RESID_F32, s)); }
+    { TimedLaunch t(ctx, WM_K_LN2, s);
+      WM_TRY(wm::launch_layernorm(x, w.ln2_g, w.ln2_b, ctx->f_u, false, (int)M, C, c.ln_eps, s)); }
+    { TimedLaunch t(ctx, WM_K_FC1, s);
+      WM_TRY(wm::launch_sgemm(ctx->f_u, w.w1, w.b1, ctx->f_h, (int)M, 4 * C, C, wm::EPI_GELU, s)); }
+    { TimedLaunch t(ctx, WM_K_FC2, s);
+      WM_TRY(wm::launch_sgemm(ctx->f_h, w.w2, w.b2, x, (int)M, C, 4 * C, wm::EPI_RESID_F32, s)); }
+    return WM_OK;
+  }
+  { TimedLaunch t(ctx, WM_K_LN1, s);
+    WM_TRY(wm::launch_layernorm(x, w.ln1_g, w.ln1_b, ctx->h_u, true, (int)M, C, c.ln_eps, s)); }
+  { TimedLaunch t(ctx, WM_K_QKV, s);
+    WM_TRY(gemm_bf16(ctx->tm_u, w.tm_qkv, M, 3 * C, C, w.bqkv, ctx->h_qkv, 3 * C, wm::EPI_STORE, s)); }
+  { TimedLaunch t(ctx, WM_K_ATTN, s);
+    WM_TRY(wm::launch_na_bf16(ctx->h_qkv, ctx->h_o, batch, c.D, c.H, c.W, C, c.heads, c.kd, c.kh, c.kw, per, s)); }
+  { TimedLaunch t(ctx, WM_K_PROJ, s);
+    WM_TRY(gemm_bf16(ctx->tm_o, w.tm_o, M, C, C, w.bo, x, C, wm::EPI_RESID_F32, s)); }
+  { TimedLaunch t(ctx, WM_K_LN2, s);
+    WM_TRY(wm::launch_layernorm(x, w.ln2_g, w.ln2_b, ctx->h_u, true, (int)M, C, c.ln_eps, s)); }
+  { TimedLaunch t(ctx, WM_K_FC1, s);
+    WM_TRY(gemm_bf16(ctx->tm_u, w.tm_1, M, 4 * C, C, w.b1, ctx->h_h, 4 * C, wm::EPI_GELU, s)); }
+  { TimedLaunch t(ctx, WM_K_FC2, s);
+    WM_TRY(gemm_bf16(ctx->tm_h, w.tm_2, M, C, 4 * C, w.b2, x, C, wm::EPI_RESID_F32, s)); }
+  return WM_OK;
+}
+
+wm_status processor_step(wm_ctx* ctx, float* x, int batch, int which, cudaStream_t s) {
+  const int L = which == WM_P6 ? ctx->cfg.blocks_p6 : ctx->cfg.blocks_p1;
+  for (int b = 0; b < L; ++b) WM_TRY(block_forward(ctx, x, batch, which, b, s));
+  return WM_OK;
+}
+
+wm_status check_compute(wm_ctx* ctx, const void* latent, int batch) {
+  if (!ctx) return fail(WM_ERR_INVALID_ARG, "context is NULL");
+  if (!latent) return fail(WM_ERR_INVALID_ARG, "latent is NULL");
+  if (batch <= 0) return fail(WM_ERR_INVALID_ARG, "batch must be >= 1");
+  if (ctx->cfg.precision != WM_PREC_FP32) WM_TRY(check_bf16_shape(ctx->cfg));
+  if (ctx->cfg.precision == WM_PREC_BF16_FP8MLP)
+    return fail(WM_ERR_INVALID_ARG, "FP8 MLP precision is not available in this build");
+  return WM_OK;
+}
+
+// Capture `body` on the context's capture stream once per key, then replay the
+// cached graph on `stream`.
+template <typename F>
+wm_status run_graph(wm_ctx* ctx, const std::vector<uintptr_t>& key, cudaStream_t stream, F body) {
+  if (ctx->timing) return body(stream);  // per-launch events need eager launches
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    if ((int)ctx->graphs.size() >= kMaxGraphs) destroy_graphs(ctx);
+    WM_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    wm_status st = body(ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (st != WM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return wm::cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return wm::cuda_fail(e, "cudaGraphInstantiate");
+    it = ctx->graphs.emplace(key, ex).first;
+  }
+  WM_CUDA(cudaGraphLaunch(it->second, stream));
+  return WM_OK;
+}
+
+wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
+  const wm_config& c = ctx->cfg;
+  const int nb = c.blocks_p6 + c.blocks_p1;
+  const size_t per = block_floats(c.C);
+  if (n != per * nb)
+    return fail(WM_ERR_INVALID_ARG, "weight count " + std::to_string(n) + " != expected " + std::to_string(per * nb));
+  WM_CUDA(cudaMalloc(&ctx->d_w32, n * 4));
+  WM_CUDA(cudaMemcpy(ctx->d_w32, host, n * 4, cudaMemcpyHostToDevice));
+  const size_t C = c.C;
+  const size_t mats = 12 * C * C;  // wqkv + wo + w1 + w2 per block
+  WM_CUDA(cudaMalloc(&ctx->d_wh, mats * nb * 2));
+  for (int i = 0; i < nb; ++i) {
+    const int which = i < c.blocks_p6 ? 0 : 1;
+    const float* p = ctx->d_w32 + per * i;
+    BlockW w{};
+    w.ln1_g = p; p += C;
+    w.ln1_b = p; p += C;
+    w.wqkv = p; p += 3 * C * C;
+    w.bqkv = p; p += 3 * C;
+    w.wo = p; p += C * C;
+    w.bo = p; p += C;
+    w.ln2_g = p; p += C;
+    w.ln2_b = p; p += C;
+    w.w1 = p; p += 4 * C * C;
+    w.b1 = p; p += 4 * C;
+    w.w2 = p; p += 4 * C * C;
+    w.b2 = p; p += C;
+    bf16* h = ctx->d_wh + mats * i;
+    w.hqkv = h; h += 3 * C * C;
+    w.ho = h; h += C * C;
+    w.h1 = h; h += 4 * C * C;
+    w.h2 = h;
+    WM_TRY(wm::launch_f32_to_bf16(w.wqkv, w.hqkv, 3 * C * C, 0));
+    WM_TRY(wm::launch_f32_to_bf16(w.wo, w.ho, C * C, 0));
+    WM_TRY(wm::launch_f32_to_bf16(w.w1, w.h1, 4 * C * C, 0));
+    WM_TRY(wm::launch_f32_to_bf16(w.w2, w.h2, 4 * C * C, 0));
+    if (C % 8 == 0) {
+      bool ok = true;
+      for (int k = 0; k < 2; ++k) {
+        const uint32_t box = k ? 256 : 128;
+        ok = ok && wm::make_tmap_bf16(&w.tm_qkv[k], w.hqkv, 3 * C, C, box);
+        ok = ok && wm::make_tmap_bf16(&w.tm_o[k], w.ho, C, C, box);
+        ok = ok && wm::make_tmap_bf16(&w.tm_1[k], w.h1, 4 * C, C, box);
+        ok = ok && wm::make_tmap_bf16(&w.tm_2[k], w.h2, C, 4 * C, box);
+      }
+      if (!ok) return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the weights");
+    }
+    ctx->blk[which].push_back(w);
+  }
+  WM_CUDA(cudaDeviceSynchronize());
+  return WM_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI ===
+extern "C" {
+
+const char* wm_last_error(void) { return wm::last_error_cstr(); }
+
+wm_status wm_schedule(int lead_hours, int* n6, int* n1) {
+  if (lead_hours < 0) return fail(WM_ERR_INVALID_ARG, "lead time must be >= 0");
+  if (!n6 || !n1) return fail(WM_ERR_INVALID_ARG, "output pointers are NULL");
+  *n6 = lead_hours / 6;
+  *n1 = lead_hours % 6;
+  return WM_OK;
+}
+
+wm_status wm_create_from_host(const wm_config* cfg, const float* weights, size_t n_floats, wm_ctx** out) {
+  if (!out) return fail(WM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  WM_TRY(validate(cfg));
+  if (!weights) return fail(WM_ERR_INVALID_ARG, "weights are NULL");
+  WM_TRY(wm::prepare_kernels());
+  wm_ctx* ctx = new wm_ctx();
+  ctx->cfg = *cfg;
+  if (ctx->cfg.max_batch < 1) ctx->cfg.max_batch = 1;
+  cudaGetDevice(&ctx->device);
+  ctx->N = (long)cfg->D * cfg->H * cfg->W;
+  wm_status st = upload_weights(ctx, weights, n_floats);
+  if (st == WM_OK) st = ensure_workspace(ctx, ctx->cfg.max_batch);
+  if (st == WM_OK && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    st = fail(WM_ERR_CUDA, "cudaStreamCreate failed");
+  if (st == WM_OK && !wm::device_status_word()) st = fail(WM_ERR_OOM, "device status word allocation failed");
+  if (st != WM_OK) {
+    wm_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return WM_OK;
+}
+
+wm_status wm_create(const wm_config* cfg, const char* weights_path, wm_ctx** out) {
+  if (!out) return fail(WM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  WM_TRY(validate(cfg));
+  if (!weights_path) return fail(WM_ERR_INVALID_ARG, "weights_path is NULL");
+  FILE* f = std::fopen(weights_path, "rb");
+  if (!f) return fail(WM_ERR_IO, std::string("cannot open ") + weights_path);
+  char magic[8];
+  int32_t hdr[4];
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "WM3WGT1\0", 8) == 0 &&
+            std::fread(hdr, 4, 4, f) == 4;
+  if (!ok || hdr[0] != cfg->C || hdr[1] != cfg->blocks_p6 || hdr[2] != cfg->blocks_p1) {
+    std::fclose(f);
+    return fail(WM_ERR_IO, "weight file header does not match the config");
+  }
+  const size_t n = block_floats(cfg->C) * (cfg->blocks_p6 + cfg->blocks_p1);
+  std::vector<float> buf(n);
+  const size_t got = std::fread(buf.data(), 4, n, f);
+  std::fclose(f);
+  if (got != n) return fail(WM_ERR_IO, "weight file is short");
+  return wm_create_from_host(cfg, buf.data(), n, out);
+}
+
+wm_status wm_destroy(wm_ctx* ctx) {
+  if (!ctx) return WM_OK;
+  cudaDeviceSynchronize();
+  destroy_graphs(ctx);
+  free_workspace(ctx);
+  cudaFree(ctx->d_w32);
+  cudaFree(ctx->d_wh);
+  cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_io);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+  return WM_OK;
+}
+
+wm_status wm_set_precision(wm_ctx* ctx, int precision) {
+  if (!ctx) return fail(WM_ERR_INVALID_ARG, "context is NULL");
+  if (precision < WM_PREC_FP32 || precision > WM_PREC_BF16_FP8MLP) return fail(WM_ERR_INVALID_ARG, "unknown precision");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->cfg.precision = precision;
+  return WM_OK;
+}
+
+wm_status wm_block_forward(wm_ctx* ctx, float* latent, int batch, int which, int block, void* stream) {
+  WM_TRY(check_compute(ctx, latent, batch));
+  if (which != WM_P6 && which != WM_P1) return fail(WM_ERR_INVALID_ARG, "which must be WM_P6 or WM_P1");
+  if (block < 0 || block >= (int)ctx->blk[which].size()) return fail(WM_ERR_INVALID_ARG, "block index out of range");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  WM_TRY(ensure_workspace(ctx, batch));
+  return block_forward(ctx, latent, batch, which, block, (cudaStream_t)stream);
+}
+
+wm_status wm_processor_step(wm_ctx* ctx, float* latent, int batch, int which, void* stream) {
+  WM_TRY(check_compute(ctx, latent, batch));
+  if (which != WM_P6 && which != WM_P1) return fail(WM_ERR_INVALID_ARG, "which must be WM_P6 or WM_P1");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  WM_TRY(ensure_workspace(ctx, batch));
+  return processor_step(ctx, latent, batch, which, (cudaStream_t)stream);
+}
+
+wm_status wm_latent_rollout(wm_ctx* ctx, float* latent, int batch, int lead_hours, void* stream) {
+  if (lead_hours < 0) return fail(WM_ERR_INVALID_ARG, "lead time must be >= 0");
+  WM_TRY(check_compute(ctx, latent, batch));
+  if (lead_hours == 0) return WM_OK;
+  int n6 = 0, n1 = 0;
+  wm_schedule(lead_hours, &n6, &n1);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  WM_TRY(ensure_workspace(ctx, batch));
+  std::vector<uintptr_t> key = {1, (uintptr_t)latent, (uintptr_t)batch, (uintptr_t)n6, (uintptr_t)n1,
+                                (uintptr_t)ctx->cfg.precision};
+  return run_graph(ctx, key, (cudaStream_t)stream, [&](cudaStream_t s) -> wm_status {
+    for (int i = 0; i < n6; ++i) WM_TRY(processor_step(ctx, latent, batch, WM_P6, s));
+    for (int i = 0; i < n1; ++i) WM_TRY(processor_step(ctx, latent, batch, WM_P1, s));
+    return WM_OK;
+  });
+}
+
+wm_status wm_forecast_host(wm_ctx* ctx, const float* host_in, float* host_out, int batch, int lead_hours,
+                           void* stream) {
+  if (!ctx || !host_in || !host_out) return fail(WM_ERR_INVALID_ARG, "NULL argument");
+  if (batch <= 0) return fail(WM_ERR_INVALID_ARG, "batch must be >= 1");
+  if (lead_hours < 0) return fail(WM_ERR_INVALID_ARG, "lead time must be >= 0");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  const size_t floats = (size_t)batch * ctx->N * ctx->cfg.C;
+  WM_TRY(ensure_buffer(&ctx->d_io, &ctx->io_cap, floats));
+  cudaStream_t s = (cudaStream_t)stream;
+  WM_CUDA(cudaMemcpyAsync(ctx->d_io, host_in, floats * 4, cudaMemcpyHostToDevice, s));
+  WM_TRY(wm_latent_rollout(ctx, ctx->d_io, batch, lead_hours, stream));
+  WM_CUDA(cudaMemcpyAsync(host_out, ctx->d_io, floats * 4, cudaMemcpyDeviceToHost, s));
+  WM_CUDA(cudaStreamSynchronize(s));
+  return WM_OK;
+}
+
+wm_status wm_rollout_batch(wm_ctx* ctx, float* const* latents, const int* lead_hours, int n, void* stream) {
+  if (!ctx || !latents || !lead_hours || n < 1) return fail(WM_ERR_INVALID_ARG, "bad batch arguments");
+  for (int i = 0; i < n; ++i) {
+    if (!latents[i]) return fail(WM_ERR_INVALID_ARG, "a latent pointer is NULL");
+    if (lead_hours[i] < 0) return fail(WM_ERR_INVALID_ARG, "lead time must be >= 0");
+  }
+  WM_TRY(check_compute(ctx, latents[0], 1));
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  std::vector<int> n6(n), n1(n);
+  int ticks = 0;
+  for (int i = 0; i < n; ++i) {
+    wm_schedule(lead_hours[i], &n6[i], &n1[i]);
+    ticks = std::max(ticks, n6[i] + n1[i]);
+  }
+  if (ticks == 0) return WM_OK;
+  WM_TRY(ensure_workspace(ctx, n));
+  const size_t lat = (size_t)ctx->N * ctx->cfg.C;
+  WM_TRY(ensure_buffer(&ctx->d_stage, &ctx->stage_cap, lat * n));
+  std::vector<uintptr_t> key = {2, (uintptr_t)n, (uintptr_t)ctx->cfg.precision};
+  for (int i = 0; i < n; ++i) {
+    key.push_back((uintptr_t)latents[i]);
+    key.push_back((uintptr_t)lead_hours[i]);
+  }
+  return run_graph(ctx, key, (cudaStream_t)stream, [&](cudaStream_t s) -> wm_status {
+    std::vector<int> grp;
+    for (int k = 0; k < ticks; ++k) {
+      for (int which = 0; which < 2; ++which) {
+        grp.clear();
+        for (int i = 0; i < n; ++i) {
+          const bool due = which == WM_P6 ? (k < n6[i]) : (k >= n6[i] && k < n6[i] + n1[i]);
+          if (due) grp.push_back(i);
+        }
+        if (grp.empty()) continue;
+        if (grp.size() == 1) {
+          WM_TRY(processor_step(ctx, latents[grp[0]], 1, which, s));
+          continue;
+        }
+        // gather the due latents into one contiguous batch, step, scatter back
+        for (size_t j = 0; j < grp.size(); ++j)
+          WM_CUDA(cudaMemcpyAsync(ctx->d_stage + j * lat, latents[grp[j]], lat * 4, cudaMemcpyDeviceToDevice, s));
+        WM_TRY(processor_step(ctx, ctx->d_stage, (int)grp.size(), which, s));
+        for (size_t j = 0; j < grp.size(); ++j)
+          WM_CUDA(cudaMemcpyAsync(latents[grp[j]], ctx->d_stage + j * lat, lat * 4, cudaMemcpyDeviceToDevice, s));
+      }
+    }
+    return WM_OK;
+  });
+}
+
+wm_status wm_timing_begin(wm_ctx* ctx, int max_launches) {
+  if (!ctx || max_launches < 1) return fail(WM_ERR_INVALID_ARG, "bad timing arguments");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  const size_t want = 2 * (size_t)max_launches;
+  while (ctx->ev_pool.size() < want) {
+    cudaEvent_t e;
+    WM_CUDA(cudaEventCreate(&e));
+    ctx->ev_pool.push_back(e);
+  }
+  ctx->ev_marks.clear();
+  ctx->timing = true;
+  return WM_OK;
+}
+
+wm_status wm_timing_end(wm_ctx* ctx, double* ms_by_kind, int* launches_by_kind) {
+  if (!ctx || !ms_by_kind || !launches_by_kind) return fail(WM_ERR_INVALID_ARG, "bad timing arguments");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->timing = false;
+  for (int k = 0; k < WM_KERNEL_KINDS; ++k) {
+    ms_by_kind[k] = 0.0;
+    launches_by_kind[k] = 0;
+  }
+  WM_CUDA(cudaDeviceSynchronize());
+  for (const auto& m : ctx->ev_marks) {
+    float ms = 0.f;
+    WM_CUDA(cudaEventElapsedTime(&ms, ctx->ev_pool[m.second], ctx->ev_pool[m.second + 1]));
+    ms_by_kind[m.first] += ms;
+    launches_by_kind[m.first] += 1;
+  }
+  ctx->ev_marks.clear();
+  return WM_OK;
+}
+
+wm_status wm_rel_l2(const float* a, const float* b, size_t n, double* out, void* stream) {
+  if (!a || !b || !out) return fail(WM_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* acc = nullptr;
+  WM_CUDA(cudaMalloc(&acc, 2 * sizeof(double)));
+  cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
+  wm_status st = wm::launch_sqdiff(a, b, n, acc, s);
+  if (st == WM_OK) {
+    cudaError_t e = cudaMemcpyAsync(out, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = wm::cuda_fail(e, "wm_rel_l2 readback");
+  }
+  cudaFree(acc);
+  return st;
+}
+
+wm_status wm_device_status(void) {
+  int* w = wm::device_status_word();
+  if (!w) return fail(WM_ERR_OOM, "no device status word");
+  WM_CUDA(cudaDeviceSynchronize());
+  int v = 0;
+  WM_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+  WM_CUDA(cudaMemset(w, 0, sizeof(int)));
+  if (v == WM_ERR_TIMEOUT) return fail(WM_ERR_TIMEOUT, "a bounded device-side wait timed out");
+  if (v != 0) return fail((wm_status)v, "device reported status " + std::to_string(v));
+  return WM_OK;
+}
+
+wm_status wm_selftest_wait_timeout(int timeout_us) {
+  if (timeout_us <= 0 || timeout_us > 10000000) return fail(WM_ERR_INVALID_ARG, "timeout must be in (0, 10 s]");
+  WM_TRY(wm::launch_wait_selftest(timeout_us, 0));
+  return wm_device_status();
+}
+
+// ----------------------------------------------------------------- ops ----
+wm_status wm_op_layernorm(const float* x, const float* gamma, const float* beta, void* out, int out_bf16, int M,
+                          int C, float eps, void* stream) {
+  if (!x || !gamma || !beta || !out || M < 0 || C <= 0) return fail(WM_ERR_INVALID_ARG, "bad layernorm arguments");
+  return wm::launch_layernorm(x, gamma, beta, out, out_bf16 != 0, M, C, eps, (cudaStream_t)stream);
+}
+
+wm_status wm_op_linear(const void* A, const void* W, const float* bias, void* out, int M, int N, int K,
+                       int precision, int epilogue, void* stream) {
+  if (!A || !W || !out || M < 0 || N <= 0 || K <= 0) return fail(WM_ERR_INVALID_ARG, "bad linear arguments");
+  if (epilogue < 0 || epilogue > 3) return fail(WM_ERR_INVALID_ARG, "unknown epilogue");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == WM_PREC_FP32)
+    return wm::launch_sgemm((const float*)A, (const float*)W, bias, (float*)out, M, N, K, epilogue, s);
+  if (precision != WM_PREC_BF16) return fail(WM_ERR_INVALID_ARG, "linear precision must be FP32 or BF16");
+  if (M == 0) return WM_OK;
+  if (K % 8 != 0) return fail(WM_ERR_INVALID_ARG, "BF16 linear needs K % 8 == 0");
+  wm::GemmArgs a;
+  a.bn = pick_bn(M, N);
+  if (!wm::make_tmap_bf16(&a.tmA, A, (uint64_t)M, (uint64_t)K, 128) ||
+      !wm::make_tmap_bf16(&a.tmB, W, (uint64_t)N, (uint64_t)K, (uint32_t)a.bn))
+    return fail(WM_ERR_INVALID_ARG, "cannot build TMA descriptors (pointer alignment or sizes)");
+  a.M = M; a.N = N; a.K = K;
+  a.bias = bias; a.out = out; a.ldo = N; a.epi = epilogue;
+  return wm::launch_gemm_tc(a, s);
+}
+
+wm_status wm_op_neighborhood_attention(const void* qkv, void* out, int batch, int D, int H, int W, int C, int heads,
+                                       int kd, int kh, int kw, int lon_periodic, int precision, void* stream) {
+  wm_config c{};
+  c.D = D; c.H = H; c.W = W; c.C = C; c.heads = heads; c.kd = kd; c.kh = kh; c.kw = kw;
+  c.blocks_p6 = c.blocks_p1 = 1;
+  c.precision = precision;
+  WM_TRY(validate(&c));
+  if (!qkv || !out || batch < 0) return fail(WM_ERR_INVALID_ARG, "bad attention arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == WM_PREC_FP32)
+    return wm::launch_na_f32((const float*)qkv, (float*)out, batch, D, H, W, C, heads, kd, kh, kw, lon_periodic != 0, s);
+  if (precision != WM_PREC_BF16) return fail(WM_ERR_INVALID_ARG, "attention precision must be FP32 or BF16");
+  if (C % 8 != 0) return fail(WM_ERR_INVALID_ARG, "BF16 attention needs C % 8 == 0");
+  return wm::launch_na_bf16((const bf16*)qkv, (bf16*)out, batch, D, H, W, C, heads, kd, kh, kw, lon_periodic != 0, s);
+}
+
+}  // extern "C"

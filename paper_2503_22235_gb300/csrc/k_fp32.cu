@@ -1,0 +1,328 @@
+// Plain FP32 path: LayerNorm, FP32-FMA GEMM with fused epilogues, and 3D
+// neighborhood attention on CUDA cores. Strict FP32 FMA everywhere (no TF32),
+// so that a block matches the float64 oracle to ~1e-6 relative L2.
+#include "wm_internal.cuh"
+
+namespace wm {
+
+// ------------------------------------------------------------ LayerNorm ----
+// One warp per row. Mean and biased variance over C in FP32 (two passes over
+// the row held in registers when C is a multiple of 128 and <= 1024).
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename OutT>
+__device__ __forceinline__ void store_val(OutT* p, float v);
+template <>
+__device__ __forceinline__ void store_val<float>(float* p, float v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_val<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+template <typename OutT, int V4>  // V4 float4 per lane, C = 128 * V4
+__global__ void ln_rows_reg(const float* __restrict__ x, const float* __restrict__ g, const float* __restrict__ b,
+                            OutT* __restrict__ out, int M, float eps) {
+  const int C = 128 * V4;
+  const int lane = threadIdx.x & 31;
+  const long row = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= M) return;
+  const float4* xr = reinterpret_cast<const float4*>(x + row * C);
+  float4 v[V4];
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < V4; ++i) {
+    v[i] = xr[lane + 32 * i];
+    s += (v[i].x + v[i].y) + (v[i].z + v[i].w);
+  }
+  const float mean = warp_sum(s) / C;
+  float q = 0.f;
+#pragma unroll
+  for (int i = 0; i < V4; ++i) {
+    float a = v[i].x - mean, bb = v[i].y - mean, c = v[i].z - mean, d = v[i].w - mean;
+    q += (a * a + bb * bb) + (c * c + d * d);
+  }
+  const float rstd = rsqrtf(warp_sum(q) / C + eps);
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  OutT* orow = out + row * C;
+#pragma unroll
+  for (int i = 0; i < V4; ++i) {
+    const int c = 4 * (lane + 32 * i);
+    float4 gg = g4[lane + 32 * i], bb = b4[lane + 32 * i];
+    float r0 = (v[i].x - mean) * rstd * gg.x + bb.x;
+    float r1 = (v[i].y - mean) * rstd * gg.y + bb.y;
+    float r2 = (v[i].z - mean) * rstd * gg.z + bb.z;
+    float r3 = (v[i].w - mean) * rstd * gg.w + bb.w;
+    if constexpr (sizeof(OutT) == 4) {
+      *reinterpret_cast<float4*>(reinterpret_cast<float*>(orow) + c) = make_float4(r0, r1, r2, r3);
+    } else {
+      __nv_bfloat162 p0 = __floats2bfloat162_rn(r0, r1), p1 = __floats2bfloat162_rn(r2, r3);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t*>(&p0);
+      u.y = *reinterpret_cast<uint32_t*>(&p1);
+      *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(orow) + c) = u;
+    }
+  }
+}
+
+template <typename OutT>
+__global__ void ln_rows_generic(const float* __restrict__ x, const float* __restrict__ g,
+                                const float* __restrict__ b, OutT* __restrict__ out, int M, int C, float eps) {
+  const int lane = threadIdx.x & 31;
+  const long row = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= M) return;
+  const float* xr = x + row * C;
+  float s = 0.f;
+  for (int c = lane; c < C; c += 32) s += xr[c];
+  const float mean = warp_sum(s) / C;
+  float q = 0.f;
+  for (int c = lane; c < C; c += 32) {
+    float d = xr[c] - mean;
+    q += d * d;
+  }
+  const float rstd = rsqrtf(warp_sum(q) / C + eps);
+  for (int c = lane; c < C; c += 32) store_val(out + row * C + c, (xr[c] - mean) * rstd * g[c] + b[c]);
+}
+
+wm_status launch_layernorm(const float* x, const float* g, const float* b, void* out, bool out_bf16, int M, int C,
+                           float eps, cudaStream_t s) {
+  if (M <= 0) return WM_OK;
+  const int warps = 8;
+  dim3 grid((M + warps - 1) / warps), block(32 * warps);
+  const bool aligned = ((uintptr_t)x % 16 == 0) && ((uintptr_t)g % 16 == 0) && ((uintptr_t)b % 16 == 0) &&
+                       ((uintptr_t)out % 16 == 0);
+  const int v4 = (C % 128 == 0 && aligned) ? C / 128 : 0;
+#define WM_LN_CASE(N)                                                                                          \
+  case N:                                                                                                     \
+    if (out_bf16)                                                                                             \
+      ln_rows_reg<__nv_bfloat16, N><<<grid, block, 0, s>>>(x, g, b, (__nv_bfloat16*)out, M, eps);             \
+    else                                                                                                      \
+      ln_rows_reg<float, N><<<grid, block, 0, s>>>(x, g, b, (float*)out, M, eps);                             \
+    break;
+  switch (v4) {
+    WM_LN_CASE(1)
+    WM_LN_CASE(2)
+    WM_LN_CASE(3)
+    WM_LN_CASE(4)
+    WM_LN_CASE(6)
+    WM_LN_CASE(8)
+    default:
+      if (out_bf16)
+        ln_rows_generic<__nv_bfloat16><<<grid, block, 0, s>>>(x, g, b, (__nv_bfloat16*)out, M, C, eps);
+      else
+        ln_rows_generic<float><<<grid, block, 0, s>>>(x, g, b, (float*)out, M, C, eps);
+  }
+#undef WM_LN_CASE
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+// ----------------------------------------------------------------- SGEMM ----
+// out[M, N] (epilogue) A[M, K] . W[N, K]^T + bias. 128 x 128 tile, k-step 16,
+// 256 threads, 8 x 8 outputs per thread, double-buffered shared memory.
+
+__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) sgemm_kernel(const float* __restrict__ A, const float* __restrict__ W,
+                                                    const float* __restrict__ bias, float* __restrict__ out, int M,
+                                                    int N, int K, int epi) {
+  constexpr int BM = 128, BN = 128, BK = 16;
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int tx = tid % 16, ty = tid / 16;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  // each thread loads 2 float4 of A and of W per k-step: rows (tid/4) + 64*r, k (tid%4)*4
+  float4 ra[2], rb[2];
+  auto load_tiles = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int row = tid / 4 + 64 * r, kk = k0 + (tid % 4) * 4;
+      const int am = m0 + row, bn = n0 + row;
+      if (VEC) {
+        ra[r] = (am < M && kk < K) ? *reinterpret_cast<const float4*>(A + (size_t)am * K + kk) : make_float4(0, 0, 0, 0);
+        rb[r] = (bn < N && kk < K) ? *reinterpret_cast<const float4*>(W + (size_t)bn * K + kk) : make_float4(0, 0, 0, 0);
+      } else {
+        float t[4], u[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          t[e] = (am < M && kk + e < K) ? A[(size_t)am * K + kk + e] : 0.f;
+          u[e] = (bn < N && kk + e < K) ? W[(size_t)bn * K + kk + e] : 0.f;
+        }
+        ra[r] = make_float4(t[0], t[1], t[2], t[3]);
+        rb[r] = make_float4(u[0], u[1], u[2], u[3]);
+      }
+    }
+  };
+  auto store_tiles = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int row = tid / 4 + 64 * r, kk = (tid % 4) * 4;
+      As[buf][kk + 0][row] = ra[r].x;
+      As[buf][kk + 1][row] = ra[r].y;
+      As[buf][kk + 2][row] = ra[r].z;
+      As[buf][kk + 3][row] = ra[r].w;
+      Bs[buf][kk + 0][row] = rb[r].x;
+      Bs[buf][kk + 1][row] = rb[r].y;
+      Bs[buf][kk + 2][row] = rb[r].z;
+      Bs[buf][kk + 3][row] = rb[r].w;
+    }
+  };
+
+  const int nk = (K + BK - 1) / BK;
+  load_tiles(0);
+  store_tiles(0);
+  __syncthreads();
+  for (int kt = 0; kt < nk; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < nk) load_tiles((kt + 1) * BK);
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      float a[8], b[8];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (kt + 1 < nk) store_tiles(cur ^ 1);
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (n >= N) continue;
+      float v = acc[i][j] + (bias ? bias[n] : 0.f);
+      float* o = out + (size_t)m * N + n;
+      if (epi == EPI_GELU)
+        *o = gelu_erf(v);
+      else if (epi == EPI_RESID_F32)
+        *o = *o + v;
+      else
+        *o = v;
+    }
+  }
+}
+
+wm_status launch_sgemm(const float* A, const float* W, const float* bias, float* out, int M, int N, int K, int epi,
+                       cudaStream_t s) {
+  if (M <= 0 || N <= 0) return WM_OK;
+  dim3 grid((N + 127) / 128, (M + 127) / 128), block(256);
+  const bool vec = (K % 4 == 0) && ((uintptr_t)A % 16 == 0) && ((uintptr_t)W % 16 == 0);
+  if (vec)
+    sgemm_kernel<true><<<grid, block, 0, s>>>(A, W, bias, out, M, N, K, epi);
+  else
+    sgemm_kernel<false><<<grid, block, 0, s>>>(A, W, bias, out, M, N, K, epi);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+// ------------------------------------------------- neighborhood attention ----
+// One warp per (token, head). Scores for the kd*kh*kw neighbours go to shared
+// memory, the softmax max and sum are warp-shuffle reductions in FP32, and the
+// output channels are split across lanes.
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__global__ void na_f32_kernel(const float* __restrict__ qkv, float* __restrict__ out, int B, int D, int H, int W,
+                              int C, int heads, int kd, int kh, int kw, int periodic) {
+  extern __shared__ float smem[];
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int dh = C / heads, K = kd * kh * kw;
+  float* qs = smem + warp * (K + dh);
+  float* sc = qs + dh;
+  const long N = (long)D * H * W;
+  const long gw = (long)blockIdx.x * warps + warp;
+  if (gw >= (long)B * N * heads) return;  // whole warp leaves together
+  const int head = (int)(gw % heads);
+  const long bt = gw / heads;
+  const long t = bt % N, b = bt / N;
+  const int l = (int)(t / ((long)H * W)), i = (int)((t / W) % H), j = (int)(t % W);
+  const int sl = clampi(l - kd / 2, 0, D - kd), si = clampi(i - kh / 2, 0, H - kh);
+  const int sj = periodic ? j - kw / 2 : clampi(j - kw / 2, 0, W - kw);
+  const long C3 = 3L * C;
+  const float scale = rsqrtf((float)dh);
+  const float* qrow = qkv + (b * N + t) * C3 + head * dh;
+  for (int c = lane; c < dh; c += 32) qs[c] = qrow[c];
+  __syncwarp();
+
+  auto key_token = [&](int kk) -> long {
+    const int a = kk / (kh * kw), bb = (kk / kw) % kh, cc = kk % kw;
+    int jj = sj + cc;
+    if (periodic) jj = ((jj % W) + W) % W;
+    return ((long)(sl + a) * H + (si + bb)) * W + jj;
+  };
+
+  float mx = -INFINITY;
+  for (int kk = lane; kk < K; kk += 32) {
+    const float* krow = qkv + (b * N + key_token(kk)) * C3 + C + head * dh;
+    float d = 0.f;
+    for (int c = 0; c < dh; ++c) d = fmaf(qs[c], krow[c], d);
+    d *= scale;
+    sc[kk] = d;
+    mx = fmaxf(mx, d);
+  }
+  mx = warp_max(mx);
+  float sum = 0.f;
+  for (int kk = lane; kk < K; kk += 32) {
+    const float e = expf(sc[kk] - mx);
+    sc[kk] = e;
+    sum += e;
+  }
+  sum = warp_sum(sum);
+  __syncwarp();
+  const float inv = 1.f / sum;
+  float* orow = out + (b * N + t) * C + head * dh;
+  for (int c = lane; c < dh; c += 32) {
+    float acc = 0.f;
+    for (int kk = 0; kk < K; ++kk) acc = fmaf(sc[kk], qkv[(b * N + key_token(kk)) * C3 + 2 * C + head * dh + c], acc);
+    orow[c] = acc * inv;
+  }
+}
+
+wm_status prepare_na_f32() {
+  WM_CUDA(cudaFuncSetAttribute(na_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  return WM_OK;
+}
+
+wm_status launch_na_f32(const float* qkv, float* out, int B, int D, int H, int W, int C, int heads, int kd, int kh,
+                        int kw, bool periodic, cudaStream_t s) {
+  const long total = (long)B * D * H * W * heads;
+  if (total <= 0) return WM_OK;
+  const int warps = 8;
+  const int K = kd * kh * kw, dh = C / heads;
+  const size_t smem = (size_t)warps * (K + dh) * sizeof(float);
+  if (smem > 227 * 1024) return fail(WM_ERR_INVALID_ARG, "neighborhood window too large for the FP32 attention kernel");
+  dim3 grid((unsigned)((total + warps - 1) / warps)), block(32 * warps);
+  na_f32_kernel<<<grid, block, smem, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, periodic ? 1 : 0);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+}  // namespace wm

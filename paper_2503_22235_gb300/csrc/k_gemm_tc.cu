@@ -1,0 +1,421 @@
+// BF16 GEMM on the 5th-generation tensor cores (tcgen05) for the processor's
+// linear layers: out = epilogue(A[M,K] . W[N,K]^T + bias), FP32 accumulation
+// in tensor memory.
+//
+// Persistent, warp-specialised kernel, one CTA per SM:
+//   warp 0     TMA producer: A (128 x 64) and W (BN x 64) k-slices into a
+//              STAGES-deep shared-memory ring (128-byte swizzle), mbarrier
+//              expect-tx completion.
+//   warp 1     MMA issuer: one thread issues tcgen05.mma (M=128, N=BN, K=16)
+//              into one of two TMEM accumulators; tcgen05.commit frees the
+//              smem stage and, after the last k-slice, hands the accumulator
+//              to the epilogue.
+//   warps 2-9  epilogue: tcgen05.ld (32x32b) rows out of TMEM, add bias, then
+//              bf16 store, GELU + bf16 store, or FP32 residual add, while the
+//              MMA warp already fills the other accumulator.
+// Every mbarrier wait is bounded in time; on a timeout the CTA records
+// WM_ERR_TIMEOUT in the device status word, drains its own copies and MMAs,
+// frees TMEM and returns.
+#include "wm_internal.cuh"
+
+namespace wm {
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;                 // bf16 elements per k-slice = one 128-byte swizzle row
+constexpr int NUM_EPI_WARPS = 8;
+constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
+
+template <int BN>
+struct Cfg {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (BN >= 256) ? 4 : 6;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;   // + alignment slack
+  static constexpr int TMEM_COLS = 2 * BN;                   // two accumulators
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity. False on timeout or when
+// another role of the CTA has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t addr = smem_u32(bar);
+  if (mbar_try_wait(addr, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(addr, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(dst), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core-matrix groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (ignored for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk(const float (&v)[32], int m, int n, int N, int ldo,
+                                               const float* __restrict__ bias, void* __restrict__ out) {
+  float x[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) x[j] = v[j] + ((bias && n + j < N) ? __ldg(bias + n + j) : 0.f);
+  const bool full = (n + 32 <= N);
+  if constexpr (EPI == EPI_STORE || EPI == EPI_GELU) {
+    if constexpr (EPI == EPI_GELU) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = gelu_erf(x[j]);
+    }
+    __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)m * ldo + n;
+    if (full && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint4 u;
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          __nv_bfloat162 p = __floats2bfloat162_rn(x[8 * q + 2 * e], x[8 * q + 2 * e + 1]);
+          w[e] = *reinterpret_cast<uint32_t*>(&p);
+        }
+        u.x = w[0]; u.y = w[1]; u.z = w[2]; u.w = w[3];
+        *reinterpret_cast<uint4*>(o + 8 * q) = u;
+      }
+    } else {
+      for (int j = 0; j < 32; ++j)
+        if (n + j < N) o[j] = __float2bfloat16_rn(x[j]);
+    }
+  } else {
+    float* o = reinterpret_cast<float*>(out) + (size_t)m * ldo + n;
+    if (full && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float4 r = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        if constexpr (EPI == EPI_RESID_F32) {
+          const float4 p = *reinterpret_cast<const float4*>(o + 4 * q);
+          r.x += p.x; r.y += p.y; r.z += p.z; r.w += p.w;
+        }
+        *reinterpret_cast<float4*>(o + 4 * q) = r;
+      }
+    } else {
+      for (int j = 0; j < 32; ++j)
+        if (n + j < N) o[j] = (EPI == EPI_RESID_F32) ? o[j] + x[j] : x[j];
+    }
+  }
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
+                        int N, int K, const float* __restrict__ bias, void* __restrict__ out, int ldo,
+                        int* __restrict__ status) {
+  using CF = Cfg<BN>;
+  constexpr int STAGES = CF::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t smem_base = smem_u32(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int num_n = (N + BN - 1) / BN;
+  const int num_tiles = ((M + BM - 1) / BM) * num_n;
+  const int nk = (K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], NUM_EPI_WARPS);
+    }
+    mbar_init(&drain_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(CF::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------- TMA producer
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, last_parity = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+        const int m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag)) { ok = false; break; }
+          const uint32_t sa = smem_base + stage * CF::STAGE_BYTES;
+          mbar_expect_tx(&full_bar[stage], CF::STAGE_BYTES);
+          tma_load_2d(sa, &tmA, &full_bar[stage], kb * BK, m0);
+          tma_load_2d(sa + CF::A_BYTES, &tmB, &full_bar[stage], kb * BK, n0);
+          issued_mask |= 1u << stage;
+          last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(status, (int)WM_ERR_TIMEOUT);
+        // let our own copies land before the CTA's shared memory is released
+        for (int s = 0; s < STAGES; ++s)
+          if (issued_mask & (1u << s)) {
+            volatile int never = 0;
+            mbar_wait(&full_bar[s], (last_parity >> s) & 1u, &never);
+          }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int it = 0;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const uint32_t acc_par = (uint32_t)(it >> 1) & 1u;
+        if (!mbar_wait(&acce_bar[buf], acc_par ^ 1u, &abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&full_bar[stage], phase, &abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_base + stage * CF::STAGE_BYTES;
+          const uint64_t adesc = sw128_desc(sa), bdesc = sw128_desc(sa + CF::A_BYTES);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            umma_bf16(d_tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (kb | k) != 0);
+          umma_commit(&empty_bar[stage]);
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        umma_commit(&accf_bar[buf]);
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(status, (int)WM_ERR_TIMEOUT);
+        umma_commit(&drain_bar);  // completes once every MMA issued above has finished
+        volatile int never = 0;
+        mbar_wait(&drain_bar, 0, &never);
+      }
+    }
+  } else {
+    // -------------------------------------------------------- epilogue
+    const int quarter = warp & 3;                 // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;             // which half of the BN columns
+    const int row_in_tile = quarter * 32 + lane;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+      const int buf = it & 1;
+      const uint32_t acc_par = (uint32_t)(it >> 1) & 1u;
+      if (!mbar_wait(&accf_bar[buf], acc_par, &abort_flag)) {
+        abort_flag = 1;
+        atomicExch(status, (int)WM_ERR_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const int m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
+      const int m = m0 + row_in_tile;
+      const uint32_t tbase = tmem_base + (uint32_t)(buf * BN) + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+        float v[32];
+        tmem_ld32(tbase + (uint32_t)c, v);
+        if (m < M && n0 + c < N) epilogue_chunk<EPI>(v, m, n0 + c, N, ldo, bias, out);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar[buf]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(CF::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+template <int BN, int EPI>
+static wm_status launch_one(const GemmArgs& a, cudaStream_t s) {
+  using CF = Cfg<BN>;
+  auto kern = gemm_bf16_tc_kernel<BN, EPI>;
+  const int tiles = ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
+  const int grid = tiles < num_sms() ? tiles : num_sms();
+  kern<<<grid, THREADS, CF::SMEM, s>>>(a.tmA, a.tmB, a.M, a.N, a.K, a.bias, a.out, a.ldo, device_status_word());
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+template <int BN, int EPI>
+static wm_status set_attr() {
+  WM_CUDA(cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               Cfg<BN>::SMEM));
+  return WM_OK;
+}
+
+}  // namespace tc
+
+wm_status prepare_gemm_tc() {
+  wm_status st = WM_OK;
+  auto chk = [&](wm_status s) { if (st == WM_OK) st = s; };
+  chk(tc::set_attr<128, EPI_STORE>()); chk(tc::set_attr<128, EPI_GELU>());
+  chk(tc::set_attr<128, EPI_RESID_F32>()); chk(tc::set_attr<128, EPI_STORE_F32>());
+  chk(tc::set_attr<256, EPI_STORE>()); chk(tc::set_attr<256, EPI_GELU>());
+  chk(tc::set_attr<256, EPI_RESID_F32>()); chk(tc::set_attr<256, EPI_STORE_F32>());
+  return st;
+}
+
+wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s) {
+  if (a.M <= 0 || a.N <= 0) return WM_OK;
+  if (a.K <= 0 || a.K % 8 != 0) return fail(WM_ERR_INVALID_ARG, "tcgen05 GEMM needs K > 0 and K % 8 == 0");
+#define WM_GEMM_CASE(BNV)                                                      \
+  switch (a.epi) {                                                             \
+    case EPI_STORE: return tc::launch_one<BNV, EPI_STORE>(a, s);               \
+    case EPI_GELU: return tc::launch_one<BNV, EPI_GELU>(a, s);                 \
+    case EPI_RESID_F32: return tc::launch_one<BNV, EPI_RESID_F32>(a, s);       \
+    case EPI_STORE_F32: return tc::launch_one<BNV, EPI_STORE_F32>(a, s);       \
+    default: return fail(WM_ERR_INVALID_ARG, "unknown GEMM epilogue");         \
+  }
+  if (a.bn == 256) {
+    WM_GEMM_CASE(256)
+  } else if (a.bn == 128) {
+    WM_GEMM_CASE(128)
+  }
+#undef WM_GEMM_CASE
+  return fail(WM_ERR_INVALID_ARG, "GEMM tile width must be 128 or 256");
+}
+
+// ------------------------------------------------------------ TMA maps ----
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || rows == 0 || cols == 0 || (cols * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace wm

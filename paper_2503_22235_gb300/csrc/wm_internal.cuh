@@ -1,0 +1,81 @@
+// Internal declarations shared by the libwm translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/wm.h"
+
+namespace wm {
+
+// ------------------------------------------------------------ errors ----
+void set_error(const std::string& msg);
+wm_status fail(wm_status st, const std::string& msg);
+wm_status cuda_fail(cudaError_t e, const char* what);
+
+#define WM_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return wm::cuda_fail(e_, #call); \
+  } while (0)
+
+// Device status word written by bounded device-side waits (one per device).
+int* device_status_word();
+
+// Upper bound on any single device-side spin-wait (nanoseconds).
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;
+
+enum Epilogue : int {
+  EPI_STORE = 0,       // out = acc + bias (fp32 path: float; bf16 path: bfloat16)
+  EPI_GELU = 1,        // out = GELU(acc + bias)
+  EPI_RESID_F32 = 2,   // out(float) += acc + bias
+  EPI_STORE_F32 = 3,   // out(float) = acc + bias
+};
+
+int num_sms();
+
+// Sets kernel attributes (dynamic shared memory limits) once per device, so
+// that no attribute call happens later inside a stream capture.
+wm_status prepare_kernels();
+wm_status prepare_gemm_tc();
+wm_status prepare_na_bf16();
+
+// ------------------------------------------------------- fp32 plain path ----
+wm_status launch_layernorm(const float* x, const float* g, const float* b, void* out, bool out_bf16, int M,
+                           int C, float eps, cudaStream_t s);
+wm_status launch_sgemm(const float* A, const float* W, const float* bias, float* out, int M, int N, int K,
+                       int epi, cudaStream_t s);
+wm_status launch_na_f32(const float* qkv, float* out, int B, int D, int H, int W, int C, int heads, int kd,
+                        int kh, int kw, bool periodic, cudaStream_t s);
+
+// ------------------------------------------------------------ bf16 path ----
+// TMA descriptor of a row-major bf16 matrix [rows, cols] (cols contiguous),
+// box = box_rows x 64 columns, 128-byte swizzle.
+bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+
+struct GemmArgs {
+  CUtensorMap tmA;     // A [M, K] bf16, box 128 x 64
+  CUtensorMap tmB;     // W [N, K] bf16, box BN x 64
+  int M, N, K;
+  const float* bias;
+  void* out;
+  int ldo;
+  int epi;
+  int bn;              // 128 or 256 (tmB box rows must match)
+};
+wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
+
+wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
+                         int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s);
+
+// ---------------------------------------------------------------- misc ----
+wm_status launch_f32_to_bf16(const float* in, __nv_bfloat16* out, size_t n, cudaStream_t s);
+wm_status launch_sqdiff(const float* a, const float* b, size_t n, double* acc2, cudaStream_t s);
+wm_status launch_wait_selftest(int timeout_us, cudaStream_t s);
+
+}  // namespace wm

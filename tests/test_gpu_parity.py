@@ -1,0 +1,321 @@
+"""GPU parity: every hot-path kernel and the composed block / processor /
+rollout, called through the C ABI, against the FP64 oracle on the same seeded
+inputs.
+
+Tolerances (relative L2 unless noted):
+  * FP32 plain path: <= 1e-5 per block (strict FP32 FMA, no TF32).
+  * BF16 path:       <= 2e-2 per block. Linear layers are checked on
+    bf16-rounded operands, where only FP32 accumulation order differs
+    (<= 1e-5); attention on bf16-rounded q, k, v, where the bf16 rounding of
+    the softmax weights adds ~2^-9 per weight (<= 1e-2).
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2503_22235_gb300 as wm
+import synth
+from oracle import wm_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+CUDA = torch.device("cuda")
+
+
+def dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(CUDA, dtype)
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().to("cpu", torch.float64).numpy()
+
+
+def rel(a, b):
+    return orc.rel_l2(a, b)
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built():
+    from paper_2503_22235_gb300 import build as wm_build
+    wm_build.build()
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+
+
+def make_ctx(shape, precision, seed=0, stress=False, max_batch=1):
+    p6, p1 = synth.processor_weights(shape, seed=seed, stress=stress)
+    blob = synth.pack_weights(p6, p1)
+    ctx = wm.wm_create_from_host(wm.make_config(shape, precision, max_batch), blob)
+    return ctx, p6, p1
+
+
+# ------------------------------------------------------------- LayerNorm ---
+
+@pytest.mark.parametrize("C", [128, 768, 40])
+def test_layernorm_fp32_and_bf16(C):
+    rng = np.random.default_rng(C)
+    M = 257
+    x = (rng.standard_normal((M, C)) * 3 + 1).astype(np.float32)
+    g = (1 + 0.1 * rng.standard_normal(C)).astype(np.float32)
+    b = (0.1 * rng.standard_normal(C)).astype(np.float32)
+    ref = orc.layer_norm(x, g, b, 1e-5)
+    out = torch.empty(M, C, device=CUDA)
+    wm.wm_op_layernorm(dev(x), dev(g), dev(b), out, 1e-5)
+    assert rel(host(out), ref) < 1e-6
+    outh = torch.empty(M, C, device=CUDA, dtype=torch.bfloat16)
+    wm.wm_op_layernorm(dev(x), dev(g), dev(b), outh, 1e-5)
+    assert rel(host(outh), ref) < 4e-3
+
+
+# ---------------------------------------------------------------- linear ---
+
+@pytest.mark.parametrize("M,N,K", [(300, 384, 128), (1000, 512, 128), (77, 130, 24)])
+@pytest.mark.parametrize("epi", [wm.EPI_STORE_F32, wm.EPI_GELU, wm.EPI_RESID_F32])
+def test_linear_fp32(M, N, K, epi):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    W = (rng.standard_normal((N, K)) / np.sqrt(K)).astype(np.float32)
+    bias = (0.1 * rng.standard_normal(N)).astype(np.float32)
+    x0 = rng.standard_normal((M, N)).astype(np.float32)
+    out = dev(x0) if epi == wm.EPI_RESID_F32 else torch.empty(M, N, device=CUDA)
+    wm.wm_op_linear(dev(A), dev(W), dev(bias), out, wm.WM_PREC_FP32, epi)
+    lin = orc.linear(A, W, bias)
+    ref = {wm.EPI_STORE_F32: lin, wm.EPI_GELU: orc.gelu(lin), wm.EPI_RESID_F32: x0 + lin}[epi]
+    assert rel(host(out), ref) < 1e-6
+
+
+@pytest.mark.parametrize("M,N,K", [(1000, 384, 128), (4608, 512, 128), (333, 256, 3072), (20000, 768, 768),
+                                   (130, 136, 72), (4608, 128, 512)])
+def test_linear_bf16_tcgen05(M, N, K):
+    rng = np.random.default_rng(M * 7 + N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    W = (rng.standard_normal((N, K)) / np.sqrt(K)).astype(np.float32)
+    bias = (0.1 * rng.standard_normal(N)).astype(np.float32)
+    Ah, Wh = dev(A, torch.bfloat16), dev(W, torch.bfloat16)
+    lin = orc.linear(bf16_round(A), bf16_round(W), bias)
+    # fp32 output: only the accumulation order differs from the float64 reference
+    out = torch.empty(M, N, device=CUDA)
+    wm.wm_op_linear(Ah, Wh, dev(bias), out, wm.WM_PREC_BF16, wm.EPI_STORE_F32)
+    assert rel(host(out), lin) < 1e-5
+    # bf16 output, GELU epilogue, residual epilogue
+    outh = torch.empty(M, N, device=CUDA, dtype=torch.bfloat16)
+    wm.wm_op_linear(Ah, Wh, dev(bias), outh, wm.WM_PREC_BF16, wm.EPI_STORE)
+    assert rel(host(outh), lin) < 4e-3
+    wm.wm_op_linear(Ah, Wh, dev(bias), outh, wm.WM_PREC_BF16, wm.EPI_GELU)
+    assert rel(host(outh), orc.gelu(lin)) < 4e-3
+    x0 = rng.standard_normal((M, N)).astype(np.float32)
+    xr = dev(x0)
+    wm.wm_op_linear(Ah, Wh, dev(bias), xr, wm.WM_PREC_BF16, wm.EPI_RESID_F32)
+    assert rel(host(xr), x0 + lin) < 1e-5
+
+
+# ------------------------------------------------- neighborhood attention ---
+
+NA_CASES = [
+    # (B, D, H, W, C, heads, kd, kh, kw, periodic)
+    (1, 3, 5, 7, 32, 2, 3, 3, 5, True),
+    (1, 3, 5, 7, 32, 2, 3, 3, 5, False),
+    (2, 4, 24, 48, 128, 4, 3, 5, 5, True),       # small latent: dh 32, window 3x5x5
+    (1, 9, 20, 36, 96, 2, 5, 7, 7, True),        # full-size window and dh 48 on a reduced grid
+    (1, 9, 13, 29, 96, 2, 5, 7, 7, False),       # ragged tiles, clamped longitude
+    (1, 2, 11, 19, 64, 4, 1, 5, 3, True),        # dh 16
+    (1, 5, 9, 23, 128, 2, 3, 9, 9, True),        # dh 64
+    (1, 3, 5, 7, 32, 2, 3, 5, 7, True),          # window = whole grid
+]
+
+
+def _na_inputs(B, D, H, W, C, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((B, D * H * W, 3 * C)) * 1.2).astype(np.float32)
+
+
+@pytest.mark.parametrize("case", NA_CASES)
+def test_neighborhood_attention_fp32(case):
+    B, D, H, W, C, heads, kd, kh, kw, per = case
+    qkv = _na_inputs(B, D, H, W, C, 1)
+    out = torch.empty(B * D * H * W, C, device=CUDA)
+    wm.wm_op_neighborhood_attention(dev(qkv), out, B, D, H, W, C, heads, kd, kh, kw, per, wm.WM_PREC_FP32)
+    nbr = orc.neighbor_index(D, H, W, kd, kh, kw, per)
+    ref = orc.neighborhood_attention(qkv[..., :C], qkv[..., C:2 * C], qkv[..., 2 * C:], heads, nbr)
+    assert rel(host(out).reshape(B, -1, C), ref) < 1e-6
+
+
+@pytest.mark.parametrize("case", NA_CASES)
+def test_neighborhood_attention_bf16(case):
+    B, D, H, W, C, heads, kd, kh, kw, per = case
+    qkv = _na_inputs(B, D, H, W, C, 2)
+    out = torch.empty(B * D * H * W, C, device=CUDA, dtype=torch.bfloat16)
+    wm.wm_op_neighborhood_attention(dev(qkv, torch.bfloat16), out, B, D, H, W, C, heads, kd, kh, kw, per,
+                                    wm.WM_PREC_BF16)
+    q = bf16_round(qkv)
+    nbr = orc.neighbor_index(D, H, W, kd, kh, kw, per)
+    ref = orc.neighborhood_attention(q[..., :C], q[..., C:2 * C], q[..., 2 * C:], heads, nbr)
+    err = rel(host(out).reshape(B, -1, C), ref)
+    assert err < 1e-2, err
+
+
+# ------------------------------------------------------- block / processor ---
+
+@pytest.mark.parametrize("stress", [False, True])
+def test_block_fp32_small_latent(stress):
+    s = synth.SMALL
+    ctx, p6, p1 = make_ctx(s, wm.WM_PREC_FP32, stress=stress)
+    try:
+        x = synth.latent(s, 1, seed=1)
+        for which, blocks in ((wm.WM_P6, p6), (wm.WM_P1, p1)):
+            for b in (0, len(blocks) - 1):
+                xt = dev(x)
+                wm.wm_block_forward(ctx, xt, which, b)
+                err = rel(host(xt), orc.block(x, blocks[b], s))
+                assert err <= 1e-5, (which, b, err)
+    finally:
+        wm.wm_destroy(ctx)
+
+
+@pytest.mark.parametrize("stress", [False, True])
+def test_block_bf16_small_latent(stress):
+    s = synth.SMALL
+    ctx, p6, p1 = make_ctx(s, wm.WM_PREC_BF16, stress=stress)
+    try:
+        x = synth.latent(s, 2, seed=1)
+        xt = dev(x)
+        wm.wm_block_forward(ctx, xt, wm.WM_P6, 0)
+        err = rel(host(xt), orc.block(x, p6[0], s))
+        assert err <= 2e-2, err
+    finally:
+        wm.wm_destroy(ctx)
+
+
+def test_processor_steps_bf16_and_fp32_small_latent():
+    s = synth.SMALL
+    ctx, p6, p1 = make_ctx(s, wm.WM_PREC_BF16, stress=True)
+    try:
+        x = synth.latent(s, 1, seed=3)
+        ref6 = orc.processor(x, p6, s)
+        ref61 = orc.processor(ref6, p1, s)
+        for prec, tol in ((wm.WM_PREC_FP32, 1e-5 * 12), (wm.WM_PREC_BF16, 2e-2 * 12)):
+            wm.wm_set_precision(ctx, prec)
+            xt = dev(x)
+            wm.wm_processor_step(ctx, xt, wm.WM_P6)
+            e6 = rel(host(xt), ref6)
+            wm.wm_processor_step(ctx, xt, wm.WM_P1)
+            e61 = rel(host(xt), ref61)
+            assert e6 < tol and e61 < tol, (prec, e6, e61)
+    finally:
+        wm.wm_destroy(ctx)
+
+
+# --------------------------------------------------------------- rollout ---
+
+def test_rollout_equals_chained_processor_steps_and_oracle():
+    s = synth.Shape(D=4, H=24, W=48, C=128, heads=4, kd=3, kh=5, kw=5, blocks_p6=3, blocks_p1=2)
+    ctx, p6, p1 = make_ctx(s, wm.WM_PREC_BF16, stress=True)
+    try:
+        x = synth.latent(s, 1, seed=4)
+        for prec in (wm.WM_PREC_BF16, wm.WM_PREC_FP32):
+            wm.wm_set_precision(ctx, prec)
+            a = dev(x)
+            wm.wm_latent_rollout(ctx, a, 13)            # graph: 2 six-hour + 1 one-hour step
+            b = dev(x)
+            for which in (wm.WM_P6, wm.WM_P6, wm.WM_P1):
+                wm.wm_processor_step(ctx, b, which)
+            torch.cuda.synchronize()
+            assert torch.equal(a, b)
+            a2 = dev(x)
+            wm.wm_latent_rollout(ctx, a2, 13)           # cached graph replay
+            assert torch.equal(a, a2)
+        ref = orc.rollout(x, 13, p6, p1, s)
+        wm.wm_set_precision(ctx, wm.WM_PREC_FP32)
+        c = dev(x)
+        wm.wm_latent_rollout(ctx, c, 13)
+        assert rel(host(c), ref) < 1e-5 * 8
+        z = dev(x)
+        wm.wm_latent_rollout(ctx, z, 0)
+        assert torch.equal(z, dev(x))
+        with pytest.raises(wm.WmError):
+            wm.wm_latent_rollout(ctx, z, -1)
+    finally:
+        wm.wm_destroy(ctx)
+
+
+def test_forecast_from_host_buffers_equals_device_rollout():
+    s = synth.Shape(D=4, H=24, W=48, C=128, heads=4, kd=3, kh=5, kw=5, blocks_p6=2, blocks_p1=1)
+    ctx, _, _ = make_ctx(s, wm.WM_PREC_BF16)
+    try:
+        x = synth.latent(s, 2, seed=5)
+        hin = torch.from_numpy(x).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        wm.wm_forecast_host(ctx, hin, hout, 7)
+        d = dev(x)
+        wm.wm_latent_rollout(ctx, d, 7)
+        assert torch.equal(hout, d.cpu())
+    finally:
+        wm.wm_destroy(ctx)
+
+
+def test_batched_uneven_rollouts_equal_single_rollouts():
+    s = synth.Shape(D=4, H=24, W=48, C=128, heads=4, kd=3, kh=5, kw=5, blocks_p6=2, blocks_p1=1)
+    ctx, _, _ = make_ctx(s, wm.WM_PREC_BF16, max_batch=4)
+    try:
+        leads = [1, 6, 7, 13, 0, 12]
+        xs = [synth.latent(s, 1, seed=10 + i) for i in range(len(leads))]
+        batch = [dev(x) for x in xs]
+        wm.wm_rollout_batch(ctx, batch, leads)
+        for x, t, got in zip(xs, leads, batch):
+            alone = dev(x)
+            wm.wm_latent_rollout(ctx, alone, t)
+            torch.cuda.synchronize()
+            assert torch.equal(got, alone), t
+    finally:
+        wm.wm_destroy(ctx)
+
+
+# ------------------------------------------------------ full-size latent ---
+
+def test_full_size_block_at_sampled_tokens():
+    s = dataclasses.replace(synth.FULL, blocks_p6=1, blocks_p1=1)
+    ctx, p6, _ = make_ctx(s, wm.WM_PREC_BF16, stress=True)
+    try:
+        x = synth.latent(s, 1, seed=1)
+        rng = np.random.default_rng(0)
+        N = s.N
+        edge = [0, s.W - 1, (s.H - 1) * s.W, N - 1, (4 * s.H + 45) * s.W + 90, (8 * s.H + 3) * s.W + 179]
+        toks = np.unique(np.concatenate([edge, rng.integers(0, N, 18)]))
+        ref = orc.block_at_tokens(x, p6[0], s, toks)
+        for prec, tol in ((wm.WM_PREC_BF16, 2e-2), (wm.WM_PREC_FP32, 1e-5)):
+            wm.wm_set_precision(ctx, prec)
+            xt = dev(x)
+            wm.wm_block_forward(ctx, xt, wm.WM_P6, 0)
+            got = host(xt).reshape(1, N, s.C)[:, toks]
+            err = rel(got, ref)
+            assert err <= tol, (prec, err)
+    finally:
+        wm.wm_destroy(ctx)
+
+
+# ------------------------------------------------------------------ misc ---
+
+def test_rel_l2_fp64_reduction():
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal(1_000_003).astype(np.float32)
+    b = (a + 1e-3 * rng.standard_normal(a.size)).astype(np.float32)
+    got = wm.wm_rel_l2(dev(b), dev(a))
+    assert abs(got - orc.rel_l2(b, a)) < 1e-12
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    assert wm.wm_selftest_wait_timeout(20000) == wm.WM_ERR_TIMEOUT
+    wm.wm_device_status()  # cleared
+    x = torch.ones(64, 128, device=CUDA)
+    g = torch.ones(128, device=CUDA)
+    b = torch.zeros(128, device=CUDA)
+    out = torch.empty_like(x)
+    wm.wm_op_layernorm(x, g, b, out)
+    torch.cuda.synchronize()
+    assert torch.all(out == 0)

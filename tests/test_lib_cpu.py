@@ -1,0 +1,65 @@
+"""Host-side checks of libwm that need no GPU: it builds, loads, exports every
+declared entry point, and its host logic (schedule, argument validation)
+agrees with the oracle and the header's error contract."""
+import ctypes
+
+import pytest
+
+import paper_2503_22235_gb300 as wm
+from paper_2503_22235_gb300 import build as wm_build
+from oracle import wm_oracle as orc
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    wm_build.build()
+
+
+def test_library_exports_every_declared_function():
+    names = wm.header_functions()
+    assert len(names) >= 15
+    L = wm.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_schedule_matches_oracle():
+    for T in range(0, 1001):
+        assert wm.wm_schedule(T) == orc.greedy_schedule(T)
+
+
+def test_schedule_rejects_negative_lead():
+    with pytest.raises(wm.WmError) as e:
+        wm.wm_schedule(-1)
+    assert e.value.status == wm.WM_ERR_INVALID_ARG
+
+
+def _cfg(**kw):
+    base = dict(D=4, H=24, W=48, C=128, heads=4, kd=3, kh=5, kw=5, blocks_p6=8, blocks_p1=4, lon_periodic=1,
+                ln_eps=1e-5, precision=wm.WM_PREC_BF16, max_batch=1)
+    base.update(kw)
+    return wm.wm_config(*[base[f] for f, _ in wm.wm_config._fields_])
+
+
+@pytest.mark.parametrize("bad", [dict(kd=4), dict(kh=0), dict(kw=49), dict(C=130), dict(heads=0),
+                                 dict(blocks_p1=0), dict(precision=7), dict(kd=5)])
+def test_create_rejects_bad_config_before_touching_the_gpu(bad):
+    ctx = ctypes.c_void_p()
+    st = wm.lib().wm_create_from_host(ctypes.byref(_cfg(**bad)), None, 0, ctypes.byref(ctx))
+    assert st == wm.WM_ERR_INVALID_ARG
+    assert ctx.value is None
+    assert wm.lib().wm_last_error()
+
+
+def test_create_reports_missing_weight_file():
+    ctx = ctypes.c_void_p()
+    st = wm.lib().wm_create(ctypes.byref(_cfg()), b"/nonexistent/weights.bin", ctypes.byref(ctx))
+    assert st == wm.WM_ERR_IO
+
+
+def test_null_arguments_are_rejected():
+    L = wm.lib()
+    assert L.wm_latent_rollout(None, None, 1, 6, None) == wm.WM_ERR_INVALID_ARG
+    assert L.wm_processor_step(None, None, 1, 0, None) == wm.WM_ERR_INVALID_ARG
+    assert L.wm_destroy(None) == wm.WM_OK
+    assert L.wm_rollout_batch(None, None, None, 0, None) == wm.WM_ERR_INVALID_ARG
