@@ -280,6 +280,9 @@ def run_ours(args):
     if not args.no_rollout:
         out["rollout_14d_small"] = small_rollout(wm, torch, dev)
 
+    if not args.no_serve and rank == 0:
+        out["serve"] = serve_bench(wm, torch, n_requests=args.serve_requests)
+
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_oracle_baseline()
     if rank == 0:
@@ -319,6 +322,83 @@ def small_rollout(wm, torch, dev, reps=3):
     return res
 
 
+def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0):
+    """Poisson request stream on the small latent through the continuous-batching server.
+
+    Requests: exponential inter-arrivals (mean 1/rate s), lead times uniform in
+    1..336 h, latent i seeded by its request index. Reported per precision:
+    p50/p99 latency (submit -> finished) at the offered rate, forecasts/s
+    closed-loop at saturation, and the BF16-vs-FP32 error of the served results.
+    """
+    s = synth.SMALL
+    p6, p1 = synth.processor_weights(s, seed=0)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    leads = rng.integers(1, 337, n_requests)
+    xs = [synth.latent(s, 1, seed=1000 + i) for i in range(n_requests)]
+    max_batch = 16
+    res = {"workload": (f"Poisson arrivals {rate}/s, {n_requests} requests, leads U{{1..336}} h, latent 4x24x48x128, "
+                        f"P6 8 + P1 4 blocks, max batch {max_batch}")}
+    outs = {}
+    for prec, name in ((wm.WM_PREC_BF16, "bf16"), (wm.WM_PREC_FP32, "fp32")):
+        ctx = wm.wm_create_from_host(wm.make_config(s, prec), synth.pack_weights(p6, p1))
+        lat_floats, ws = wm.wm_ctx_sizes(ctx, max_batch)
+        budget = ws + (max_batch + 64) * lat_floats * 4   # 64 resident request slots
+        try:
+            # ---- open loop at the offered rate
+            srv = wm.wm_server_start(ctx, budget, max_batch)
+            try:
+                t0 = time.perf_counter()
+                arrive = np.cumsum(gaps)
+                ids, got = [], {}
+                i = 0
+                while len(got) < n_requests:
+                    now = time.perf_counter() - t0
+                    while i < n_requests and arrive[i] <= now:
+                        ids.append(wm.wm_server_submit(srv, xs[i], int(leads[i])))
+                        i += 1
+                    for j, rid in enumerate(ids):
+                        if j in got:
+                            continue
+                        buf = np.empty_like(xs[0])
+                        done, _ = wm.wm_server_poll(srv, rid, buf)
+                        if done:
+                            got[j] = buf
+                    time.sleep(0.0005)
+                st = wm.wm_server_stats(srv)
+            finally:
+                wm.wm_server_stop(srv)
+            outs[name] = got
+            res[f"{name}_p50_ms"] = st["p50_ms"]
+            res[f"{name}_p99_ms"] = st["p99_ms"]
+            res[f"{name}_open_loop_forecasts_per_s"] = st["forecasts_per_s"]
+            res[f"{name}_max_resident"] = st["max_active"]
+            # ---- closed loop: all requests at once, throughput at saturation
+            n_sat = min(64, n_requests)
+            srv = wm.wm_server_start(ctx, budget, max_batch)
+            try:
+                t0 = time.perf_counter()
+                ids = [wm.wm_server_submit(srv, xs[j], int(leads[j])) for j in range(n_sat)]
+                left = set(ids)
+                while left:
+                    for rid in list(left):
+                        done, _ = wm.wm_server_poll(srv, rid, None)
+                        if done:
+                            left.discard(rid)
+                    time.sleep(0.0005)
+                dt = time.perf_counter() - t0
+            finally:
+                wm.wm_server_stop(srv)
+            res[f"{name}_saturated_forecasts_per_s"] = n_sat / dt
+        finally:
+            wm.wm_destroy(ctx)
+    errs = [float(np.linalg.norm(outs["bf16"][j].astype(np.float64) - outs["fp32"][j]) /
+                  np.linalg.norm(outs["fp32"][j].astype(np.float64))) for j in range(n_requests)]
+    res["bf16_vs_fp32_rel_l2_median"] = float(np.median(errs))
+    res["bf16_vs_fp32_rel_l2_max"] = float(np.max(errs))
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,6 +409,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rollout", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=120)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

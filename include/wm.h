@@ -94,6 +94,14 @@ wm_status wm_destroy(wm_ctx* ctx);
 /* Switch the precision used by later compute calls (weights for all precisions are resident). */
 wm_status wm_set_precision(wm_ctx* ctx, int precision);
 
+/* Sizes for `batch` latents at the context's current precision: floats per
+ * latent (D*H*W*C) and bytes of the workspace the compute calls need. */
+wm_status wm_ctx_sizes(wm_ctx* ctx, int batch, size_t* latent_floats, size_t* workspace_bytes);
+
+/* Allocate the workspace for `batch` latents now (at the current precision),
+ * so that later calls, and graph captures, allocate nothing. */
+wm_status wm_ctx_reserve(wm_ctx* ctx, int batch);
+
 /* ----------------------------------------------------------- compute ---- */
 
 /* One block (index `block` of processor `which`) applied in place to
@@ -155,6 +163,39 @@ wm_status wm_timing_end(wm_ctx* ctx, double* ms_by_kind /* [WM_KERNEL_KINDS] */,
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* wm_last_error(void);
+
+/* ----------------------------------------------------------- serving ---- */
+/* Forecast server with continuous batching (one worker thread per server).
+ * Requests are a HOST latent (float32 [1, D, H, W, C], copied at submit) and a
+ * lead time. They are admitted into device-resident latent slots in arrival
+ * order while slots are free; the number of slots is set by the HBM budget:
+ *   slots = (hbm_budget_bytes - workspace(max_batch) - max_batch latents of
+ *            staging) / latent bytes.
+ * Each tick, every admitted request with steps left takes one processor step
+ * (greedy schedule, six-hour steps first); the requests due for the same
+ * processor run as batched steps of at most max_batch latents; requests that
+ * arrive meanwhile join at the next tick. A finished request keeps its result
+ * in its slot until wm_server_poll collects it (which frees the slot).
+ * Latency = submit call -> the host sees the tick that finished the request. */
+wm_status wm_server_start(wm_ctx* ctx, size_t hbm_budget_bytes, int max_batch, wm_server** out);
+
+/* Queue a request; WM_ERR_BUSY when the pending queue is full, WM_ERR_INVALID_ARG for T < 0. */
+wm_status wm_server_submit(wm_server* srv, const float* host_latent, int lead_hours, uint64_t* req_id);
+
+/* *done = 1 once the request has finished: its result is copied to host_out
+ * (HOST, may be NULL to discard), latency_ms (may be NULL) is set, and the
+ * request and its slot are released. *done = 0 while it is queued or running.
+ * WM_ERR_NOT_FOUND for an unknown or already collected id. */
+wm_status wm_server_poll(wm_server* srv, uint64_t req_id, float* host_out, int* done, double* latency_ms);
+
+/* out[9] (HOST): completed requests, p50 latency ms, p99 latency ms, mean
+ * latency ms, forecasts/s (completed / (last completion - first arrival)),
+ * most requests resident at once, ticks, batched steps launched, slots. */
+wm_status wm_server_stats(wm_server* srv, double* out);
+
+/* Stops the worker after its current tick and frees the slots; pending and
+ * uncollected requests are dropped. Returns the worker's error, if any. */
+wm_status wm_server_stop(wm_server* srv);
 
 /* ---------------------------------------------------------- op level ---- */
 /* The individual hot-path kernels on caller device buffers, for parity tests

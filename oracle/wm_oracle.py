@@ -254,6 +254,39 @@ def rollout(x, lead_hours, p6_blocks, p1_blocks, shape, per_step=None):
     return x
 
 
+# ---------------------------------------------------------- FP8 E4M3 codec --
+# The FP8 MLP precision (a product-level choice, not a paper requirement)
+# rounds MLP GEMM operands to E4M3 as defined by the OCP 8-bit floating point
+# specification: 1 sign bit, 4 exponent bits with bias 7, 3 mantissa bits;
+# exponent field 0 holds subnormals m/8 * 2^-6; S.1111.111 is NaN; there are
+# no infinities, so the largest finite magnitude is 1.75 * 2^8 = 448.
+
+def e4m3_decode(code: int) -> float:
+    """Value of an E4M3 code (0..255)."""
+    sign = -1.0 if code & 0x80 else 1.0
+    e = (code >> 3) & 0xF
+    m = code & 0x7
+    if e == 0xF and m == 0x7:
+        return float("nan")
+    if e == 0:
+        return sign * (m / 8.0) * 2.0 ** -6
+    return sign * (1.0 + m / 8.0) * 2.0 ** (e - 7)
+
+
+def e4m3_round(x):
+    """Round to the nearest E4M3 value, ties to the even code, saturating at +-448."""
+    x = np.asarray(x, dtype=np.float64)
+    codes = np.arange(0, 0x7F)                       # non-negative finite codes, increasing values
+    vals = np.array([e4m3_decode(int(c)) for c in codes])
+    a = np.minimum(np.abs(x), 448.0)
+    hi = np.clip(np.searchsorted(vals, a, side="left"), 0, len(vals) - 1)
+    lo = np.clip(hi - 1, 0, len(vals) - 1)
+    d_lo, d_hi = a - vals[lo], vals[hi] - a
+    pick_hi = (d_hi < d_lo) | ((d_hi == d_lo) & (codes[hi] % 2 == 0))
+    r = np.where(pick_hi, vals[hi], vals[lo])
+    return np.sign(x) * r
+
+
 def rel_l2(y, y_ref) -> float:
     """||y - y_ref||_2 / ||y_ref||_2 accumulated in float64."""
     y = np.asarray(y, np.float64).ravel()

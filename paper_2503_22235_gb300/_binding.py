@@ -52,9 +52,16 @@ _SIGS = {
     "wm_last_error": (ctypes.c_char_p, []),
     "wm_timing_begin": (_c_int, [_vp, _c_int]),
     "wm_timing_end": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
+    "wm_ctx_sizes": (_c_int, [_vp, _c_int, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
+    "wm_ctx_reserve": (_c_int, [_vp, _c_int]),
+    "wm_server_start": (_c_int, [_vp, _sz, _c_int, ctypes.POINTER(_vp)]),
+    "wm_server_submit": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(ctypes.c_uint64)]),
+    "wm_server_poll": (_c_int, [_vp, ctypes.c_uint64, _vp, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_double)]),
+    "wm_server_stats": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "wm_server_stop": (_c_int, [_vp]),
     "wm_op_layernorm": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _vp]),
     "wm_op_linear": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _vp]),
-    "wm_op_neighborhood_attention": (_c_int, [_vp, _vp] + [_c_int] * 12 + [_vp]),
+    "wm_op_neighborhood_attention": (_c_int, [_vp, _vp] + [_c_int] * 11 + [_vp]),
 }
 
 _lib = None
@@ -187,6 +194,52 @@ def wm_device_status() -> None:
 def wm_selftest_wait_timeout(timeout_us: int) -> int:
     """Returns the status code (WM_ERR_TIMEOUT expected) instead of raising."""
     return lib().wm_selftest_wait_timeout(int(timeout_us))
+
+
+def wm_ctx_sizes(ctx, batch=1) -> tuple[int, int]:
+    lat, ws = _sz(), _sz()
+    _check(lib().wm_ctx_sizes(ctx, int(batch), ctypes.byref(lat), ctypes.byref(ws)))
+    return lat.value, ws.value
+
+
+def wm_ctx_reserve(ctx, batch):
+    _check(lib().wm_ctx_reserve(ctx, int(batch)))
+
+
+# ------------------------------------------------------------------ serving ---
+
+def wm_server_start(ctx, hbm_budget_bytes, max_batch) -> int:
+    out = _vp()
+    _check(lib().wm_server_start(ctx, int(hbm_budget_bytes), int(max_batch), ctypes.byref(out)))
+    return out.value
+
+
+def wm_server_submit(srv, host_latent, lead_hours) -> int:
+    """host_latent: contiguous float32 host array/tensor of one latent. Raises WmError (WM_ERR_BUSY) when full."""
+    rid = ctypes.c_uint64()
+    _check(lib().wm_server_submit(srv, _ptr(host_latent), int(lead_hours), ctypes.byref(rid)))
+    return rid.value
+
+
+def wm_server_poll(srv, req_id, host_out=None):
+    """(done, latency_ms): copies the result into host_out when done."""
+    done, lat = _c_int(), ctypes.c_double()
+    _check(lib().wm_server_poll(srv, ctypes.c_uint64(req_id), _ptr(host_out), ctypes.byref(done), ctypes.byref(lat)))
+    return bool(done.value), lat.value
+
+
+SERVER_STATS = ("completed", "p50_ms", "p99_ms", "mean_ms", "forecasts_per_s", "max_active", "ticks",
+                "batched_steps", "slots")
+
+
+def wm_server_stats(srv) -> dict:
+    out = (ctypes.c_double * len(SERVER_STATS))()
+    _check(lib().wm_server_stats(srv, out))
+    return {k: out[i] for i, k in enumerate(SERVER_STATS)}
+
+
+def wm_server_stop(srv):
+    _check(lib().wm_server_stop(srv))
 
 
 KERNEL_KINDS = ("ln1", "qkv", "attn", "proj", "ln2", "fc1", "fc2")

@@ -47,6 +47,7 @@ struct wm_ctx {
   float *f_u = nullptr, *f_qkv = nullptr, *f_o = nullptr, *f_h = nullptr;
   bf16 *h_u = nullptr, *h_qkv = nullptr, *h_o = nullptr, *h_h = nullptr;
   CUtensorMap tm_u{}, tm_o{}, tm_h{};
+  CUtensorMap tmc_qkv{}, tmc_h{};   // GEMM outputs (TMA store descriptors)
   // staging
   float* d_stage = nullptr;
   size_t stage_cap = 0;  // floats
@@ -139,9 +140,19 @@ wm_status ensure_workspace(wm_ctx* ctx, int batch, bool fp32) {
     return fail(WM_ERR_OOM, "workspace allocation failed for batch " + std::to_string(batch));
   }
   cap = batch;
+  if (!fp32 && check_bf16_shape(ctx->cfg) == WM_OK) {
+    // pick the attention kernel's CTA plan for this batch by timing the candidates
+    const wm_config& c = ctx->cfg;
+    WM_CUDA(cudaMemset(ctx->h_qkv, 0, M * 3 * C * 2));
+    WM_TRY(wm::autotune_na_bf16(ctx->h_qkv, ctx->h_o, batch, c.D, c.H, c.W, c.C, c.heads, c.kd, c.kh, c.kw,
+                                c.lon_periodic != 0, 0, nullptr));
+    WM_CUDA(cudaDeviceSynchronize());
+  }
   if (!fp32 && ctx->cfg.C % 8 == 0) {
     if (!wm::make_tmap_bf16(&ctx->tm_u, ctx->h_u, M, C, 128) || !wm::make_tmap_bf16(&ctx->tm_o, ctx->h_o, M, C, 128) ||
-        !wm::make_tmap_bf16(&ctx->tm_h, ctx->h_h, M, 4 * C, 128))
+        !wm::make_tmap_bf16(&ctx->tm_h, ctx->h_h, M, 4 * C, 128) ||
+        !wm::make_tmap_out(&ctx->tmc_qkv, ctx->h_qkv, M, 3 * C, false) ||
+        !wm::make_tmap_out(&ctx->tmc_h, ctx->h_h, M, 4 * C, false))
       return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspace");
   }
   return WM_OK;
@@ -170,14 +181,15 @@ int pick_bn(long M, int N) {
   return 128;
 }
 
-wm_status gemm_bf16(const CUtensorMap& tmA, const CUtensorMap* tmB2, long M, int N, int K, const float* bias,
-                    void* out, int ldo, int epi, cudaStream_t s) {
+wm_status gemm_bf16(const CUtensorMap& tmA, const CUtensorMap* tmB2, const CUtensorMap& tmC, long M, int N, int K,
+                    const float* bias, int epi, cudaStream_t s) {
   wm::GemmArgs a;
   a.bn = pick_bn(M, N);
   a.tmA = tmA;
   a.tmB = tmB2[a.bn == 256 ? 1 : 0];
+  a.tmC = tmC;
   a.M = (int)M; a.N = N; a.K = K;
-  a.bias = bias; a.out = out; a.ldo = ldo; a.epi = epi;
+  a.bias = bias; a.epi = epi;
   return wm::launch_gemm_tc(a, s);
 }
 
@@ -222,20 +234,23 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, cuda
       WM_TRY(wm::launch_sgemm(ctx->f_h, w.w2, w.b2, x, (int)M, C, 4 * C, wm::EPI_RESID_F32, s)); }
     return WM_OK;
   }
+  CUtensorMap tm_x;   // the caller's latent as the residual-add target
+  if (!wm::make_tmap_out(&tm_x, x, (uint64_t)M, (uint64_t)C, true))
+    return fail(WM_ERR_INVALID_ARG, "latent pointer must be 16-byte aligned for the BF16 path");
   { TimedLaunch t(ctx, WM_K_LN1, s);
     WM_TRY(wm::launch_layernorm(x, w.ln1_g, w.ln1_b, ctx->h_u, true, (int)M, C, c.ln_eps, s)); }
   { TimedLaunch t(ctx, WM_K_QKV, s);
-    WM_TRY(gemm_bf16(ctx->tm_u, w.tm_qkv, M, 3 * C, C, w.bqkv, ctx->h_qkv, 3 * C, wm::EPI_STORE, s)); }
+    WM_TRY(gemm_bf16(ctx->tm_u, w.tm_qkv, ctx->tmc_qkv, M, 3 * C, C, w.bqkv, wm::EPI_STORE, s)); }
   { TimedLaunch t(ctx, WM_K_ATTN, s);
     WM_TRY(wm::launch_na_bf16(ctx->h_qkv, ctx->h_o, batch, c.D, c.H, c.W, C, c.heads, c.kd, c.kh, c.kw, per, s)); }
   { TimedLaunch t(ctx, WM_K_PROJ, s);
-    WM_TRY(gemm_bf16(ctx->tm_o, w.tm_o, M, C, C, w.bo, x, C, wm::EPI_RESID_F32, s)); }
+    WM_TRY(gemm_bf16(ctx->tm_o, w.tm_o, tm_x, M, C, C, w.bo, wm::EPI_RESID_F32, s)); }
   { TimedLaunch t(ctx, WM_K_LN2, s);
     WM_TRY(wm::launch_layernorm(x, w.ln2_g, w.ln2_b, ctx->h_u, true, (int)M, C, c.ln_eps, s)); }
   { TimedLaunch t(ctx, WM_K_FC1, s);
-    WM_TRY(gemm_bf16(ctx->tm_u, w.tm_1, M, 4 * C, C, w.b1, ctx->h_h, 4 * C, wm::EPI_GELU, s)); }
+    WM_TRY(gemm_bf16(ctx->tm_u, w.tm_1, ctx->tmc_h, M, 4 * C, C, w.b1, wm::EPI_GELU, s)); }
   { TimedLaunch t(ctx, WM_K_FC2, s);
-    WM_TRY(gemm_bf16(ctx->tm_h, w.tm_2, M, C, 4 * C, w.b2, x, C, wm::EPI_RESID_F32, s)); }
+    WM_TRY(gemm_bf16(ctx->tm_h, w.tm_2, tm_x, M, C, 4 * C, w.b2, wm::EPI_RESID_F32, s)); }
   return WM_OK;
 }
 
@@ -519,6 +534,20 @@ wm_status wm_rollout_batch(wm_ctx* ctx, float* const* latents, const int* lead_h
   });
 }
 
+wm_status wm_ctx_sizes(wm_ctx* ctx, int batch, size_t* latent_floats, size_t* workspace_bytes) {
+  if (!ctx || batch < 1 || !latent_floats || !workspace_bytes) return fail(WM_ERR_INVALID_ARG, "bad size query");
+  const size_t C = ctx->cfg.C, M = (size_t)batch * ctx->N;
+  *latent_floats = (size_t)ctx->N * C;
+  *workspace_bytes = M * C * 9 * (ctx->cfg.precision == WM_PREC_FP32 ? 4 : 2);
+  return WM_OK;
+}
+
+wm_status wm_ctx_reserve(wm_ctx* ctx, int batch) {
+  if (!ctx || batch < 1) return fail(WM_ERR_INVALID_ARG, "bad reserve arguments");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  return ensure_workspace(ctx, batch);
+}
+
 wm_status wm_timing_begin(wm_ctx* ctx, int max_launches) {
   if (!ctx || max_launches < 1) return fail(WM_ERR_INVALID_ARG, "bad timing arguments");
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
@@ -582,6 +611,7 @@ wm_status wm_device_status(void) {
 
 wm_status wm_selftest_wait_timeout(int timeout_us) {
   if (timeout_us <= 0 || timeout_us > 10000000) return fail(WM_ERR_INVALID_ARG, "timeout must be in (0, 10 s]");
+  WM_TRY(wm::prepare_kernels());
   WM_TRY(wm::launch_wait_selftest(timeout_us, 0));
   return wm_device_status();
 }
@@ -590,6 +620,7 @@ wm_status wm_selftest_wait_timeout(int timeout_us) {
 wm_status wm_op_layernorm(const float* x, const float* gamma, const float* beta, void* out, int out_bf16, int M,
                           int C, float eps, void* stream) {
   if (!x || !gamma || !beta || !out || M < 0 || C <= 0) return fail(WM_ERR_INVALID_ARG, "bad layernorm arguments");
+  WM_TRY(wm::prepare_kernels());
   return wm::launch_layernorm(x, gamma, beta, out, out_bf16 != 0, M, C, eps, (cudaStream_t)stream);
 }
 
@@ -597,19 +628,22 @@ wm_status wm_op_linear(const void* A, const void* W, const float* bias, void* ou
                        int precision, int epilogue, void* stream) {
   if (!A || !W || !out || M < 0 || N <= 0 || K <= 0) return fail(WM_ERR_INVALID_ARG, "bad linear arguments");
   if (epilogue < 0 || epilogue > 3) return fail(WM_ERR_INVALID_ARG, "unknown epilogue");
+  WM_TRY(wm::prepare_kernels());
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == WM_PREC_FP32)
     return wm::launch_sgemm((const float*)A, (const float*)W, bias, (float*)out, M, N, K, epilogue, s);
   if (precision != WM_PREC_BF16) return fail(WM_ERR_INVALID_ARG, "linear precision must be FP32 or BF16");
   if (M == 0) return WM_OK;
-  if (K % 8 != 0) return fail(WM_ERR_INVALID_ARG, "BF16 linear needs K % 8 == 0");
+  if (K % 8 != 0 || N % 8 != 0) return fail(WM_ERR_INVALID_ARG, "BF16 linear needs K % 8 == 0 and N % 8 == 0");
   wm::GemmArgs a;
   a.bn = pick_bn(M, N);
+  const bool out_f32 = epilogue == wm::EPI_RESID_F32 || epilogue == wm::EPI_STORE_F32;
   if (!wm::make_tmap_bf16(&a.tmA, A, (uint64_t)M, (uint64_t)K, 128) ||
-      !wm::make_tmap_bf16(&a.tmB, W, (uint64_t)N, (uint64_t)K, (uint32_t)a.bn))
+      !wm::make_tmap_bf16(&a.tmB, W, (uint64_t)N, (uint64_t)K, (uint32_t)a.bn) ||
+      !wm::make_tmap_out(&a.tmC, out, (uint64_t)M, (uint64_t)N, out_f32))
     return fail(WM_ERR_INVALID_ARG, "cannot build TMA descriptors (pointer alignment or sizes)");
   a.M = M; a.N = N; a.K = K;
-  a.bias = bias; a.out = out; a.ldo = N; a.epi = epilogue;
+  a.bias = bias; a.epi = epilogue;
   return wm::launch_gemm_tc(a, s);
 }
 
@@ -621,6 +655,7 @@ wm_status wm_op_neighborhood_attention(const void* qkv, void* out, int batch, in
   c.precision = precision;
   WM_TRY(validate(&c));
   if (!qkv || !out || batch < 0) return fail(WM_ERR_INVALID_ARG, "bad attention arguments");
+  WM_TRY(wm::prepare_kernels());
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == WM_PREC_FP32)
     return wm::launch_na_f32((const float*)qkv, (float*)out, batch, D, H, W, C, heads, kd, kh, kw, lon_periodic != 0, s);

@@ -32,7 +32,8 @@ struct Cfg {
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGES = (BN >= 256) ? 4 : 6;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;   // + alignment slack
+  static constexpr int EPI_BYTES = NUM_EPI_WARPS * 4096;     // one 32x32 staging tile per epilogue warp
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;   // + alignment slack
   static constexpr int TMEM_COLS = 2 * BN;                   // two accumulators
 };
 
@@ -133,59 +134,52 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 __device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+               "r"(src), "r"(c0), "r"(c1)
+               : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
+  asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   (uint64_t)map),
+               "r"(src), "r"(c0), "r"(c1)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Write this thread's row of a 32 x 32 output chunk into the warp's staging
+// tile in the layout the output tensor map expects: bf16 rows of 64 bytes with
+// the 64-byte swizzle (16-byte unit k of row r at k ^ ((r >> 1) & 3)), or fp32
+// rows of 128 bytes with the 128-byte swizzle (unit k at k ^ (r & 7)). The
+// swizzles keep the 32 row-parallel stores free of bank conflicts.
 template <int EPI>
-__device__ __forceinline__ void epilogue_chunk(const float (&v)[32], int m, int n, int N, int ldo,
-                                               const float* __restrict__ bias, void* __restrict__ out) {
-  float x[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) x[j] = v[j] + ((bias && n + j < N) ? __ldg(bias + n + j) : 0.f);
-  const bool full = (n + 32 <= N);
+__device__ __forceinline__ void stage_row(uint8_t* buf, const float (&x)[32], int r) {
   if constexpr (EPI == EPI_STORE || EPI == EPI_GELU) {
-    if constexpr (EPI == EPI_GELU) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) x[j] = gelu_erf(x[j]);
-    }
-    __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + (size_t)m * ldo + n;
-    if (full && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+    for (int k = 0; k < 4; ++k) {
+      uint32_t w[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint4 u;
-        uint32_t w[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          __nv_bfloat162 p = __floats2bfloat162_rn(x[8 * q + 2 * e], x[8 * q + 2 * e + 1]);
-          w[e] = *reinterpret_cast<uint32_t*>(&p);
-        }
-        u.x = w[0]; u.y = w[1]; u.z = w[2]; u.w = w[3];
-        *reinterpret_cast<uint4*>(o + 8 * q) = u;
+      for (int e = 0; e < 4; ++e) {
+        __nv_bfloat162 p = __floats2bfloat162_rn(x[8 * k + 2 * e], x[8 * k + 2 * e + 1]);
+        w[e] = *reinterpret_cast<uint32_t*>(&p);
       }
-    } else {
-      for (int j = 0; j < 32; ++j)
-        if (n + j < N) o[j] = __float2bfloat16_rn(x[j]);
+      *reinterpret_cast<uint4*>(buf + r * 64 + ((k ^ ((r >> 1) & 3)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   } else {
-    float* o = reinterpret_cast<float*>(out) + (size_t)m * ldo + n;
-    if (full && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        float4 r = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-        if constexpr (EPI == EPI_RESID_F32) {
-          const float4 p = *reinterpret_cast<const float4*>(o + 4 * q);
-          r.x += p.x; r.y += p.y; r.z += p.z; r.w += p.w;
-        }
-        *reinterpret_cast<float4*>(o + 4 * q) = r;
-      }
-    } else {
-      for (int j = 0; j < 32; ++j)
-        if (n + j < N) o[j] = (EPI == EPI_RESID_F32) ? o[j] + x[j] : x[j];
-    }
+    for (int k = 0; k < 8; ++k)
+      *reinterpret_cast<float4*>(buf + r * 128 + ((k ^ (r & 7)) << 4)) =
+          make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
   }
 }
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
-    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
-                        int N, int K, const float* __restrict__ bias, void* __restrict__ out, int ldo,
+    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmC, int M, int N, int K, const float* __restrict__ bias,
                         int* __restrict__ status) {
   using CF = Cfg<BN>;
   constexpr int STAGES = CF::STAGES;
@@ -303,7 +297,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // -------------------------------------------------------- epilogue
     const int quarter = warp & 3;                 // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;             // which half of the BN columns
-    const int row_in_tile = quarter * 32 + lane;
+    uint8_t* ebuf = smem + STAGES * CF::STAGE_BYTES + (warp - 2) * 4096;
+    const uint32_t ebuf32 = smem_u32(ebuf);
     int it = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
       const int buf = it & 1;
@@ -315,18 +310,41 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       tc_fence_after();
       const int m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
-      const int m = m0 + row_in_tile;
+      const int row0 = m0 + quarter * 32;
       const uint32_t tbase = tmem_base + (uint32_t)(buf * BN) + ((uint32_t)(quarter * 32) << 16);
+      const int c_begin = half * (BN / 2), c_end = (half + 1) * (BN / 2);
 #pragma unroll 1
-      for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+      for (int c = c_begin; c < c_end; c += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c, v);
-        if (m < M && n0 + c < N) epilogue_chunk<EPI>(v, m, n0 + c, N, ldo, bias, out);
+        if (c + 32 >= c_end) {
+          // last TMEM read of this tile: hand the accumulator back to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce_bar[buf]);
+        }
+        const int n = n0 + c;
+        if (row0 >= M || n >= N) continue;   // whole chunk outside the output (warp-uniform)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          v[j] += (bias && n + j < N) ? __ldg(bias + n + j) : 0.f;
+          if constexpr (EPI == EPI_GELU) v[j] = gelu_erf(v[j]);
+        }
+        if (lane == 0) bulk_wait_read_all();   // the previous chunk's store has left the staging tile
+        __syncwarp();
+        stage_row<EPI>(ebuf, v, lane);
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          if constexpr (EPI == EPI_RESID_F32)
+            tma_reduce_add_2d(&tmC, ebuf32, n, row0);
+          else
+            tma_store_2d(&tmC, ebuf32, n, row0);
+          bulk_commit();
+        }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acce_bar[buf]);
     }
+    if (lane == 0) bulk_wait_all();
   }
 
   tc_fence_before();
@@ -344,7 +362,7 @@ static wm_status launch_one(const GemmArgs& a, cudaStream_t s) {
   auto kern = gemm_bf16_tc_kernel<BN, EPI>;
   const int tiles = ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  kern<<<grid, THREADS, CF::SMEM, s>>>(a.tmA, a.tmB, a.M, a.N, a.K, a.bias, a.out, a.ldo, device_status_word());
+  kern<<<grid, THREADS, CF::SMEM, s>>>(a.tmA, a.tmB, a.tmC, a.M, a.N, a.K, a.bias, device_status_word());
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
@@ -403,6 +421,21 @@ static EncodeTiledFn encode_fn() {
       fn = reinterpret_cast<EncodeTiledFn>(p);
   }
   return fn;
+}
+
+bool make_tmap_out(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, bool f32) {
+  EncodeTiledFn fn = encode_fn();
+  const uint64_t el = f32 ? 4 : 2;
+  if (!fn || rows == 0 || cols == 0 || (cols * el) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * el};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  f32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {

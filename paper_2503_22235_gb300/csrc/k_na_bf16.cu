@@ -14,6 +14,11 @@
 //   O += P V       P re-packed from the S accumulators, V by ldmatrix.trans
 // The result is normalised once at the end and stored as bf16.
 #include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "wm_internal.cuh"
 
@@ -26,7 +31,7 @@ struct Params {
   int B, D, H, W, C, heads, kd, kh, kw, periodic;
   int WH, WW, NWH, NWW;  // warp patch and warp grid
   int HRmax, WC;          // smem slab rows / columns
-  int span8;              // columns of a warp's key rectangle (multiple of 8)
+  int log2span;           // columns of a warp's key rectangle = 1 << log2span (8, 16 or 32)
   int tiles_w;
   float scale_log2;       // log2(e) / sqrt(dh)
 };
@@ -64,11 +69,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 template <int DH>
-__global__ void __launch_bounds__(256) na_bf16_kernel(const Params p) {
+__global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
   constexpr int DHP = DH + 8;   // padded key row: odd number of 16-byte units -> conflict-free ldmatrix
   constexpr int CH = DH / 8;    // 16-byte chunks per key row
   constexpr int KC = DH / 16;   // k16 steps of Q K^T
   constexpr int ND = DH / 8;    // n8 blocks of P V
+  constexpr int GCH = 8;        // 16-key groups per softmax update
   extern __shared__ __align__(16) __nv_bfloat16 sm[];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -91,29 +97,45 @@ __global__ void __launch_bounds__(256) na_bf16_kernel(const Params p) {
   const int WC = p.WC;
   const int slab = p.HRmax * WC * DHP;  // elements of one K (or V) slab
 
-  // ---- stage one key level (K and V) into buffer `buf`
+  // ---- stage one key level (K and V) into buffer `buf`. Work item = one
+  // 16-byte chunk of one key row; the (kv, row, col, chunk) indices advance
+  // incrementally (no integer division in the loop).
+  const int total_rows = 2 * HR * WC;
   auto load_level = [&](int lev, int buf) {
-    __nv_bfloat16* dstK = sm + (size_t)buf * 2 * slab;
-    const int per_kv = HR * WC * CH;
-    for (int idx = tid; idx < 2 * per_kv; idx += blockDim.x) {
-      const int kv = idx / per_kv;
-      const int rem = idx - kv * per_kv;
-      const int r = rem / (WC * CH);
-      const int c = (rem / CH) % WC;
-      const int ch = rem % CH;
+    __nv_bfloat16* sbuf = sm + (size_t)buf * 2 * slab;
+    const __nv_bfloat16* lbase = base + (long)lev * H * W * C3 + (1L * p.C) + head * DH;
+    const int nthreads = blockDim.x;
+    const int DROW = nthreads / CH, DCH = nthreads % CH;
+    int ch = tid % CH, row = tid / CH;
+    int c = row % WC, r = (row / WC) % HR, kv = row / (WC * HR);
+    while (row < total_rows) {
       int lon = ws0 + c;
       bool ok = true;
       if (p.periodic) {
-        lon %= W;
-        if (lon < 0) lon += W;
+        if (lon < 0 || lon >= W) lon = ((lon % W) + W) % W;
       } else if (lon >= W) {
         ok = false;
         lon = 0;
       }
-      const long tok = ((long)lev * H + (hs0 + r)) * W + lon;
-      const __nv_bfloat16* src = base + tok * C3 + (1 + kv) * p.C + head * DH + ch * 8;
-      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(dstK + (size_t)kv * slab + (size_t)(r * WC + c) * DHP + ch * 8);
+      const __nv_bfloat16* src = lbase + ((long)(hs0 + r) * W + lon) * C3 + kv * p.C + ch * 8;
+      const uint32_t dst =
+          (uint32_t)__cvta_generic_to_shared(sbuf + (size_t)kv * slab + (size_t)(r * WC + c) * DHP + ch * 8);
       cp_async16(dst, ok ? (const void*)src : (const void*)p.qkv, ok ? 16 : 0);
+      ch += DCH;
+      int adv = DROW;
+      if (ch >= CH) {
+        ch -= CH;
+        ++adv;
+      }
+      row += adv;
+      c += adv;
+      while (c >= WC) {
+        c -= WC;
+        if (++r == HR) {
+          r = 0;
+          ++kv;
+        }
+      }
     }
   };
 
@@ -136,9 +158,18 @@ __global__ void __launch_bounds__(256) na_bf16_kernel(const Params p) {
   const int wr0 = clampi(min(wh0, H - 1) - rh, 0, H - p.kh) - hs0;
   const int wr1 = clampi(min(wh0 + p.WH - 1, H - 1) - rh, 0, H - p.kh) + p.kh - hs0;
   const int wc0 = p.periodic ? (ww0 - w0) : (clampi(min(ww0, W - 1) - rw, 0, W - p.kw) - ws0);
-  const int span8 = p.span8;
-  const int nkeys = (wr1 - wr0) * span8;
+  const int ls = p.log2span, smask = (1 << ls) - 1;
+  const int nkeys = (wr1 - wr0) << ls;
   const int ngroups = (nkeys + 15) / 16;
+  // window of each of this thread's two queries inside the warp's key
+  // rectangle: rows [rlo, rlo + kh), columns = set bits of colmask
+  int rlo[2];
+  uint32_t colmask[2];
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr) {
+    rlo[rr] = qsr[rr] - wr0;
+    colmask[rr] = (0xFFFFFFFFu >> (32 - p.kw)) << max(qsc[rr] - wc0, 0);
+  }
 
   // Q fragments (A operand), rows g and g+8 of the warp's 16 queries
   uint32_t qa[KC][4];
@@ -174,76 +205,89 @@ __global__ void __launch_bounds__(256) na_bf16_kernel(const Params p) {
     const uint32_t sK32 = (uint32_t)__cvta_generic_to_shared(sK);
     const uint32_t sV32 = (uint32_t)__cvta_generic_to_shared(sV);
     if (warp_live) {
-      for (int grp = 0; grp < ngroups; ++grp) {
-        // ---- S = Q K^T for 16 keys
-        // ldmatrix row address of this lane: key j = (mi>>1)*8 + (lane&7) for K, (mi&1)*8 + (lane&7) for V
+      // Up to GCH groups of 16 keys are scored before one online-softmax
+      // update: their MMAs, masks and exponentials are independent, which
+      // keeps the tensor and MUFU pipes busy with only a few warps per SM.
+      for (int g0 = 0; g0 < ngroups; g0 += GCH) {
         const int mi = lane >> 3;
-        int jk = grp * 16 + (mi >> 1) * 8 + (lane & 7);
-        int jv = grp * 16 + (mi & 1) * 8 + (lane & 7);
-        if (jk >= nkeys) jk = 0;
-        if (jv >= nkeys) jv = 0;
-        const int krow = (wr0 + jk / span8) * WC + wc0 + jk % span8;
-        const int vrow = (wr0 + jv / span8) * WC + wc0 + jv % span8;
-        float s[2][4];
+        float s[GCH][2][4];
 #pragma unroll
-        for (int nb = 0; nb < 2; ++nb) s[nb][0] = s[nb][1] = s[nb][2] = s[nb][3] = 0.f;
+        for (int gi = 0; gi < GCH; ++gi) {
 #pragma unroll
-        for (int kc = 0; kc < KC; ++kc) {
-          uint32_t b0, b1, b2, b3;
-          ldsm_x4(sK32 + (uint32_t)((krow * DHP + kc * 16 + (mi & 1) * 8) * 2), b0, b1, b2, b3);
-          mma_bf16(s[0], qa[kc][0], qa[kc][1], qa[kc][2], qa[kc][3], b0, b1);
-          mma_bf16(s[1], qa[kc][0], qa[kc][1], qa[kc][2], qa[kc][3], b2, b3);
-        }
-        // ---- mask + scale
+          for (int nb = 0; nb < 2; ++nb) s[gi][nb][0] = s[gi][nb][1] = s[gi][nb][2] = s[gi][nb][3] = 0.f;
+          if (g0 + gi < ngroups) {
+            int jk = (g0 + gi) * 16 + (mi >> 1) * 8 + (lane & 7);
+            if (jk >= nkeys) jk = 0;
+            const int krow = (wr0 + (jk >> ls)) * WC + wc0 + (jk & smask);
 #pragma unroll
-        for (int nb = 0; nb < 2; ++nb)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int j = grp * 16 + nb * 8 + 2 * t4 + (e & 1);
-            const int rr = e >> 1;
-            const int kr = wr0 + j / span8, kcn = wc0 + j % span8;
-            const bool ok = (j < nkeys) && (kr >= qsr[rr]) && (kr < qsr[rr] + p.kh) && (kcn >= qsc[rr]) &&
-                            (kcn < qsc[rr] + p.kw);
-            s[nb][e] = ok ? s[nb][e] * p.scale_log2 : -INFINITY;
+            for (int kc = 0; kc < KC; ++kc) {
+              uint32_t b0, b1, b2, b3;
+              ldsm_x4(sK32 + (uint32_t)((krow * DHP + kc * 16 + (mi & 1) * 8) * 2), b0, b1, b2, b3);
+              mma_bf16(s[gi][0], qa[kc][0], qa[kc][1], qa[kc][2], qa[kc][3], b0, b1);
+              mma_bf16(s[gi][1], qa[kc][0], qa[kc][1], qa[kc][2], qa[kc][3], b2, b3);
+            }
           }
-        // ---- online softmax (rows g and g+8)
-        float pr[2][4];
+        }
+        // mask + scale + chunk row max
+        float mx[2] = {-INFINITY, -INFINITY};
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-          float mx = fmaxf(fmaxf(s[0][2 * rr], s[0][2 * rr + 1]), fmaxf(s[1][2 * rr], s[1][2 * rr + 1]));
-          mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-          mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-          const float mnew = fmaxf(mrow[rr], mx);
-          const float mref = (mnew == -INFINITY) ? 0.f : mnew;
-          const float alpha = exp2f(mrow[rr] - mref);
-          mrow[rr] = mnew;
-          float ls = 0.f;
+        for (int gi = 0; gi < GCH; ++gi)
 #pragma unroll
           for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const float v = exp2f(s[nb][2 * rr + e] - mref);
-              pr[nb][2 * rr + e] = v;
-              ls += v;
+            for (int e = 0; e < 4; ++e) {
+              const int j = (g0 + gi) * 16 + nb * 8 + 2 * t4 + (e & 1);
+              const int rr = e >> 1;
+              const bool ok = (g0 + gi < ngroups) && (j < nkeys) &&
+                              ((unsigned)((j >> ls) - rlo[rr]) < (unsigned)p.kh) &&
+                              ((colmask[rr] >> (j & smask)) & 1u);
+              const float v = ok ? s[gi][nb][e] * p.scale_log2 : -INFINITY;
+              s[gi][nb][e] = v;
+              mx[rr] = fmaxf(mx[rr], v);
             }
-          lrow[rr] = lrow[rr] * alpha + ls;
+        float mref[2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+          mx[rr] = fmaxf(mx[rr], __shfl_xor_sync(0xffffffffu, mx[rr], 1));
+          mx[rr] = fmaxf(mx[rr], __shfl_xor_sync(0xffffffffu, mx[rr], 2));
+          const float mnew = fmaxf(mrow[rr], mx[rr]);
+          mref[rr] = (mnew == -INFINITY) ? 0.f : mnew;
+          const float alpha = exp2f(mrow[rr] - mref[rr]);
+          mrow[rr] = mnew;
+          lrow[rr] *= alpha;
 #pragma unroll
           for (int nd = 0; nd < ND; ++nd) {
             o[nd][2 * rr] *= alpha;
             o[nd][2 * rr + 1] *= alpha;
           }
         }
-        // ---- O += P V
-        const uint32_t pa0 = pack_bf16(pr[0][0], pr[0][1]);
-        const uint32_t pa1 = pack_bf16(pr[0][2], pr[0][3]);
-        const uint32_t pa2 = pack_bf16(pr[1][0], pr[1][1]);
-        const uint32_t pa3 = pack_bf16(pr[1][2], pr[1][3]);
+        // P = exp2(S - m), row sums (per thread; quad-reduced at the end), O += P V
 #pragma unroll
-        for (int nd = 0; nd < ND; nd += 2) {
-          uint32_t b0, b1, b2, b3;
-          ldsm_x4_t(sV32 + (uint32_t)((vrow * DHP + nd * 8 + (mi >> 1) * 8) * 2), b0, b1, b2, b3);
-          mma_bf16(o[nd], pa0, pa1, pa2, pa3, b0, b1);
-          mma_bf16(o[nd + 1], pa0, pa1, pa2, pa3, b2, b3);
+        for (int gi = 0; gi < GCH; ++gi) {
+          if (g0 + gi >= ngroups) break;
+          float pr[2][4];
+#pragma unroll
+          for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float v = exp2f(s[gi][nb][e] - mref[e >> 1]);
+              pr[nb][e] = v;
+              lrow[e >> 1] += v;
+            }
+          const uint32_t pa0 = pack_bf16(pr[0][0], pr[0][1]);
+          const uint32_t pa1 = pack_bf16(pr[0][2], pr[0][3]);
+          const uint32_t pa2 = pack_bf16(pr[1][0], pr[1][1]);
+          const uint32_t pa3 = pack_bf16(pr[1][2], pr[1][3]);
+          int jv = (g0 + gi) * 16 + (mi & 1) * 8 + (lane & 7);
+          if (jv >= nkeys) jv = 0;
+          const int vrow = (wr0 + (jv >> ls)) * WC + wc0 + (jv & smask);
+#pragma unroll
+          for (int nd = 0; nd < ND; nd += 2) {
+            uint32_t b0, b1, b2, b3;
+            ldsm_x4_t(sV32 + (uint32_t)((vrow * DHP + nd * 8 + (mi >> 1) * 8) * 2), b0, b1, b2, b3);
+            mma_bf16(o[nd], pa0, pa1, pa2, pa3, b0, b1);
+            mma_bf16(o[nd + 1], pa0, pa1, pa2, pa3, b2, b3);
+          }
         }
       }
     }
@@ -277,68 +321,190 @@ wm_status prepare_na_bf16() {
   return WM_OK;
 }
 
-static int round8(int v) { return (v + 7) / 8 * 8; }
+// smallest power of two >= max(8, v)
+static int pow2span(int v) {
+  int s = 8;
+  while (s < v) s <<= 1;
+  return s;
+}
 
-wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C, int heads,
-                         int kd, int kh, int kw, bool periodic, cudaStream_t s) {
-  if (B <= 0) return WM_OK;
-  const int dh = C / heads;
+namespace {
+
+struct NaPlan {
+  int NWH, NWW;  // warp grid of a CTA (query tile = NWH*WH x NWW*WW)
+};
+
+using NaKey = std::array<int, 11>;
+std::mutex g_na_mu;
+std::map<NaKey, NaPlan> g_na_plans;  // autotuned plans
+
+NaKey na_key(int B, int D, int H, int W, int C, int heads, int kd, int kh, int kw, bool per) {
+  return NaKey{B, D, H, W, C, heads, kd, kh, kw, per ? 1 : 0, 0};
+}
+
+// Warp patch (WH x WW queries) with the fewest issued keys per query per
+// level; fixed by the window alone, so a query's arithmetic (its key
+// rectangle and the order it is walked in) never depends on the CTA plan.
+bool warp_patch(int kh, int kw, int* WH, int* WW, int* span) {
+  const int cand[5][2] = {{1, 16}, {2, 8}, {4, 4}, {8, 2}, {16, 1}};
+  int best = -1, best_cost = 1 << 30;
+  for (int i = 0; i < 5; ++i) {
+    if (cand[i][1] + kw - 1 > 32) continue;
+    const int cost = (cand[i][0] + kh - 1) * pow2span(cand[i][1] + kw - 1);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = i;
+    }
+  }
+  if (best < 0) return false;
+  *WH = cand[best][0];
+  *WW = cand[best][1];
+  *span = pow2span(*WW + kw - 1);
+  return true;
+}
+
+size_t plan_smem(const NaPlan& pl, int WH, int WW, int span, int kh, int H, int dh) {
+  const int hr = std::min(pl.NWH * WH + kh - 1, H);
+  const int wc = (pl.NWW - 1) * WW + span;
+  return (size_t)2 * 2 * hr * wc * (dh + 8) * 2;
+}
+
+std::vector<NaPlan> na_candidates(int WH, int WW, int span, int kh, int H, int dh) {
+  std::vector<NaPlan> out;
+  for (int nw : {8, 12})
+    for (int nwh = 1; nwh <= nw; ++nwh) {
+      if (nw % nwh) continue;
+      NaPlan pl{nwh, nw / nwh};
+      if (plan_smem(pl, WH, WW, span, kh, H, dh) <= 200 * 1024) out.push_back(pl);
+    }
+  return out;
+}
+
+// Heuristic when no tuned plan exists: fewest staged keys per query times
+// tile waste, over the candidates with the most warps that still give every
+// SM a CTA.
+NaPlan na_heuristic(int B, int D, int H, int W, int heads, int WH, int WW, int span, int kh, int dh) {
+  NaPlan best{0, 0};
+  double best_score = 1e30;
+  for (const NaPlan& pl : na_candidates(WH, WW, span, kh, H, dh)) {
+    const int TH = pl.NWH * WH, TW = pl.NWW * WW;
+    const int th = (H + TH - 1) / TH, tw = (W + TW - 1) / TW;
+    const int hr = std::min(TH + kh - 1, H), wc = (pl.NWW - 1) * WW + span;
+    const long ctas = (long)th * tw * D * B * heads;
+    double score = (double)hr * wc / (TH * TW) * ((double)th * TH / H) * ((double)tw * TW / W);
+    if (ctas < num_sms()) score *= (double)num_sms() / ctas;   // idle SMs
+    score /= std::sqrt((double)(pl.NWH * pl.NWW) / 8.0);      // more warps hide more latency
+    if (score < best_score) {
+      best_score = score;
+      best = pl;
+    }
+  }
+  return best;
+}
+
+template <int DH>
+wm_status launch_plan(const NaPlan& pl, na::Params p, int WH, int WW, int span, cudaStream_t s) {
+  p.WH = WH;
+  p.WW = WW;
+  p.log2span = 0;
+  while ((1 << p.log2span) < span) ++p.log2span;
+  p.NWH = pl.NWH;
+  p.NWW = pl.NWW;
+  p.HRmax = std::min(p.NWH * p.WH + p.kh - 1, p.H);
+  p.WC = (p.NWW - 1) * p.WW + span;
+  const int TH = p.NWH * p.WH, TW = p.NWW * p.WW;
+  const int tiles_h = (p.H + TH - 1) / TH;
+  p.tiles_w = (p.W + TW - 1) / TW;
+  p.scale_log2 = 1.4426950408889634f / sqrtf((float)DH);
+  if ((long)p.B * p.heads > 65535 || p.D > 65535) return fail(WM_ERR_INVALID_ARG, "batch*heads or D too large");
+  dim3 grid(tiles_h * p.tiles_w, p.D, p.B * p.heads), block(32 * p.NWH * p.NWW);
+  const int smem = (int)plan_smem(pl, WH, WW, span, p.kh, p.H, DH);
+  na::na_bf16_kernel<DH><<<grid, block, smem, s>>>(p);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+wm_status launch_with(const NaPlan& pl, const na::Params& p, int dh, int WH, int WW, int span, cudaStream_t s) {
+  switch (dh) {
+    case 16: return launch_plan<16>(pl, p, WH, WW, span, s);
+    case 32: return launch_plan<32>(pl, p, WH, WW, span, s);
+    case 48: return launch_plan<48>(pl, p, WH, WW, span, s);
+    case 64: return launch_plan<64>(pl, p, WH, WW, span, s);
+    default: return fail(WM_ERR_INVALID_ARG, "BF16 attention needs head dim 16, 32, 48 or 64");
+  }
+}
+
+na::Params make_params(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C, int heads,
+                       int kd, int kh, int kw, bool periodic) {
   na::Params p{};
   p.qkv = qkv;
   p.out = out;
   p.B = B; p.D = D; p.H = H; p.W = W; p.C = C; p.heads = heads;
   p.kd = kd; p.kh = kh; p.kw = kw; p.periodic = periodic ? 1 : 0;
-  // warp patch: fewest keys per query per level
-  const int cand[5][2] = {{1, 16}, {2, 8}, {4, 4}, {8, 2}, {16, 1}};
-  int best = 0, best_cost = 1 << 30;
-  for (int i = 0; i < 5; ++i) {
-    const int cost = (cand[i][0] + kh - 1) * round8(cand[i][1] + kw - 1);
-    if (cost < best_cost) { best_cost = cost; best = i; }
+  return p;
+}
+
+}  // namespace
+
+wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C, int heads,
+                         int kd, int kh, int kw, bool periodic, cudaStream_t s) {
+  if (B <= 0) return WM_OK;
+  const int dh = C / heads;
+  int WH, WW, span;
+  if (!warp_patch(kh, kw, &WH, &WW, &span))
+    return fail(WM_ERR_INVALID_ARG, "longitude window too wide for the BF16 attention kernel");
+  NaPlan pl{0, 0};
+  {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    auto it = g_na_plans.find(na_key(B, D, H, W, C, heads, kd, kh, kw, periodic));
+    if (it != g_na_plans.end()) pl = it->second;
   }
-  p.WH = cand[best][0];
-  p.WW = cand[best][1];
-  p.span8 = round8(p.WW + kw - 1);
-  const int DHP = dh + 8;
-  // warp grid (8 warps): least staged keys per query within the shared-memory budget
-  int bestg = -1;
-  double best_ratio = 1e30;
-  size_t best_smem = 0;
-  for (int nwh = 1; nwh <= 8; nwh *= 2) {
-    const int nww = 8 / nwh;
-    const int TH = nwh * p.WH;
-    const int hr = std::min(TH + kh - 1, H);
-    const int wc = (nww - 1) * p.WW + p.span8;
-    const size_t smem = (size_t)2 * 2 * hr * wc * DHP * 2;
-    if (smem > 200 * 1024) continue;
-    const double ratio = (double)hr * wc / (TH * nww * p.WW);
-    if (ratio < best_ratio) { best_ratio = ratio; bestg = nwh; best_smem = smem; }
+  if (!pl.NWH) pl = na_heuristic(B, D, H, W, heads, WH, WW, span, kh, dh);
+  if (!pl.NWH) return fail(WM_ERR_INVALID_ARG, "attention window too large for the BF16 attention kernel");
+  return launch_with(pl, make_params(qkv, out, B, D, H, W, C, heads, kd, kh, kw, periodic), dh, WH, WW, span, s);
+}
+
+// Time every candidate CTA plan for this shape (1 warm-up + 3 timed launches
+// each, CUDA events on `s`) and keep the fastest for later launches. The
+// outputs are written to `out`; results do not depend on the plan.
+wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
+                           int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s, double* best_ms) {
+  const int dh = C / heads;
+  int WH, WW, span;
+  if (!warp_patch(kh, kw, &WH, &WW, &span)) return fail(WM_ERR_INVALID_ARG, "window too wide");
+  const na::Params p = make_params(qkv, out, B, D, H, W, C, heads, kd, kh, kw, periodic);
+  cudaEvent_t e0, e1;
+  WM_CUDA(cudaEventCreate(&e0));
+  WM_CUDA(cudaEventCreate(&e1));
+  NaPlan best{0, 0};
+  float best_t = 1e30f;
+  wm_status st = WM_OK;
+  for (const NaPlan& pl : na_candidates(WH, WW, span, kh, H, dh)) {
+    st = launch_with(pl, p, dh, WH, WW, span, s);
+    if (st != WM_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3 && st == WM_OK; ++r) st = launch_with(pl, p, dh, WH, WW, span, s);
+    cudaEventRecord(e1, s);
+    if (st != WM_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = fail(WM_ERR_CUDA, "autotune synchronisation failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_t) {
+      best_t = ms;
+      best = pl;
+    }
   }
-  if (bestg < 0) return fail(WM_ERR_INVALID_ARG, "attention window too large for the BF16 attention kernel");
-  p.NWH = bestg;
-  p.NWW = 8 / bestg;
-  p.HRmax = std::min(p.NWH * p.WH + kh - 1, H);
-  p.WC = (p.NWW - 1) * p.WW + p.span8;
-  const int TH = p.NWH * p.WH, TW = p.NWW * p.WW;
-  const int tiles_h = (H + TH - 1) / TH;
-  p.tiles_w = (W + TW - 1) / TW;
-  p.scale_log2 = 1.4426950408889634f / sqrtf((float)dh);
-  if ((long)B * heads > 65535 || D > 65535) return fail(WM_ERR_INVALID_ARG, "batch*heads or D too large");
-  dim3 grid(tiles_h * p.tiles_w, D, B * heads), block(256);
-  const int smem = (int)best_smem;
-#define WM_NA_CASE(DHV)                                \
-  case DHV:                                           \
-    na::na_bf16_kernel<DHV><<<grid, block, smem, s>>>(p); \
-    break;
-  switch (dh) {
-    WM_NA_CASE(16)
-    WM_NA_CASE(32)
-    WM_NA_CASE(48)
-    WM_NA_CASE(64)
-    default:
-      return fail(WM_ERR_INVALID_ARG, "BF16 attention needs head dim 16, 32, 48 or 64");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != WM_OK) return st;
+  if (best.NWH) {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    g_na_plans[na_key(B, D, H, W, C, heads, kd, kh, kw, periodic)] = best;
   }
-#undef WM_NA_CASE
-  WM_CUDA(cudaGetLastError());
+  if (best_ms) *best_ms = best_t / 3.0;
   return WM_OK;
 }
 

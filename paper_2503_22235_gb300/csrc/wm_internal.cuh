@@ -58,13 +58,16 @@ wm_status launch_na_f32(const float* qkv, float* out, int B, int D, int H, int W
 // box = box_rows x 64 columns, 128-byte swizzle.
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows);
 
+// TMA descriptor of the GEMM output [rows, cols] (bf16 or fp32, row major),
+// box 32 x 32, 64-byte (bf16) / 128-byte (fp32) swizzle.
+bool make_tmap_out(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, bool f32);
+
 struct GemmArgs {
   CUtensorMap tmA;     // A [M, K] bf16, box 128 x 64
   CUtensorMap tmB;     // W [N, K] bf16, box BN x 64
+  CUtensorMap tmC;     // output [M, N]: bf16 for EPI_STORE / EPI_GELU, fp32 otherwise (make_tmap_out)
   int M, N, K;
   const float* bias;
-  void* out;
-  int ldo;
   int epi;
   int bn;              // 128 or 256 (tmB box rows must match)
 };
@@ -72,6 +75,10 @@ wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
 
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
                          int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s);
+// Times the candidate CTA plans of the attention kernel for this exact shape
+// and keeps the fastest for later launch_na_bf16 calls (writes `out`).
+wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
+                           int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s, double* best_ms);
 
 // ---------------------------------------------------------------- misc ----
 wm_status launch_f32_to_bf16(const float* in, __nv_bfloat16* out, size_t n, cudaStream_t s);

@@ -1,0 +1,107 @@
+"""Serving loop: continuous batching with HBM-budget admission.
+
+Requests with uneven lead times arrive while others run, share batched
+processor steps, and each result must equal the same forecast computed alone
+(wm_latent_rollout on one latent) bit for bit: the kernels are row
+independent and the schedule per request does not depend on the mix.
+"""
+import dataclasses
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2503_22235_gb300 as wm
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = dataclasses.replace(synth.SMALL, blocks_p6=2, blocks_p1=1)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2503_22235_gb300 import build as wm_build
+    wm_build.build()
+    p6, p1 = synth.processor_weights(SHAPE, seed=0, stress=True)
+    c = wm.wm_create_from_host(wm.make_config(SHAPE, wm.WM_PREC_BF16), synth.pack_weights(p6, p1))
+    yield c
+    wm.wm_destroy(c)
+
+
+def _budget(ctx, slots, max_batch):
+    lat, ws = wm.wm_ctx_sizes(ctx, max_batch)
+    return ws + (max_batch + slots) * lat * 4
+
+
+def _alone(ctx, x, lead):
+    d = torch.from_numpy(x).cuda()
+    wm.wm_latent_rollout(ctx, d, lead)
+    torch.cuda.synchronize()
+    return d.cpu().numpy()
+
+
+def test_server_results_equal_alone_and_in_the_mix(ctx):
+    leads = [13, 1, 0, 7, 6, 24, 2, 19, 12, 5]
+    xs = [synth.latent(SHAPE, 1, seed=100 + i) for i in range(len(leads))]
+    srv = wm.wm_server_start(ctx, _budget(ctx, slots=4, max_batch=3), max_batch=3)
+    try:
+        ids = []
+        for i, (x, t) in enumerate(zip(xs, leads)):
+            ids.append(wm.wm_server_submit(srv, x, t))
+            if i % 3 == 2:
+                time.sleep(0.005)        # later requests arrive while earlier ones run
+        outs = {}
+        deadline = time.time() + 120
+        while len(outs) < len(ids) and time.time() < deadline:
+            for rid in ids:
+                if rid in outs:
+                    continue
+                buf = np.empty_like(xs[0])
+                done, lat_ms = wm.wm_server_poll(srv, rid, buf)
+                if done:
+                    assert lat_ms >= 0
+                    outs[rid] = buf
+            time.sleep(0.001)
+        assert len(outs) == len(ids)
+        st = wm.wm_server_stats(srv)
+        assert st["completed"] == len(ids)
+        assert st["slots"] == 4 and st["max_active"] <= 4
+        assert st["p50_ms"] <= st["p99_ms"]
+    finally:
+        wm.wm_server_stop(srv)
+    for rid, x, t in zip(ids, xs, leads):
+        ref = _alone(ctx, x, t)
+        assert np.array_equal(outs[rid], ref), t
+    with pytest.raises(wm.WmError):
+        wm.wm_server_poll(0, 1)  # a NULL server handle is rejected
+
+
+def test_server_budget_and_arguments(ctx):
+    with pytest.raises(wm.WmError) as e:
+        wm.wm_server_start(ctx, 1024, max_batch=2)
+    assert e.value.status == wm.WM_ERR_INVALID_ARG
+    srv = wm.wm_server_start(ctx, _budget(ctx, slots=1, max_batch=1), max_batch=1)
+    try:
+        x = synth.latent(SHAPE, 1, seed=7)
+        with pytest.raises(wm.WmError):
+            wm.wm_server_submit(srv, x, -1)
+        with pytest.raises(wm.WmError) as e:
+            wm.wm_server_poll(srv, 12345)
+        assert e.value.status == wm.WM_ERR_NOT_FOUND
+        # one slot: requests queue and are admitted one after the other
+        ids = [wm.wm_server_submit(srv, x, t) for t in (6, 1, 7)]
+        got = {}
+        deadline = time.time() + 60
+        while len(got) < 3 and time.time() < deadline:
+            for rid in ids:
+                if rid not in got:
+                    done, _ = wm.wm_server_poll(srv, rid, None)
+                    if done:
+                        got[rid] = True
+            time.sleep(0.001)
+        assert len(got) == 3
+        assert wm.wm_server_stats(srv)["max_active"] == 1
+    finally:
+        wm.wm_server_stop(srv)

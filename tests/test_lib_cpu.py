@@ -63,3 +63,24 @@ def test_null_arguments_are_rejected():
     assert L.wm_processor_step(None, None, 1, 0, None) == wm.WM_ERR_INVALID_ARG
     assert L.wm_destroy(None) == wm.WM_OK
     assert L.wm_rollout_batch(None, None, None, 0, None) == wm.WM_ERR_INVALID_ARG
+
+
+def _header_arity():
+    import re
+    with open(wm.HEADER if hasattr(wm, "HEADER") else wm._binding.HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(wm_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header_arity():
+    from paper_2503_22235_gb300 import _binding
+    arity = _header_arity()
+    assert arity, "no declarations parsed"
+    for name, (_, args) in _binding._SIGS.items():
+        assert name in arity, name
+        assert len(args) == arity[name], (name, len(args), arity[name])

@@ -343,3 +343,33 @@ def test_rel_l2():
     a = np.array([3.0, 4.0])
     assert orc.rel_l2(a, a) == 0.0
     assert math.isclose(orc.rel_l2(np.array([3.0, 5.0]), a), 1.0 / 5.0)
+
+
+# ------------------------------------------------------------- FP8 codec ---
+
+def test_e4m3_decode_matches_torch_on_all_codes():
+    ref = torch.arange(256, dtype=torch.uint8).view(torch.float8_e4m3fn).double().numpy()
+    got = np.array([orc.e4m3_decode(c) for c in range(256)])
+    both_nan = np.isnan(ref) & np.isnan(got)
+    assert np.all(both_nan | (ref == got))
+    assert orc.e4m3_decode(0x7E) == 448.0 and orc.e4m3_decode(0x38) == 1.0
+    assert orc.e4m3_decode(0x08) == 2.0 ** -6 and orc.e4m3_decode(0x01) == 2.0 ** -9
+    assert np.isnan(orc.e4m3_decode(0x7F)) and np.isnan(orc.e4m3_decode(0xFF))
+
+
+def test_e4m3_round_trips_every_finite_code_and_rounds_ties_to_even():
+    finite = [orc.e4m3_decode(c) for c in range(256) if not np.isnan(orc.e4m3_decode(c))]
+    assert np.array_equal(orc.e4m3_round(finite), np.array(finite))
+    # ties: 1.0625 between 1.0 (even code) and 1.125; 1.1875 between 1.125 and 1.25 (even)
+    assert orc.e4m3_round(1.0625) == 1.0 and orc.e4m3_round(1.1875) == 1.25
+    assert orc.e4m3_round(-1.1875) == -1.25
+    # saturation (OCP "satfinite"): beyond 448 clamps to 448
+    assert orc.e4m3_round(1e6) == 448.0 and orc.e4m3_round(-500.0) == -448.0
+
+
+def test_e4m3_round_matches_torch_in_range():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(20000) * 30, rng.uniform(-448, 448, 20000),
+                        rng.standard_normal(5000) * 1e-3])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.float8_e4m3fn).double().numpy()
+    assert np.array_equal(orc.e4m3_round(x.astype(np.float32)), ref)
