@@ -63,12 +63,18 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
+// 2^x by the MUFU.EX2 hardware instruction (flush-to-zero; 2^-inf = 0).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&p);
 }
 
-template <int DH>
+template <int DH, int LS>   // LS = log2 of the key-rectangle width (3, 4 or 5)
 __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
   constexpr int DHP = DH + 8;   // padded key row: odd number of 16-byte units -> conflict-free ldmatrix
   constexpr int CH = DH / 8;    // 16-byte chunks per key row
@@ -97,18 +103,17 @@ __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
   const int WC = p.WC;
   const int slab = p.HRmax * WC * DHP;  // elements of one K (or V) slab
 
-  // ---- stage one key level (K and V) into buffer `buf`. Work item = one
-  // 16-byte chunk of one key row; the (kv, row, col, chunk) indices advance
-  // incrementally (no integer division in the loop).
-  const int total_rows = 2 * HR * WC;
+  // ---- stage one key level (K and V) into buffer `buf`. Each thread owns
+  // fixed (K or V, slab column, 16-byte chunk) items and walks the slab rows,
+  // so the per-copy work is two pointer increments.
+  const int items = 2 * WC * CH;
   auto load_level = [&](int lev, int buf) {
     __nv_bfloat16* sbuf = sm + (size_t)buf * 2 * slab;
-    const __nv_bfloat16* lbase = base + (long)lev * H * W * C3 + (1L * p.C) + head * DH;
-    const int nthreads = blockDim.x;
-    const int DROW = nthreads / CH, DCH = nthreads % CH;
-    int ch = tid % CH, row = tid / CH;
-    int c = row % WC, r = (row / WC) % HR, kv = row / (WC * HR);
-    while (row < total_rows) {
+    const __nv_bfloat16* lbase = base + (long)lev * H * W * C3 + (long)hs0 * W * C3 + (1L * p.C) + head * DH;
+    for (int it = tid; it < items; it += blockDim.x) {
+      const int kv = it / (WC * CH);
+      const int rem = it - kv * (WC * CH);
+      const int c = rem / CH, ch = rem - c * CH;
       int lon = ws0 + c;
       bool ok = true;
       if (p.periodic) {
@@ -117,24 +122,14 @@ __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
         ok = false;
         lon = 0;
       }
-      const __nv_bfloat16* src = lbase + ((long)(hs0 + r) * W + lon) * C3 + kv * p.C + ch * 8;
-      const uint32_t dst =
-          (uint32_t)__cvta_generic_to_shared(sbuf + (size_t)kv * slab + (size_t)(r * WC + c) * DHP + ch * 8);
-      cp_async16(dst, ok ? (const void*)src : (const void*)p.qkv, ok ? 16 : 0);
-      ch += DCH;
-      int adv = DROW;
-      if (ch >= CH) {
-        ch -= CH;
-        ++adv;
-      }
-      row += adv;
-      c += adv;
-      while (c >= WC) {
-        c -= WC;
-        if (++r == HR) {
-          r = 0;
-          ++kv;
-        }
+      const __nv_bfloat16* src = lbase + (long)lon * C3 + kv * p.C + ch * 8;
+      uint32_t dst = (uint32_t)__cvta_generic_to_shared(sbuf + (size_t)kv * slab + (size_t)c * DHP + ch * 8);
+      const long sstep = (long)W * C3;
+      const uint32_t dstep = (uint32_t)(WC * DHP * 2);
+      for (int r = 0; r < HR; ++r) {
+        cp_async16(dst, ok ? (const void*)src : (const void*)p.qkv, ok ? 16 : 0);
+        src += sstep;
+        dst += dstep;
       }
     }
   };
@@ -158,7 +153,7 @@ __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
   const int wr0 = clampi(min(wh0, H - 1) - rh, 0, H - p.kh) - hs0;
   const int wr1 = clampi(min(wh0 + p.WH - 1, H - 1) - rh, 0, H - p.kh) + p.kh - hs0;
   const int wc0 = p.periodic ? (ww0 - w0) : (clampi(min(ww0, W - 1) - rw, 0, W - p.kw) - ws0);
-  const int ls = p.log2span, smask = (1 << ls) - 1;
+  constexpr int ls = LS, smask = (1 << LS) - 1;
   const int nkeys = (wr1 - wr0) << ls;
   const int ngroups = (nkeys + 15) / 16;
   // window of each of this thread's two queries inside the warp's key
@@ -170,6 +165,19 @@ __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
     rlo[rr] = qsr[rr] - wr0;
     colmask[rr] = (0xFFFFFFFFu >> (32 - p.kw)) << max(qsc[rr] - wc0, 0);
   }
+  // column bias of accumulator entry (group parity, n8 block, query, e & 1)
+  float cbias[2][2][2][2];
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+    for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int col = (hf * 16 + nb * 8 + 2 * t4 + e) & smask;
+          cbias[hf][nb][rr][e] = ((colmask[rr] >> col) & 1u) ? 0.f : -INFINITY;
+        }
 
   // Q fragments (A operand), rows g and g+8 of the warp's 16 queries
   uint32_t qa[KC][4];
@@ -228,23 +236,40 @@ __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
             }
           }
         }
-        // mask + scale + chunk row max
-        float mx[2] = {-INFINITY, -INFINITY};
+        // mask + scale + chunk row max. Key j sits at rectangle row j >> LS and
+        // column j & smask. The column of each accumulator entry depends on
+        // the group only through (g & 1) for 32-wide rectangles, so the column
+        // test is a precomputed additive bias (0 or -inf); the row test is one
+        // unsigned compare per n8 block.
+        float gmx[GCH][2];
 #pragma unroll
-        for (int gi = 0; gi < GCH; ++gi)
+        for (int gi = 0; gi < GCH; ++gi) {
+          const int gg = g0 + gi;
+          const bool live = gg < ngroups;
 #pragma unroll
-          for (int nb = 0; nb < 2; ++nb)
+          for (int nb = 0; nb < 2; ++nb) {
+            const int row = (gg * 16 + nb * 8) >> LS;   // rectangle row of this n8 block
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int j = (g0 + gi) * 16 + nb * 8 + 2 * t4 + (e & 1);
-              const int rr = e >> 1;
-              const bool ok = (g0 + gi < ngroups) && (j < nkeys) &&
-                              ((unsigned)((j >> ls) - rlo[rr]) < (unsigned)p.kh) &&
-                              ((colmask[rr] >> (j & smask)) & 1u);
-              const float v = ok ? s[gi][nb][e] * p.scale_log2 : -INFINITY;
-              s[gi][nb][e] = v;
-              mx[rr] = fmaxf(mx[rr], v);
+            for (int rr = 0; rr < 2; ++rr) {
+              const bool rok = live && ((unsigned)(row - rlo[rr]) < (unsigned)p.kh);
+              const int half = (LS == 5) ? (gg & 1) : 0;
+              const float cb0 = cbias[half][nb][rr][0], cb1 = cbias[half][nb][rr][1];
+              s[gi][nb][2 * rr] = rok ? fmaf(s[gi][nb][2 * rr], p.scale_log2, cb0) : -INFINITY;
+              s[gi][nb][2 * rr + 1] = rok ? fmaf(s[gi][nb][2 * rr + 1], p.scale_log2, cb1) : -INFINITY;
             }
+          }
+#pragma unroll
+          for (int rr = 0; rr < 2; ++rr)
+            gmx[gi][rr] = fmaxf(fmaxf(s[gi][0][2 * rr], s[gi][0][2 * rr + 1]),
+                                fmaxf(s[gi][1][2 * rr], s[gi][1][2 * rr + 1]));
+        }
+        float mx[2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {   // tree over the groups
+          float a = fmaxf(fmaxf(gmx[0][rr], gmx[1][rr]), fmaxf(gmx[2][rr], gmx[3][rr]));
+          float b = fmaxf(fmaxf(gmx[4][rr], gmx[5][rr]), fmaxf(gmx[6][rr], gmx[7][rr]));
+          mx[rr] = fmaxf(a, b);
+        }
         float mref[2];
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr) {
@@ -252,7 +277,7 @@ __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
           mx[rr] = fmaxf(mx[rr], __shfl_xor_sync(0xffffffffu, mx[rr], 2));
           const float mnew = fmaxf(mrow[rr], mx[rr]);
           mref[rr] = (mnew == -INFINITY) ? 0.f : mnew;
-          const float alpha = exp2f(mrow[rr] - mref[rr]);
+          const float alpha = ex2(mrow[rr] - mref[rr]);
           mrow[rr] = mnew;
           lrow[rr] *= alpha;
 #pragma unroll
@@ -262,18 +287,20 @@ __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
           }
         }
         // P = exp2(S - m), row sums (per thread; quad-reduced at the end), O += P V
+        float lsum[GCH][2];
 #pragma unroll
         for (int gi = 0; gi < GCH; ++gi) {
-          if (g0 + gi >= ngroups) break;
+          if (g0 + gi >= ngroups) {
+            lsum[gi][0] = lsum[gi][1] = 0.f;
+            continue;
+          }
           float pr[2][4];
 #pragma unroll
           for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float v = exp2f(s[gi][nb][e] - mref[e >> 1]);
-              pr[nb][e] = v;
-              lrow[e >> 1] += v;
-            }
+            for (int e = 0; e < 4; ++e) pr[nb][e] = ex2(s[gi][nb][e] - mref[e >> 1]);
+          lsum[gi][0] = (pr[0][0] + pr[0][1]) + (pr[1][0] + pr[1][1]);
+          lsum[gi][1] = (pr[0][2] + pr[0][3]) + (pr[1][2] + pr[1][3]);
           const uint32_t pa0 = pack_bf16(pr[0][0], pr[0][1]);
           const uint32_t pa1 = pack_bf16(pr[0][2], pr[0][3]);
           const uint32_t pa2 = pack_bf16(pr[1][0], pr[1][1]);
@@ -289,6 +316,10 @@ __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
             mma_bf16(o[nd + 1], pa0, pa1, pa2, pa3, b2, b3);
           }
         }
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+          lrow[rr] += ((lsum[0][rr] + lsum[1][rr]) + (lsum[2][rr] + lsum[3][rr])) +
+                      ((lsum[4][rr] + lsum[5][rr]) + (lsum[6][rr] + lsum[7][rr]));
       }
     }
     __syncthreads();
@@ -312,13 +343,21 @@ __global__ void __launch_bounds__(384, 1) na_bf16_kernel(const Params p) {
 
 }  // namespace na
 
+template <int DH>
+static wm_status prep_dh(int lim) {
+  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  return WM_OK;
+}
+
 wm_status prepare_na_bf16() {
   const int lim = 200 * 1024;  // the launcher never asks for more
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  return WM_OK;
+  wm_status st = prep_dh<16>(lim);
+  if (st == WM_OK) st = prep_dh<32>(lim);
+  if (st == WM_OK) st = prep_dh<48>(lim);
+  if (st == WM_OK) st = prep_dh<64>(lim);
+  return st;
 }
 
 // smallest power of two >= max(8, v)
@@ -419,7 +458,12 @@ wm_status launch_plan(const NaPlan& pl, na::Params p, int WH, int WW, int span, 
   if ((long)p.B * p.heads > 65535 || p.D > 65535) return fail(WM_ERR_INVALID_ARG, "batch*heads or D too large");
   dim3 grid(tiles_h * p.tiles_w, p.D, p.B * p.heads), block(32 * p.NWH * p.NWW);
   const int smem = (int)plan_smem(pl, WH, WW, span, p.kh, p.H, DH);
-  na::na_bf16_kernel<DH><<<grid, block, smem, s>>>(p);
+  switch (p.log2span) {
+    case 3: na::na_bf16_kernel<DH, 3><<<grid, block, smem, s>>>(p); break;
+    case 4: na::na_bf16_kernel<DH, 4><<<grid, block, smem, s>>>(p); break;
+    case 5: na::na_bf16_kernel<DH, 5><<<grid, block, smem, s>>>(p); break;
+    default: return fail(WM_ERR_INVALID_ARG, "unsupported key rectangle width");
+  }
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
