@@ -140,6 +140,26 @@ wm_status wm_schedule(int lead_hours, int* n6, int* n1);
  * after an internal synchronisation of `stream`. rel-L2 = sqrt(out[0]/out[1]). */
 wm_status wm_rel_l2(const float* a, const float* b, size_t n, double* out, void* stream);
 
+/* Allocation-free variant of wm_rel_l2 (the paper has no counterpart; this is
+ * a library service). Same inputs, outputs and result as wm_rel_l2, but it
+ * allocates nothing: its scratch is a fixed 64 KiB device array inside the
+ * library, present on every GPU that loads the library until the process
+ * exits. For callers that cannot allocate device memory at the point of the
+ * check -- a framework's caching allocator holds all free memory, or the
+ * caller must not take cudaMalloc/cudaFree (cudaFree synchronises the whole
+ * device and stalls every other stream).
+ *   - n <= 268,435,456 elements (4096 partial sums of 65,536 elements each);
+ *     larger n gives WM_ERR_INVALID_ARG and launches nothing.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls share the one scratch array; calls whose kernels overlap on
+ *     the GPU (e.g. from two streams at once) race and may return wrong sums.
+ *     Every partial is rewritten on each call, so nothing needs clearing.
+ *   - The sums are deterministic (fixed summation order), so they can differ
+ *     from wm_rel_l2's atomically accumulated sums in the last bits. */
+wm_status wm_rel_l2_noalloc(const float* a, const float* b, size_t n, double* out, void* stream);
+
 /* Reads (and clears) the device status word that bounded device-side waits
  * write; synchronises the device. WM_OK or WM_ERR_TIMEOUT. */
 wm_status wm_device_status(void);

@@ -47,6 +47,7 @@ _SIGS = {
     "wm_rollout_batch": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_c_int), _c_int, _vp]),
     "wm_schedule": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "wm_rel_l2": (_c_int, [_vp, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp]),
+    "wm_rel_l2_noalloc": (_c_int, [_vp, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp]),
     "wm_device_status": (_c_int, []),
     "wm_selftest_wait_timeout": (_c_int, [_c_int]),
     "wm_last_error": (ctypes.c_char_p, []),
@@ -184,6 +185,13 @@ def wm_schedule(lead_hours: int) -> tuple[int, int]:
 def wm_rel_l2(a, b, stream=None) -> float:
     out = (ctypes.c_double * 2)()
     _check(lib().wm_rel_l2(_ptr(a), _ptr(b), a.numel(), out, _stream(stream)))
+    return (out[0] / out[1]) ** 0.5 if out[1] > 0 else float(out[0] > 0)
+
+
+def wm_rel_l2_noalloc(a, b, stream=None) -> float:
+    """wm_rel_l2 without any device allocation (fixed in-library scratch, n <= 268,435,456)."""
+    out = (ctypes.c_double * 2)()
+    _check(lib().wm_rel_l2_noalloc(_ptr(a), _ptr(b), a.numel(), out, _stream(stream)))
     return (out[0] / out[1]) ** 0.5 if out[1] > 0 else float(out[0] > 0)
 
 
