@@ -120,6 +120,23 @@ def _traffic(kind):
     return d["dram_bytes_per_launch"]
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Largest x over the ranks of the default process group (x itself when single)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(local_total_ms: float, steps: int, world_size: int, device) -> tuple[float, float]:
+    """(slowest rank's total ms, whole-job forecasts/s) for `steps` steps on every replica."""
+    total_ms = max_over_ranks(local_total_ms, device)
+    return total_ms, world_size * steps / (total_ms / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -221,13 +238,8 @@ def run_ours(args):
         barrier()
     kt = wm.wm_timing_end(ctx)
     wm.wm_device_status()
-    total_ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = replica_value(ev0.elapsed_time(ev1), args.steps, ws, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * args.steps / (total_ms / 1e3)
     launches = sum(c for _, c in kt.values())
 
     # ---------------- roofline of the dominant kernel (and of every GEMM)
@@ -301,11 +313,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             wm.wm_forecast_host(ctx, hin, hout, 6)
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, dev)
         nbytes = hin.numel() * 4
         out["e2e"] = {"value": ws * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                       "d2h_bytes_per_step": nbytes, "call": "wm_forecast_host(lead 6 h)"}

@@ -236,6 +236,28 @@ wm_status wm_op_layernorm(const float* x, const float* gamma, const float* beta,
 wm_status wm_op_linear(const void* A, const void* W, const float* bias, void* out, int M, int N, int K,
                        int precision, int epilogue, void* stream);
 
+/* e4m3 linear layer (the FP8 MLP's GEMMs): A [M, K] and W [N, K] are E4M3 codes
+ * (one byte each, OCP FP8 E4M3), D = alpha * (A W^T) + bias with FP32 accumulation.
+ * epilogue 2: out (float32) += D;  3: out (float32) = D;
+ * epilogue 4: out (E4M3 codes [M, N]) = e4m3(GELU(D) * out_scale), round to nearest
+ *             even, saturating at +-448.  K % 16 == 0, N % 16 == 0. */
+wm_status wm_op_linear_e4m3(const void* A, const void* W, float alpha, const float* bias, void* out, float out_scale,
+                            int M, int N, int K, int epilogue, void* stream);
+
+/* LayerNorm with E4M3 output: out[M, C] = e4m3(LN(x) * inv_scale) (RNE, saturating).
+ * C in {128, 256, 384, 512, 768, 1024}. */
+wm_status wm_op_layernorm_e4m3(const float* x, const float* gamma, const float* beta, void* out, int M, int C,
+                               float eps, float inv_scale, void* stream);
+
+/* The static per-tensor scales the FP8 MLP precision uses for block `block` of
+ * processor `which` (HOST out[4]): s_u (LN2 output), s_w1, s_h (GELU output), s_w2.
+ *   s_u  = max_c(|gamma2_c| sqrt(C-1) + |beta2_c|) / 448   (bound on |LN2(x)|)
+ *   s_w1 = max|W1| / 448, s_w2 = max|W2| / 448
+ *   s_h  = max(max_j(sum_c |W1_jc| (|gamma2_c| sqrt(C-1) + |beta2_c|) + |b1_j|), 0.17) / 448
+ * (bound on |GELU(FC1)|). Bounds hold for every input, so no value saturates and
+ * the scales do not depend on the batch or the request. */
+wm_status wm_fp8_scales(wm_ctx* ctx, int which, int block, float* out);
+
 /* 3D neighborhood attention on qkv [batch*D*H*W, 3C] (q | k | v, each head-major)
  * -> out [batch*D*H*W, C]. precision FP32: float32 in/out; BF16: bfloat16 in/out
  * (BF16 requires dh = C/heads in {16, 32, 48, 64}). */

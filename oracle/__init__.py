@@ -4,6 +4,6 @@ Only tests/, __graft_entry__.smoke() and the CPU-baseline leg of bench.py may
 import this package. The GPU library never depends on it.
 """
 from .wm_oracle import (  # noqa: F401
-    axis_window, block, e4m3_decode, e4m3_round, block_at_tokens, gelu, greedy_schedule, layer_norm, linear,
+    axis_window, block, block_fp8mlp, e4m3_decode, e4m3_round, fp8_mlp_scales, block_at_tokens, gelu, greedy_schedule, layer_norm, linear,
     neighbor_index, neighborhood_attention, processor, rel_l2, rollout,
 )

@@ -287,6 +287,55 @@ def e4m3_round(x):
     return np.sign(x) * r
 
 
+def fp8_mlp_scales(w, C):
+    """Static per-tensor E4M3 scales of the FP8-MLP precision for one block.
+
+    Each scale is a bound on the magnitude of its tensor divided by 448 (the
+    largest E4M3 value), so no value saturates for any input:
+      LN2 output: |u_c| <= |gamma_c| sqrt(C - 1) + |beta_c|, because a biased
+        standard deviation s over C values satisfies |x_c - mean| <= sqrt(C - 1) s;
+      W1, W2: their largest magnitude;
+      GELU(FC1) output: |z_j| <= sum_c |W1_jc| bound_u_c + |b1_j| (triangle
+        inequality) and |GELU(z)| <= max(|z|, 0.17) (GELU's minimum is -0.16997).
+    Returns (s_u, s_w1, s_h, s_w2).
+    """
+    g = np.abs(np.asarray(w["ln2_g"], np.float64))
+    b = np.abs(np.asarray(w["ln2_b"], np.float64))
+    W1 = np.abs(np.asarray(w["w1"], np.float64))
+    W2 = np.abs(np.asarray(w["w2"], np.float64))
+    b1 = np.abs(np.asarray(w["b1"], np.float64))
+    bound_u = g * np.sqrt(C - 1.0) + b
+    bound_z = W1 @ bound_u + b1
+    return (bound_u.max() / 448.0, W1.max() / 448.0, max(bound_z.max(), 0.17) / 448.0, W2.max() / 448.0)
+
+
+def block_fp8mlp(x, w, shape, rounding=None):
+    """The block with its MLP operands rounded to E4M3 under the static scales.
+
+    Same as ``block`` except: LN2's output, W1, the GELU output and W2 are each
+    divided by their scale, rounded to E4M3 (``rounding``, default
+    ``e4m3_round``) and the products rescaled. The attention half is exact.
+    """
+    q = e4m3_round if rounding is None else rounding
+    w = _f64(w)
+    x = np.asarray(x, np.float64)
+    B = x.shape[0]
+    C = shape.C
+    N = shape.D * shape.H * shape.W
+    xf = x.reshape(B, N, C)
+    nbr = neighbor_index(shape.D, shape.H, shape.W, shape.kd, shape.kh, shape.kw, shape.lon_periodic)
+    u = layer_norm(xf, w["ln1_g"], w["ln1_b"], shape.ln_eps)
+    qkv = linear(u, w["wqkv"], w["bqkv"])
+    o = neighborhood_attention(qkv[..., :C], qkv[..., C:2 * C], qkv[..., 2 * C:], shape.heads, nbr)
+    x1 = xf + linear(o, w["wo"], w["bo"])
+    s_u, s_w1, s_h, s_w2 = fp8_mlp_scales(w, C)
+    u2 = q(layer_norm(x1, w["ln2_g"], w["ln2_b"], shape.ln_eps) / s_u)
+    z = (u2 @ q(w["w1"] / s_w1).T) * (s_u * s_w1) + w["b1"]
+    h = q(gelu(z) / s_h)
+    x2 = x1 + (h @ q(w["w2"] / s_w2).T) * (s_h * s_w2) + w["b2"]
+    return x2.reshape(x.shape)
+
+
 def rel_l2(y, y_ref) -> float:
     """||y - y_ref||_2 / ||y_ref||_2 accumulated in float64."""
     y = np.asarray(y, np.float64).ravel()

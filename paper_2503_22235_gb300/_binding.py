@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "wm.h")
 WM_OK, WM_ERR_INVALID_ARG, WM_ERR_OOM, WM_ERR_CUDA, WM_ERR_TIMEOUT, WM_ERR_BUSY, WM_ERR_IO, WM_ERR_NOT_FOUND = range(8)
 WM_P6, WM_P1 = 0, 1
 WM_PREC_FP32, WM_PREC_BF16, WM_PREC_BF16_FP8MLP = 0, 1, 2
-EPI_STORE, EPI_GELU, EPI_RESID_F32, EPI_STORE_F32 = 0, 1, 2, 3
+EPI_STORE, EPI_GELU, EPI_RESID_F32, EPI_STORE_F32, EPI_GELU_F8 = 0, 1, 2, 3, 4
 
 _c_int, _c_float, _vp, _sz = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
 
@@ -63,6 +63,9 @@ _SIGS = {
     "wm_op_layernorm": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _vp]),
     "wm_op_linear": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _vp]),
     "wm_op_neighborhood_attention": (_c_int, [_vp, _vp] + [_c_int] * 11 + [_vp]),
+    "wm_op_linear_e4m3": (_c_int, [_vp, _vp, _c_float, _vp, _vp, _c_float, _c_int, _c_int, _c_int, _c_int, _vp]),
+    "wm_op_layernorm_e4m3": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_float, _c_float, _vp]),
+    "wm_fp8_scales": (_c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_c_float)]),
 }
 
 _lib = None
@@ -286,3 +289,23 @@ def wm_op_neighborhood_attention(qkv, out, batch, D, H, W, C, heads, kd, kh, kw,
                                  stream=None):
     _check(lib().wm_op_neighborhood_attention(_ptr(qkv), _ptr(out), batch, D, H, W, C, heads, kd, kh, kw,
                                               int(bool(lon_periodic)), int(precision), _stream(stream)))
+
+
+def wm_op_linear_e4m3(A, W, alpha, bias, out, out_scale, epilogue, stream=None):
+    """A [M, K], W [N, K]: uint8 tensors of E4M3 codes."""
+    M, K = A.shape
+    N = W.shape[0]
+    _check(lib().wm_op_linear_e4m3(_ptr(A), _ptr(W), float(alpha), _ptr(bias), _ptr(out), float(out_scale), M, N, K,
+                                   int(epilogue), _stream(stream)))
+
+
+def wm_op_layernorm_e4m3(x, gamma, beta, out, eps, inv_scale, stream=None):
+    M, C = x.shape[0], x.shape[-1]
+    _check(lib().wm_op_layernorm_e4m3(_ptr(x), _ptr(gamma), _ptr(beta), _ptr(out), M, C, float(eps), float(inv_scale),
+                                      _stream(stream)))
+
+
+def wm_fp8_scales(ctx, which, block) -> tuple:
+    out = (_c_float * 4)()
+    _check(lib().wm_fp8_scales(ctx, int(which), int(block), out))
+    return tuple(out)

@@ -31,6 +31,10 @@ struct BlockW {
   const float *ln1_g, *ln1_b, *wqkv, *bqkv, *wo, *bo, *ln2_g, *ln2_b, *w1, *b1, *w2, *b2;
   bf16 *hqkv, *ho, *h1, *h2;
   CUtensorMap tm_qkv[2], tm_o[2], tm_1[2], tm_2[2];  // [0]: box 128 rows, [1]: box 256 rows
+  // FP8 MLP: e4m3 copies of W1, W2 and the static per-tensor scales
+  uint8_t *q1, *q2;
+  CUtensorMap tm_q1[2], tm_q2[2];
+  float s_u, s_w1, s_h, s_w2;   // LN2 output, W1, GELU output, W2
 };
 
 }  // namespace
@@ -41,11 +45,14 @@ struct wm_ctx {
   long N = 0;
   float* d_w32 = nullptr;
   bf16* d_wh = nullptr;
+  uint8_t* d_wq = nullptr;   // e4m3 W1, W2 per block
   std::vector<BlockW> blk[2];
   // workspace for cap32 (FP32 path) / cap16 (BF16 path) latents
   int cap32 = 0, cap16 = 0;
   float *f_u = nullptr, *f_qkv = nullptr, *f_o = nullptr, *f_h = nullptr;
   bf16 *h_u = nullptr, *h_qkv = nullptr, *h_o = nullptr, *h_h = nullptr;
+  uint8_t *q_u = nullptr, *q_h = nullptr;   // e4m3 MLP operands (FP8 MLP precision)
+  CUtensorMap tm_qu{}, tm_qh{}, tmc_qh{};
   CUtensorMap tm_u{}, tm_o{}, tm_h{};
   CUtensorMap tmc_qkv{}, tmc_h{};   // GEMM outputs (TMA store descriptors)
   // staging
@@ -103,6 +110,8 @@ void destroy_graphs(wm_ctx* ctx) {
 void free_workspace(wm_ctx* ctx) {
   cudaFree(ctx->f_u); cudaFree(ctx->f_qkv); cudaFree(ctx->f_o); cudaFree(ctx->f_h);
   cudaFree(ctx->h_u); cudaFree(ctx->h_qkv); cudaFree(ctx->h_o); cudaFree(ctx->h_h);
+  cudaFree(ctx->q_u); cudaFree(ctx->q_h);
+  ctx->q_u = ctx->q_h = nullptr;
   ctx->f_u = ctx->f_qkv = ctx->f_o = ctx->f_h = nullptr;
   ctx->h_u = ctx->h_qkv = ctx->h_o = ctx->h_h = nullptr;
   ctx->cap32 = ctx->cap16 = 0;
@@ -138,6 +147,19 @@ wm_status ensure_workspace(wm_ctx* ctx, int batch, bool fp32) {
     }
     cudaGetLastError();
     return fail(WM_ERR_OOM, "workspace allocation failed for batch " + std::to_string(batch));
+  }
+  if (!fp32) {
+    cudaFree(ctx->q_u);
+    cudaFree(ctx->q_h);
+    ctx->q_u = ctx->q_h = nullptr;
+    if (cudaMalloc(&ctx->q_u, M * C) != cudaSuccess || cudaMalloc(&ctx->q_h, M * 4 * C) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(WM_ERR_OOM, "e4m3 workspace allocation failed");
+    }
+    if (C % 16 == 0 && (!wm::make_tmap_e4m3(&ctx->tm_qu, ctx->q_u, M, C, 128) ||
+                        !wm::make_tmap_e4m3(&ctx->tm_qh, ctx->q_h, M, 4 * C, 128) ||
+                        !wm::make_tmap_out_e4m3(&ctx->tmc_qh, ctx->q_h, M, 4 * C)))
+      return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the e4m3 workspace");
   }
   cap = batch;
   if (!fp32 && check_bf16_shape(ctx->cfg) == WM_OK) {
@@ -245,6 +267,25 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, cuda
     WM_TRY(wm::launch_na_bf16(ctx->h_qkv, ctx->h_o, batch, c.D, c.H, c.W, C, c.heads, c.kd, c.kh, c.kw, per, s)); }
   { TimedLaunch t(ctx, WM_K_PROJ, s);
     WM_TRY(gemm_bf16(ctx->tm_o, w.tm_o, tm_x, M, C, C, w.bo, wm::EPI_RESID_F32, s)); }
+  if (c.precision == WM_PREC_BF16_FP8MLP) {
+    // MLP in e4m3 with static per-tensor scales: u2 / s_u and W1 / s_w1 into
+    // FC1 (alpha = s_u s_w1), GELU output / s_h and W2 / s_w2 into FC2
+    { TimedLaunch t(ctx, WM_K_LN2, s);
+      WM_TRY(wm::launch_layernorm_e4m3(x, w.ln2_g, w.ln2_b, ctx->q_u, (int)M, C, c.ln_eps, 1.f / w.s_u, s)); }
+    wm::GemmArgs a;
+    a.f8 = true;
+    a.M = (int)M; a.K = C; a.N = 4 * C;
+    a.bn = pick_bn(M, a.N);
+    a.tmA = ctx->tm_qu; a.tmB = w.tm_q1[a.bn == 256]; a.tmC = ctx->tmc_qh;
+    a.bias = w.b1; a.epi = wm::EPI_GELU_F8; a.alpha = w.s_u * w.s_w1; a.out_scale = 1.f / w.s_h;
+    { TimedLaunch t(ctx, WM_K_FC1, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+    a.K = 4 * C; a.N = C;
+    a.bn = pick_bn(M, a.N);
+    a.tmA = ctx->tm_qh; a.tmB = w.tm_q2[a.bn == 256]; a.tmC = tm_x;
+    a.bias = w.b2; a.epi = wm::EPI_RESID_F32; a.alpha = w.s_h * w.s_w2; a.out_scale = 1.f;
+    { TimedLaunch t(ctx, WM_K_FC2, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+    return WM_OK;
+  }
   { TimedLaunch t(ctx, WM_K_LN2, s);
     WM_TRY(wm::launch_layernorm(x, w.ln2_g, w.ln2_b, ctx->h_u, true, (int)M, C, c.ln_eps, s)); }
   { TimedLaunch t(ctx, WM_K_FC1, s);
@@ -265,8 +306,11 @@ wm_status check_compute(wm_ctx* ctx, const void* latent, int batch) {
   if (!latent) return fail(WM_ERR_INVALID_ARG, "latent is NULL");
   if (batch <= 0) return fail(WM_ERR_INVALID_ARG, "batch must be >= 1");
   if (ctx->cfg.precision != WM_PREC_FP32) WM_TRY(check_bf16_shape(ctx->cfg));
-  if (ctx->cfg.precision == WM_PREC_BF16_FP8MLP)
-    return fail(WM_ERR_INVALID_ARG, "FP8 MLP precision is not available in this build");
+  if (ctx->cfg.precision == WM_PREC_BF16_FP8MLP) {
+    const int C = ctx->cfg.C;
+    if (C != 128 && C != 256 && C != 384 && C != 512 && C != 768 && C != 1024)
+      return fail(WM_ERR_INVALID_ARG, "FP8 MLP precision needs C in {128, 256, 384, 512, 768, 1024}");
+  }
   return WM_OK;
 }
 
@@ -308,6 +352,7 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
   const size_t C = c.C;
   const size_t mats = 12 * C * C;  // wqkv + wo + w1 + w2 per block
   WM_CUDA(cudaMalloc(&ctx->d_wh, mats * nb * 2));
+  WM_CUDA(cudaMalloc(&ctx->d_wq, 8 * C * C * nb));
   for (int i = 0; i < nb; ++i) {
     const int which = i < c.blocks_p6 ? 0 : 1;
     const float* p = ctx->d_w32 + per * i;
@@ -333,6 +378,52 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
     WM_TRY(wm::launch_f32_to_bf16(w.wo, w.ho, C * C, 0));
     WM_TRY(wm::launch_f32_to_bf16(w.w1, w.h1, 4 * C * C, 0));
     WM_TRY(wm::launch_f32_to_bf16(w.w2, w.h2, 4 * C * C, 0));
+    // ---- FP8 MLP: static per-tensor scales from bounds that hold for every input
+    {
+      const float* hp = host + per * i;
+      const float* g2 = hp + 6 * C + 4 * C * C;   // ln1_g ln1_b wqkv bqkv wo bo precede ln2_g
+      const float* b2v = g2 + C;
+      const float* hw1 = b2v + C;
+      const float* hb1 = hw1 + 4 * C * C;
+      const float* hw2 = hb1 + 4 * C;
+      // |LN2(x)_c| <= |gamma_c| sqrt(C - 1) + |beta_c|  (|x_c - mean| <= sqrt(C-1) * biased std)
+      std::vector<double> bu(C);
+      double bu_max = 0.0;
+      for (size_t c2 = 0; c2 < C; ++c2) {
+        bu[c2] = std::fabs((double)g2[c2]) * std::sqrt((double)C - 1.0) + std::fabs((double)b2v[c2]);
+        bu_max = std::max(bu_max, bu[c2]);
+      }
+      double aw1 = 0.0, aw2 = 0.0, bz = 0.0;
+      for (size_t j = 0; j < 4 * C; ++j) {
+        double z = std::fabs((double)hb1[j]);
+        for (size_t c2 = 0; c2 < C; ++c2) {
+          const double a = std::fabs((double)hw1[j * C + c2]);
+          aw1 = std::max(aw1, a);
+          z += a * bu[c2];
+        }
+        bz = std::max(bz, z);
+      }
+      for (size_t j = 0; j < 4 * C * C; ++j) aw2 = std::max(aw2, std::fabs((double)hw2[j]));
+      // |GELU(z)| <= max(|z|, 0.17): the GELU minimum is -0.16997 at z = -0.7518
+      const double bh = std::max(bz, 0.17);
+      w.s_u = (float)(std::max(bu_max, 1e-30) / 448.0);
+      w.s_w1 = (float)(std::max(aw1, 1e-30) / 448.0);
+      w.s_h = (float)(bh / 448.0);
+      w.s_w2 = (float)(std::max(aw2, 1e-30) / 448.0);
+    }
+    w.q1 = ctx->d_wq + 8 * C * C * i;
+    w.q2 = w.q1 + 4 * C * C;
+    WM_TRY(wm::launch_f32_to_e4m3(w.w1, w.q1, 4 * C * C, 1.f / w.s_w1, 0));
+    WM_TRY(wm::launch_f32_to_e4m3(w.w2, w.q2, 4 * C * C, 1.f / w.s_w2, 0));
+    if (C % 16 == 0) {
+      bool ok = true;
+      for (int k = 0; k < 2; ++k) {
+        const uint32_t box = k ? 256 : 128;
+        ok = ok && wm::make_tmap_e4m3(&w.tm_q1[k], w.q1, 4 * C, C, box);
+        ok = ok && wm::make_tmap_e4m3(&w.tm_q2[k], w.q2, C, 4 * C, box);
+      }
+      if (!ok) return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the e4m3 weights");
+    }
     if (C % 8 == 0) {
       bool ok = true;
       for (int k = 0; k < 2; ++k) {
@@ -419,6 +510,7 @@ wm_status wm_destroy(wm_ctx* ctx) {
   free_workspace(ctx);
   cudaFree(ctx->d_w32);
   cudaFree(ctx->d_wh);
+  cudaFree(ctx->d_wq);
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_io);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -645,6 +737,45 @@ wm_status wm_op_linear(const void* A, const void* W, const float* bias, void* ou
   a.M = M; a.N = N; a.K = K;
   a.bias = bias; a.epi = epilogue;
   return wm::launch_gemm_tc(a, s);
+}
+
+wm_status wm_fp8_scales(wm_ctx* ctx, int which, int block, float* out) {
+  if (!ctx || !out || (which != WM_P6 && which != WM_P1)) return fail(WM_ERR_INVALID_ARG, "bad arguments");
+  if (block < 0 || block >= (int)ctx->blk[which].size()) return fail(WM_ERR_INVALID_ARG, "block index out of range");
+  const BlockW& w = ctx->blk[which][block];
+  out[0] = w.s_u;
+  out[1] = w.s_w1;
+  out[2] = w.s_h;
+  out[3] = w.s_w2;
+  return WM_OK;
+}
+
+wm_status wm_op_layernorm_e4m3(const float* x, const float* gamma, const float* beta, void* out, int M, int C,
+                               float eps, float inv_scale, void* stream) {
+  if (!x || !gamma || !beta || !out || M < 0 || C <= 0) return fail(WM_ERR_INVALID_ARG, "bad layernorm arguments");
+  WM_TRY(wm::prepare_kernels());
+  return wm::launch_layernorm_e4m3(x, gamma, beta, (uint8_t*)out, M, C, eps, inv_scale, (cudaStream_t)stream);
+}
+
+wm_status wm_op_linear_e4m3(const void* A, const void* W, float alpha, const float* bias, void* out, float out_scale,
+                            int M, int N, int K, int epilogue, void* stream) {
+  if (!A || !W || !out || M < 0 || N <= 0 || K <= 0) return fail(WM_ERR_INVALID_ARG, "bad linear arguments");
+  if (epilogue != wm::EPI_STORE_F32 && epilogue != wm::EPI_RESID_F32 && epilogue != wm::EPI_GELU_F8)
+    return fail(WM_ERR_INVALID_ARG, "e4m3 linear epilogue must be 2, 3 or 4");
+  if (K % 16 != 0 || N % 16 != 0) return fail(WM_ERR_INVALID_ARG, "e4m3 linear needs K % 16 == 0 and N % 16 == 0");
+  WM_TRY(wm::prepare_kernels());
+  if (M == 0) return WM_OK;
+  wm::GemmArgs a;
+  a.f8 = true;
+  a.bn = pick_bn(M, N);
+  const bool okc = epilogue == wm::EPI_GELU_F8 ? wm::make_tmap_out_e4m3(&a.tmC, out, (uint64_t)M, (uint64_t)N)
+                                               : wm::make_tmap_out(&a.tmC, out, (uint64_t)M, (uint64_t)N, true);
+  if (!okc || !wm::make_tmap_e4m3(&a.tmA, A, (uint64_t)M, (uint64_t)K, 128) ||
+      !wm::make_tmap_e4m3(&a.tmB, W, (uint64_t)N, (uint64_t)K, (uint32_t)a.bn))
+    return fail(WM_ERR_INVALID_ARG, "cannot build TMA descriptors (pointer alignment or sizes)");
+  a.M = M; a.N = N; a.K = K;
+  a.bias = bias; a.epi = epilogue; a.alpha = alpha; a.out_scale = out_scale;
+  return wm::launch_gemm_tc(a, (cudaStream_t)stream);
 }
 
 wm_status wm_op_neighborhood_attention(const void* qkv, void* out, int batch, int D, int H, int W, int C, int heads,

@@ -1,6 +1,8 @@
 // Plain FP32 path: LayerNorm, FP32-FMA GEMM with fused epilogues, and 3D
 // neighborhood attention on CUDA cores. Strict FP32 FMA everywhere (no TF32),
 // so that a block matches the float64 oracle to ~1e-6 relative L2.
+#include <cuda_fp8.h>
+
 #include "wm_internal.cuh"
 
 namespace wm {
@@ -85,6 +87,65 @@ __global__ void ln_rows_generic(const float* __restrict__ x, const float* __rest
   }
   const float rstd = rsqrtf(warp_sum(q) / C + eps);
   for (int c = lane; c < C; c += 32) store_val(out + row * C + c, (xr[c] - mean) * rstd * g[c] + b[c]);
+}
+
+// LayerNorm rows to e4m3: one warp per row, FP32 statistics as above, output
+// e4m3(LN(x) * inv_scale) with round-to-nearest-even and saturation.
+template <int V4>
+__global__ void ln_rows_e4m3(const float* __restrict__ x, const float* __restrict__ g, const float* __restrict__ b,
+                             uint8_t* __restrict__ out, int M, float eps, float inv_scale) {
+  const int C = 128 * V4;
+  const int lane = threadIdx.x & 31;
+  const long row = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= M) return;
+  const float4* xr = reinterpret_cast<const float4*>(x + row * C);
+  float4 v[V4];
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < V4; ++i) {
+    v[i] = xr[lane + 32 * i];
+    s += (v[i].x + v[i].y) + (v[i].z + v[i].w);
+  }
+  const float mean = warp_sum(s) / C;
+  float q = 0.f;
+#pragma unroll
+  for (int i = 0; i < V4; ++i) {
+    float a = v[i].x - mean, bb = v[i].y - mean, c = v[i].z - mean, d = v[i].w - mean;
+    q += (a * a + bb * bb) + (c * c + d * d);
+  }
+  const float rstd = rsqrtf(warp_sum(q) / C + eps);
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+#pragma unroll
+  for (int i = 0; i < V4; ++i) {
+    const int c = 4 * (lane + 32 * i);
+    float4 gg = g4[lane + 32 * i], bb = b4[lane + 32 * i];
+    const float r0 = ((v[i].x - mean) * rstd * gg.x + bb.x) * inv_scale;
+    const float r1 = ((v[i].y - mean) * rstd * gg.y + bb.y) * inv_scale;
+    const float r2 = ((v[i].z - mean) * rstd * gg.z + bb.z) * inv_scale;
+    const float r3 = ((v[i].w - mean) * rstd * gg.w + bb.w) * inv_scale;
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(r0, r1), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(r2, r3), __NV_SATFINITE, __NV_E4M3);
+    *reinterpret_cast<uint32_t*>(out + row * C + c) = lo | (hi << 16);
+  }
+}
+
+wm_status launch_layernorm_e4m3(const float* x, const float* g, const float* b, uint8_t* out, int M, int C,
+                                float eps, float inv_scale, cudaStream_t s) {
+  if (M <= 0) return WM_OK;
+  const int warps = 8;
+  dim3 grid((M + warps - 1) / warps), block(32 * warps);
+  switch (C) {
+    case 128: ln_rows_e4m3<1><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
+    case 256: ln_rows_e4m3<2><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
+    case 384: ln_rows_e4m3<3><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
+    case 512: ln_rows_e4m3<4><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
+    case 768: ln_rows_e4m3<6><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
+    case 1024: ln_rows_e4m3<8><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
+    default: return fail(WM_ERR_INVALID_ARG, "e4m3 LayerNorm needs C in {128, 256, 384, 512, 768, 1024}");
+  }
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
 }
 
 wm_status launch_layernorm(const float* x, const float* g, const float* b, void* out, bool out_bf16, int M, int C,

@@ -16,6 +16,8 @@
 // Every mbarrier wait is bounded in time; on a timeout the CTA records
 // WM_ERR_TIMEOUT in the device status word, drains its own copies and MMAs,
 // frees TMEM and returns.
+#include <cuda_fp8.h>
+
 #include "wm_internal.cuh"
 
 namespace wm {
@@ -23,13 +25,14 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;                 // bf16 elements per k-slice = one 128-byte swizzle row
+constexpr int BKB = 128;               // bytes per k-slice row (bf16: 64 elements, e4m3: 128)
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
 
 template <int BN>
 struct Cfg {
-  static constexpr int A_BYTES = BM * BK * 2;
-  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int A_BYTES = BM * BKB;
+  static constexpr int B_BYTES = BN * BKB;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGES = (BN >= 256) ? 4 : 6;
   static constexpr int EPI_BYTES = NUM_EPI_WARPS * 4096;     // one 32x32 staging tile per epilogue warp
@@ -102,6 +105,20 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f8f6f4: D f32, A and B E4M3 (format 0), both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
   asm volatile(
@@ -157,7 +174,22 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // swizzles keep the 32 row-parallel stores free of bank conflicts.
 template <int EPI>
 __device__ __forceinline__ void stage_row(uint8_t* buf, const float (&x)[32], int r) {
-  if constexpr (EPI == EPI_STORE || EPI == EPI_GELU) {
+  if constexpr (EPI == EPI_GELU_F8) {
+    // e4m3 rows of 32 bytes with the 32-byte swizzle (unit k of row r at k ^ ((r >> 2) & 1));
+    // x is already divided by the output scale; RNE, saturating at +-448
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = 16 * k + 4 * e;
+        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(x[j], x[j + 1]), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(x[j + 2], x[j + 3]), __NV_SATFINITE, __NV_E4M3);
+        w[e] = lo | (hi << 16);
+      }
+      *reinterpret_cast<uint4*>(buf + r * 32 + ((k ^ ((r >> 2) & 1)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else if constexpr (EPI == EPI_STORE || EPI == EPI_GELU) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       uint32_t w[4];
@@ -176,11 +208,12 @@ __device__ __forceinline__ void stage_row(uint8_t* buf, const float (&x)[32], in
   }
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, bool F8>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmC, int M, int N, int K, const float* __restrict__ bias,
-                        int* __restrict__ status) {
+                        float alpha, float out_scale, int* __restrict__ status) {
+  constexpr int BKE = F8 ? 128 : 64;     // elements per k-slice
   using CF = Cfg<BN>;
   constexpr int STAGES = CF::STAGES;
   extern __shared__ uint8_t smem_raw[];
@@ -197,7 +230,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_n = (N + BN - 1) / BN;
   const int num_tiles = ((M + BM - 1) / BM) * num_n;
-  const int nk = (K + BK - 1) / BK;
+  const int nk = (K + BKE - 1) / BKE;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -239,8 +272,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag)) { ok = false; break; }
           const uint32_t sa = smem_base + stage * CF::STAGE_BYTES;
           mbar_expect_tx(&full_bar[stage], CF::STAGE_BYTES);
-          tma_load_2d(sa, &tmA, &full_bar[stage], kb * BK, m0);
-          tma_load_2d(sa + CF::A_BYTES, &tmB, &full_bar[stage], kb * BK, n0);
+          tma_load_2d(sa, &tmA, &full_bar[stage], kb * BKE, m0);
+          tma_load_2d(sa + CF::A_BYTES, &tmB, &full_bar[stage], kb * BKE, n0);
           issued_mask |= 1u << stage;
           last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -260,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------------ MMA issuer
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -277,8 +310,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t sa = smem_base + stage * CF::STAGE_BYTES;
           const uint64_t adesc = sw128_desc(sa), bdesc = sw128_desc(sa + CF::A_BYTES);
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            umma_bf16(d_tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (kb | k) != 0);
+          for (int k = 0; k < 4; ++k) {   // 4 MMAs of 32 bytes of K (16 bf16 / 32 e4m3) per slice
+            if constexpr (F8)
+              umma_e4m3(d_tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (kb | k) != 0);
+            else
+              umma_bf16(d_tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (kb | k) != 0);
+          }
           umma_commit(&empty_bar[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
@@ -327,8 +364,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (row0 >= M || n >= N) continue;   // whole chunk outside the output (warp-uniform)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
+          if constexpr (F8) v[j] *= alpha;
           v[j] += (bias && n + j < N) ? __ldg(bias + n + j) : 0.f;
-          if constexpr (EPI == EPI_GELU) v[j] = gelu_erf(v[j]);
+          if constexpr (EPI == EPI_GELU || EPI == EPI_GELU_F8) v[j] = gelu_erf(v[j]);
+          if constexpr (EPI == EPI_GELU_F8) v[j] *= out_scale;
         }
         if (lane == 0) bulk_wait_read_all();   // the previous chunk's store has left the staging tile
         __syncwarp();
@@ -356,53 +395,71 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, bool F8>
 static wm_status launch_one(const GemmArgs& a, cudaStream_t s) {
   using CF = Cfg<BN>;
-  auto kern = gemm_bf16_tc_kernel<BN, EPI>;
+  auto kern = gemm_bf16_tc_kernel<BN, EPI, F8>;
   const int tiles = ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  kern<<<grid, THREADS, CF::SMEM, s>>>(a.tmA, a.tmB, a.tmC, a.M, a.N, a.K, a.bias, device_status_word());
+  kern<<<grid, THREADS, CF::SMEM, s>>>(a.tmA, a.tmB, a.tmC, a.M, a.N, a.K, a.bias, a.alpha, a.out_scale,
+                                       device_status_word());
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
-template <int BN, int EPI>
+template <int BN, int EPI, bool F8>
 static wm_status set_attr() {
-  WM_CUDA(cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  WM_CUDA(cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, EPI, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                Cfg<BN>::SMEM));
   return WM_OK;
+}
+
+template <int BN>
+static wm_status set_attrs_bn() {
+  wm_status st = WM_OK;
+  auto chk = [&](wm_status x) { if (st == WM_OK) st = x; };
+  chk(set_attr<BN, EPI_STORE, false>());
+  chk(set_attr<BN, EPI_GELU, false>());
+  chk(set_attr<BN, EPI_RESID_F32, false>());
+  chk(set_attr<BN, EPI_STORE_F32, false>());
+  chk(set_attr<BN, EPI_GELU_F8, true>());
+  chk(set_attr<BN, EPI_RESID_F32, true>());
+  chk(set_attr<BN, EPI_STORE_F32, true>());
+  return st;
+}
+
+template <int BN>
+static wm_status launch_bn(const GemmArgs& a, cudaStream_t s) {
+  if (a.f8) {
+    switch (a.epi) {
+      case EPI_GELU_F8: return launch_one<BN, EPI_GELU_F8, true>(a, s);
+      case EPI_RESID_F32: return launch_one<BN, EPI_RESID_F32, true>(a, s);
+      case EPI_STORE_F32: return launch_one<BN, EPI_STORE_F32, true>(a, s);
+      default: return fail(WM_ERR_INVALID_ARG, "unsupported epilogue for the e4m3 GEMM");
+    }
+  }
+  switch (a.epi) {
+    case EPI_STORE: return launch_one<BN, EPI_STORE, false>(a, s);
+    case EPI_GELU: return launch_one<BN, EPI_GELU, false>(a, s);
+    case EPI_RESID_F32: return launch_one<BN, EPI_RESID_F32, false>(a, s);
+    case EPI_STORE_F32: return launch_one<BN, EPI_STORE_F32, false>(a, s);
+    default: return fail(WM_ERR_INVALID_ARG, "unsupported epilogue for the bf16 GEMM");
+  }
 }
 
 }  // namespace tc
 
 wm_status prepare_gemm_tc() {
-  wm_status st = WM_OK;
-  auto chk = [&](wm_status s) { if (st == WM_OK) st = s; };
-  chk(tc::set_attr<128, EPI_STORE>()); chk(tc::set_attr<128, EPI_GELU>());
-  chk(tc::set_attr<128, EPI_RESID_F32>()); chk(tc::set_attr<128, EPI_STORE_F32>());
-  chk(tc::set_attr<256, EPI_STORE>()); chk(tc::set_attr<256, EPI_GELU>());
-  chk(tc::set_attr<256, EPI_RESID_F32>()); chk(tc::set_attr<256, EPI_STORE_F32>());
+  wm_status st = tc::set_attrs_bn<128>();
+  if (st == WM_OK) st = tc::set_attrs_bn<256>();
   return st;
 }
 
 wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0) return WM_OK;
-  if (a.K <= 0 || a.K % 8 != 0) return fail(WM_ERR_INVALID_ARG, "tcgen05 GEMM needs K > 0 and K % 8 == 0");
-#define WM_GEMM_CASE(BNV)                                                      \
-  switch (a.epi) {                                                             \
-    case EPI_STORE: return tc::launch_one<BNV, EPI_STORE>(a, s);               \
-    case EPI_GELU: return tc::launch_one<BNV, EPI_GELU>(a, s);                 \
-    case EPI_RESID_F32: return tc::launch_one<BNV, EPI_RESID_F32>(a, s);       \
-    case EPI_STORE_F32: return tc::launch_one<BNV, EPI_STORE_F32>(a, s);       \
-    default: return fail(WM_ERR_INVALID_ARG, "unknown GEMM epilogue");         \
-  }
-  if (a.bn == 256) {
-    WM_GEMM_CASE(256)
-  } else if (a.bn == 128) {
-    WM_GEMM_CASE(128)
-  }
-#undef WM_GEMM_CASE
+  if (a.K <= 0 || a.K % (a.f8 ? 16 : 8) != 0) return fail(WM_ERR_INVALID_ARG, "tcgen05 GEMM needs K > 0 and 16-byte rows");
+  if (a.bn == 256) return tc::launch_bn<256>(a, s);
+  if (a.bn == 128) return tc::launch_bn<128>(a, s);
   return fail(WM_ERR_INVALID_ARG, "GEMM tile width must be 128 or 256");
 }
 
@@ -421,6 +478,30 @@ static EncodeTiledFn encode_fn() {
       fn = reinterpret_cast<EncodeTiledFn>(p);
   }
   return fn;
+}
+
+bool make_tmap_e4m3(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || rows == 0 || cols == 0 || cols % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols};
+  cuuint32_t box[2] = {128, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool make_tmap_out_e4m3(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || rows == 0 || cols == 0 || cols % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool make_tmap_out(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, bool f32) {

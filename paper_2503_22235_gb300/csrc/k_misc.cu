@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cuda_fp8.h>
+
 #include "wm_internal.cuh"
 
 namespace wm {
@@ -81,6 +83,20 @@ wm_status launch_f32_to_bf16(const float* in, __nv_bfloat16* out, size_t n, cuda
   if (!n) return WM_OK;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 8);
   f32_to_bf16_kernel<<<blocks, 256, 0, s>>>(in, out, n);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+__global__ void f32_to_e4m3_kernel(const float* __restrict__ in, uint8_t* __restrict__ out, size_t n,
+                                   float inv_scale) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (uint8_t)(__nv_cvt_float2_to_fp8x2(make_float2(in[i] * inv_scale, 0.f), __NV_SATFINITE, __NV_E4M3) & 0xFF);
+}
+
+wm_status launch_f32_to_e4m3(const float* in, uint8_t* out, size_t n, float inv_scale, cudaStream_t s) {
+  if (!n) return WM_OK;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 8);
+  f32_to_e4m3_kernel<<<blocks, 256, 0, s>>>(in, out, n, inv_scale);
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }

@@ -35,6 +35,7 @@ enum Epilogue : int {
   EPI_GELU = 1,        // out = GELU(acc + bias)
   EPI_RESID_F32 = 2,   // out(float) += acc + bias
   EPI_STORE_F32 = 3,   // out(float) = acc + bias
+  EPI_GELU_F8 = 4,     // out(e4m3) = GELU(alpha * acc + bias) * out_scale, RNE, saturating
 };
 
 int num_sms();
@@ -48,6 +49,9 @@ wm_status prepare_na_bf16();
 // ------------------------------------------------------- fp32 plain path ----
 wm_status launch_layernorm(const float* x, const float* g, const float* b, void* out, bool out_bf16, int M,
                            int C, float eps, cudaStream_t s);
+// LayerNorm with e4m3 output: out = e4m3(LN(x) * inv_scale), RNE, saturating.
+wm_status launch_layernorm_e4m3(const float* x, const float* g, const float* b, uint8_t* out, int M, int C,
+                                float eps, float inv_scale, cudaStream_t s);
 wm_status launch_sgemm(const float* A, const float* W, const float* bias, float* out, int M, int N, int K,
                        int epi, cudaStream_t s);
 wm_status launch_na_f32(const float* qkv, float* out, int B, int D, int H, int W, int C, int heads, int kd,
@@ -62,14 +66,23 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t 
 // box 32 x 32, 64-byte (bf16) / 128-byte (fp32) swizzle.
 bool make_tmap_out(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, bool f32);
 
+// TMA descriptors for e4m3 (byte) matrices: operand [rows, cols] with box
+// box_rows x 128 columns and the 128-byte swizzle; output with box 32 x 32 and
+// the 32-byte swizzle.
+bool make_tmap_e4m3(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+bool make_tmap_out_e4m3(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols);
+
 struct GemmArgs {
-  CUtensorMap tmA;     // A [M, K] bf16, box 128 x 64
-  CUtensorMap tmB;     // W [N, K] bf16, box BN x 64
-  CUtensorMap tmC;     // output [M, N]: bf16 for EPI_STORE / EPI_GELU, fp32 otherwise (make_tmap_out)
+  CUtensorMap tmA;     // A [M, K], box 128 rows x 128 bytes
+  CUtensorMap tmB;     // W [N, K], box BN rows x 128 bytes
+  CUtensorMap tmC;     // output [M, N]: bf16 (EPI_STORE / EPI_GELU), e4m3 (EPI_GELU_F8), fp32 otherwise
   int M, N, K;
   const float* bias;
   int epi;
   int bn;              // 128 or 256 (tmB box rows must match)
+  bool f8 = false;     // A and W are e4m3 (kind::f8f6f4); otherwise bf16 (kind::f16)
+  float alpha = 1.f;   // e4m3 only: accumulator scale (product of the operand scales)
+  float out_scale = 1.f;  // EPI_GELU_F8: 1 / output scale
 };
 wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
 
@@ -82,6 +95,7 @@ wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, 
 
 // ---------------------------------------------------------------- misc ----
 wm_status launch_f32_to_bf16(const float* in, __nv_bfloat16* out, size_t n, cudaStream_t s);
+wm_status launch_f32_to_e4m3(const float* in, uint8_t* out, size_t n, float inv_scale, cudaStream_t s);
 wm_status launch_sqdiff(const float* a, const float* b, size_t n, double* acc2, cudaStream_t s);
 wm_status launch_wait_selftest(int timeout_us, cudaStream_t s);
 

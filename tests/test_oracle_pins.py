@@ -373,3 +373,31 @@ def test_e4m3_round_matches_torch_in_range():
                         rng.standard_normal(5000) * 1e-3])
     ref = torch.from_numpy(x.astype(np.float32)).to(torch.float8_e4m3fn).double().numpy()
     assert np.array_equal(orc.e4m3_round(x.astype(np.float32)), ref)
+
+
+# ------------------------------------------------------------ FP8 MLP ---
+
+def test_fp8_scale_bounds_hold_and_are_reached_by_an_outlier():
+    C = 64
+    w = synth.block_weights(C, 0, 0, 0, stress=True)
+    s_u, s_w1, s_h, s_w2 = orc.fp8_mlp_scales(w, C)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((400, C)) * rng.uniform(0.1, 50, (400, 1))
+    x[0] = 0.0
+    x[0, 7] = 1e4                       # one-hot row: |x_c - mean| / std = sqrt(C - 1) at c = 7
+    u = orc.layer_norm(x, w["ln2_g"], w["ln2_b"], 0.0)
+    assert np.abs(u).max() <= s_u * 448.0 * (1 + 1e-12)
+    assert np.abs(u[0, 7]) >= 0.5 * s_u * 448.0
+    h = orc.gelu(orc.linear(u, w["w1"], w["b1"]))
+    assert np.abs(h).max() <= s_h * 448.0 * (1 + 1e-12)
+    assert s_w1 * 448.0 == np.abs(w["w1"]).max() and s_w2 * 448.0 == np.abs(w["w2"]).max()
+
+
+def test_fp8_block_without_rounding_is_the_block():
+    x = synth.latent(TINY, 1, seed=9)
+    w = synth.block_weights(TINY.C, 0, 0, 1, stress=True)
+    same = orc.block_fp8mlp(x, w, TINY, rounding=lambda v: v)
+    assert np.max(np.abs(same - orc.block(x, w, TINY))) < 1e-12
+    q = orc.block_fp8mlp(x, w, TINY)
+    err = orc.rel_l2(q, orc.block(x, w, TINY))
+    assert 1e-4 < err < 5e-2     # E4M3 keeps 3 mantissa bits
