@@ -323,6 +323,9 @@ def run_ours(args):
     if not args.no_rollout:
         out["rollout_14d_small"] = small_rollout(wm, torch, dev)
 
+    if not args.no_batch:
+        out["batch_uneven_small"] = batch_bench(wm, torch, dev)
+
     if not args.no_serve and rank == 0:
         out["serve"] = serve_bench(wm, torch, n_requests=args.serve_requests)
 
@@ -360,6 +363,44 @@ def small_rollout(wm, torch, dev, reps=3):
                 finals[(name, T)] = x.clone()
         for T in (336, 337):
             res[f"bf16_vs_fp32_final_rel_l2_T{T}"] = wm.wm_rel_l2(finals[("bf16", T)], finals[("fp32", T)])
+    finally:
+        wm.wm_destroy(ctx)
+    return res
+
+
+def batch_bench(wm, torch, dev, reps=3):
+    """Eight small latents with uneven leads advanced together (wm_rollout_batch,
+    one captured graph): forecasts/s per precision and each lead's error
+    against the FP32 plain path."""
+    s = synth.SMALL
+    leads = [1, 6, 7, 24, 72, 120, 240, 336]
+    p6, p1 = synth.processor_weights(s, seed=0)
+    x0 = [torch.from_numpy(synth.latent(s, 1, seed=1 + i)).to(dev) for i in range(len(leads))]
+    ctx = wm.wm_create_from_host(wm.make_config(s, wm.WM_PREC_BF16, max_batch=len(leads)),
+                                 synth.pack_weights(p6, p1))
+    res = {"workload": "8 latents 4x24x48x128, leads {1,6,7,24,72,120,240,336} h, 1080 blocks, one graph"}
+    outs = {}
+    try:
+        for prec, name in ((wm.WM_PREC_BF16_FP8MLP, "fp8mlp"), (wm.WM_PREC_BF16, "bf16"), (wm.WM_PREC_FP32, "fp32")):
+            wm.wm_set_precision(ctx, prec)
+            lat = [x.clone() for x in x0]
+            wm.wm_rollout_batch(ctx, lat, leads)        # capture + first replay
+            torch.cuda.synchronize()
+            total = 0.0
+            for _ in range(reps):
+                for a, b in zip(lat, x0):
+                    a.copy_(b)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                wm.wm_rollout_batch(ctx, lat, leads)
+                e1.record()
+                torch.cuda.synchronize()
+                total += e0.elapsed_time(e1)
+            res[f"{name}_forecasts_per_s"] = len(leads) * reps / (total / 1e3)
+            outs[name] = [t.clone() for t in lat]
+        for name in ("fp8mlp", "bf16"):
+            res[f"{name}_vs_fp32_rel_l2_by_lead"] = {str(t): wm.wm_rel_l2(a, b)
+                                                     for t, a, b in zip(leads, outs[name], outs["fp32"])}
     finally:
         wm.wm_destroy(ctx)
     return res
@@ -453,6 +494,7 @@ def main():
     ap.add_argument("--no-rollout", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=120)
     args = ap.parse_args()
     if args.impl == "reference":
