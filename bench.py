@@ -317,6 +317,7 @@ def run_ours(args):
         nbytes = hin.numel() * 4
         out["e2e"] = {"value": ws * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                       "d2h_bytes_per_step": nbytes, "call": "wm_forecast_host(lead 6 h)"}
+    out["autotune"] = wm.wm_autotune_report().strip().splitlines()
     wm.wm_destroy(ctx)
 
     # ---------------- 14-day rollout on the small latent (whole rollout as one CUDA graph)

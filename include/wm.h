@@ -102,6 +102,11 @@ wm_status wm_ctx_sizes(wm_ctx* ctx, int batch, size_t* latent_floats, size_t* wo
  * so that later calls, and graph captures, allocate nothing. */
 wm_status wm_ctx_reserve(wm_ctx* ctx, int batch);
 
+/* The tile plans the autotuner chose so far in this process (text, one line
+ * per shape, NUL-terminated, truncated to len - 1 bytes). The attention
+ * kernel's plans are timed when a context's BF16 workspace is allocated. */
+wm_status wm_autotune_report(char* buf, size_t len);
+
 /* ----------------------------------------------------------- compute ---- */
 
 /* One block (index `block` of processor `which`) applied in place to

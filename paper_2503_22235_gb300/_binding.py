@@ -55,6 +55,7 @@ _SIGS = {
     "wm_timing_end": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
     "wm_ctx_sizes": (_c_int, [_vp, _c_int, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "wm_ctx_reserve": (_c_int, [_vp, _c_int]),
+    "wm_autotune_report": (_c_int, [ctypes.c_char_p, _sz]),
     "wm_server_start": (_c_int, [_vp, _sz, _c_int, ctypes.POINTER(_vp)]),
     "wm_server_submit": (_c_int, [_vp, _vp, _c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "wm_server_poll": (_c_int, [_vp, ctypes.c_uint64, _vp, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_double)]),
@@ -211,6 +212,12 @@ def wm_ctx_sizes(ctx, batch=1) -> tuple[int, int]:
     lat, ws = _sz(), _sz()
     _check(lib().wm_ctx_sizes(ctx, int(batch), ctypes.byref(lat), ctypes.byref(ws)))
     return lat.value, ws.value
+
+
+def wm_autotune_report() -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().wm_autotune_report(buf, len(buf)))
+    return buf.value.decode()
 
 
 def wm_ctx_reserve(ctx, batch):

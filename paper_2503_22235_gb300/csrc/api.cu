@@ -634,6 +634,15 @@ wm_status wm_ctx_sizes(wm_ctx* ctx, int batch, size_t* latent_floats, size_t* wo
   return WM_OK;
 }
 
+wm_status wm_autotune_report(char* buf, size_t len) {
+  if (!buf || len == 0) return fail(WM_ERR_INVALID_ARG, "bad report buffer");
+  const std::string r = wm::describe_na_plans();
+  const size_t n = std::min(len - 1, r.size());
+  std::memcpy(buf, r.data(), n);
+  buf[n] = 0;
+  return WM_OK;
+}
+
 wm_status wm_ctx_reserve(wm_ctx* ctx, int batch) {
   if (!ctx || batch < 1) return fail(WM_ERR_INVALID_ARG, "bad reserve arguments");
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);

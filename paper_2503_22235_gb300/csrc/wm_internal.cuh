@@ -88,6 +88,8 @@ wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
 
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
                          int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s);
+// One line per autotuned attention shape: the plan chosen and its time.
+std::string describe_na_plans();
 // Times the candidate CTA plans of the attention kernel for this exact shape
 // and keeps the fastest for later launch_na_bf16 calls (writes `out`).
 wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
