@@ -31,6 +31,11 @@ struct BlockW {
   const float *ln1_g, *ln1_b, *wqkv, *bqkv, *wo, *bo, *ln2_g, *ln2_b, *w1, *b1, *w2, *b2;
   bf16 *hqkv, *ho, *h1, *h2;
   CUtensorMap tm_qkv[2], tm_o[2], tm_1[2], tm_2[2];  // [0]: box 128 rows, [1]: box 256 rows
+  // LayerNorm folded into QKV and FC1: bf16 W diag(gamma), its column sums,
+  // and the folded bias b + W beta
+  bf16 *fqkv, *f1;
+  const float *cs_qkv, *bb_qkv, *cs_1, *bb_1;
+  CUtensorMap tm_fqkv[2], tm_f1[2];
   // FP8 MLP: e4m3 copies of W1, W2 and the static per-tensor scales
   uint8_t *q1, *q2;
   CUtensorMap tm_q1[2], tm_q2[2];
@@ -46,6 +51,8 @@ struct wm_ctx {
   float* d_w32 = nullptr;
   bf16* d_wh = nullptr;
   uint8_t* d_wq = nullptr;   // e4m3 W1, W2 per block
+  bf16* d_wf = nullptr;      // LayerNorm-folded bf16 Wqkv, W1 per block
+  float* d_vf = nullptr;     // their column sums and folded biases
   std::vector<BlockW> blk[2];
   // workspace for cap32 (FP32 path) / cap16 (BF16 path) latents
   int cap32 = 0, cap16 = 0;
@@ -53,6 +60,10 @@ struct wm_ctx {
   bf16 *h_u = nullptr, *h_qkv = nullptr, *h_o = nullptr, *h_h = nullptr;
   uint8_t *q_u = nullptr, *q_h = nullptr;   // e4m3 MLP operands (FP8 MLP precision)
   CUtensorMap tm_qu{}, tm_qh{}, tmc_qh{};
+  bf16* xb = nullptr;        // bf16 copy of the residual, A operand of the folded GEMMs
+  float* stats = nullptr;    // per-row (mean, M2) partials feeding the folded GEMMs
+  CUtensorMap tm_xb{}, tmc_xb{};
+  int np_next = 0;           // partials per row the last residual GEMM left in `stats`
   CUtensorMap tm_u{}, tm_o{}, tm_h{};
   CUtensorMap tmc_qkv{}, tmc_h{};   // GEMM outputs (TMA store descriptors)
   // staging
@@ -112,6 +123,9 @@ void free_workspace(wm_ctx* ctx) {
   cudaFree(ctx->h_u); cudaFree(ctx->h_qkv); cudaFree(ctx->h_o); cudaFree(ctx->h_h);
   cudaFree(ctx->q_u); cudaFree(ctx->q_h);
   ctx->q_u = ctx->q_h = nullptr;
+  cudaFree(ctx->xb); cudaFree(ctx->stats);
+  ctx->xb = nullptr;
+  ctx->stats = nullptr;
   ctx->f_u = ctx->f_qkv = ctx->f_o = ctx->f_h = nullptr;
   ctx->h_u = ctx->h_qkv = ctx->h_o = ctx->h_h = nullptr;
   ctx->cap32 = ctx->cap16 = 0;
@@ -151,7 +165,19 @@ wm_status ensure_workspace(wm_ctx* ctx, int batch, bool fp32) {
   if (!fp32) {
     cudaFree(ctx->q_u);
     cudaFree(ctx->q_h);
+    cudaFree(ctx->xb);
+    cudaFree(ctx->stats);
     ctx->q_u = ctx->q_h = nullptr;
+    ctx->xb = nullptr;
+    ctx->stats = nullptr;
+    const size_t np_max = 2 * ((C + 127) / 128);
+    if (cudaMalloc(&ctx->xb, M * C * 2) != cudaSuccess || cudaMalloc(&ctx->stats, M * np_max * 2 * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(WM_ERR_OOM, "LayerNorm statistics workspace allocation failed");
+    }
+    if (C % 8 == 0 && (!wm::make_tmap_bf16(&ctx->tm_xb, ctx->xb, M, C, 128) ||
+                       !wm::make_tmap_out(&ctx->tmc_xb, ctx->xb, M, C, false)))
+      return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the residual copy");
     if (cudaMalloc(&ctx->q_u, M * C) != cudaSuccess || cudaMalloc(&ctx->q_h, M * 4 * C) != cudaSuccess) {
       cudaGetLastError();
       return fail(WM_ERR_OOM, "e4m3 workspace allocation failed");
@@ -203,18 +229,6 @@ int pick_bn(long M, int N) {
   return 128;
 }
 
-wm_status gemm_bf16(const CUtensorMap& tmA, const CUtensorMap* tmB2, const CUtensorMap& tmC, long M, int N, int K,
-                    const float* bias, int epi, cudaStream_t s) {
-  wm::GemmArgs a;
-  a.bn = pick_bn(M, N);
-  a.tmA = tmA;
-  a.tmB = tmB2[a.bn == 256 ? 1 : 0];
-  a.tmC = tmC;
-  a.M = (int)M; a.N = N; a.K = K;
-  a.bias = bias; a.epi = epi;
-  return wm::launch_gemm_tc(a, s);
-}
-
 // ---- optional per-launch timing: an event pair around each hot-path kernel
 struct TimedLaunch {
   wm_ctx* ctx;
@@ -233,7 +247,7 @@ struct TimedLaunch {
   }
 };
 
-wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, cudaStream_t s) {
+wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool first, cudaStream_t s) {
   const wm_config& c = ctx->cfg;
   const BlockW& w = ctx->blk[which][b];
   const long M = (long)batch * ctx->N;
@@ -256,48 +270,86 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, cuda
       WM_TRY(wm::launch_sgemm(ctx->f_h, w.w2, w.b2, x, (int)M, C, 4 * C, wm::EPI_RESID_F32, s)); }
     return WM_OK;
   }
-  CUtensorMap tm_x;   // the caller's latent as the residual-add target
+  CUtensorMap tm_x;   // the caller's latent as the residual target
   if (!wm::make_tmap_out(&tm_x, x, (uint64_t)M, (uint64_t)C, true))
     return fail(WM_ERR_INVALID_ARG, "latent pointer must be 16-byte aligned for the BF16 path");
-  { TimedLaunch t(ctx, WM_K_LN1, s);
-    WM_TRY(wm::launch_layernorm(x, w.ln1_g, w.ln1_b, ctx->h_u, true, (int)M, C, c.ln_eps, s)); }
-  { TimedLaunch t(ctx, WM_K_QKV, s);
-    WM_TRY(gemm_bf16(ctx->tm_u, w.tm_qkv, ctx->tmc_qkv, M, 3 * C, C, w.bqkv, wm::EPI_STORE, s)); }
+  const bool fp8 = c.precision == WM_PREC_BF16_FP8MLP;
+  // LayerNorm 1, folded into the QKV GEMM. Its row statistics come from the
+  // previous block's FC2 epilogue, or from one statistics pass for the first
+  // block of a processor call.
+  if (first) {
+    TimedLaunch t(ctx, WM_K_LN1, s);
+    WM_TRY(wm::launch_row_stats(x, ctx->xb, ctx->stats, (int)M, C, s));
+    ctx->np_next = 1;
+  }
+  wm::GemmArgs a;
+  a.M = (int)M;
+  a.K = C;
+  a.N = 3 * C;
+  a.bn = pick_bn(M, a.N);
+  a.tmA = ctx->tm_xb; a.tmB = w.tm_fqkv[a.bn == 256]; a.tmC = ctx->tmc_qkv;
+  a.bias = w.bb_qkv; a.colsum = w.cs_qkv; a.stats = ctx->stats; a.np = ctx->np_next; a.eps = c.ln_eps;
+  a.epi = wm::EPI_LNF_STORE;
+  { TimedLaunch t(ctx, WM_K_QKV, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
   { TimedLaunch t(ctx, WM_K_ATTN, s);
     WM_TRY(wm::launch_na_bf16(ctx->h_qkv, ctx->h_o, batch, c.D, c.H, c.W, C, c.heads, c.kd, c.kh, c.kw, per, s)); }
-  { TimedLaunch t(ctx, WM_K_PROJ, s);
-    WM_TRY(gemm_bf16(ctx->tm_o, w.tm_o, tm_x, M, C, C, w.bo, wm::EPI_RESID_F32, s)); }
-  if (c.precision == WM_PREC_BF16_FP8MLP) {
+  // output projection + residual; in BF16 it also leaves LayerNorm 2's statistics
+  a = wm::GemmArgs();
+  a.M = (int)M; a.K = C; a.N = C;
+  a.bn = pick_bn(M, a.N);
+  a.tmA = ctx->tm_o; a.tmB = w.tm_o[a.bn == 256]; a.tmC = tm_x;
+  a.bias = w.bo;
+  if (fp8) {
+    a.epi = wm::EPI_RESID_F32;
+  } else {
+    a.epi = wm::EPI_RESID_LN; a.tmC2 = ctx->tmc_xb; a.x = x; a.stats = ctx->stats;
+  }
+  { TimedLaunch t(ctx, WM_K_PROJ, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+  const int np2 = 2 * ((C + a.bn - 1) / a.bn);
+  if (fp8) {
     // MLP in e4m3 with static per-tensor scales: u2 / s_u and W1 / s_w1 into
     // FC1 (alpha = s_u s_w1), GELU output / s_h and W2 / s_w2 into FC2
     { TimedLaunch t(ctx, WM_K_LN2, s);
       WM_TRY(wm::launch_layernorm_e4m3(x, w.ln2_g, w.ln2_b, ctx->q_u, (int)M, C, c.ln_eps, 1.f / w.s_u, s)); }
-    wm::GemmArgs a;
+    a = wm::GemmArgs();
     a.f8 = true;
     a.M = (int)M; a.K = C; a.N = 4 * C;
     a.bn = pick_bn(M, a.N);
     a.tmA = ctx->tm_qu; a.tmB = w.tm_q1[a.bn == 256]; a.tmC = ctx->tmc_qh;
     a.bias = w.b1; a.epi = wm::EPI_GELU_F8; a.alpha = w.s_u * w.s_w1; a.out_scale = 1.f / w.s_h;
     { TimedLaunch t(ctx, WM_K_FC1, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
-    a.K = 4 * C; a.N = C;
+    a = wm::GemmArgs();
+    a.f8 = true;
+    a.M = (int)M; a.K = 4 * C; a.N = C;
     a.bn = pick_bn(M, a.N);
-    a.tmA = ctx->tm_qh; a.tmB = w.tm_q2[a.bn == 256]; a.tmC = tm_x;
-    a.bias = w.b2; a.epi = wm::EPI_RESID_F32; a.alpha = w.s_h * w.s_w2; a.out_scale = 1.f;
+    a.tmA = ctx->tm_qh; a.tmB = w.tm_q2[a.bn == 256]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
+    a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.alpha = w.s_h * w.s_w2; a.x = x; a.stats = ctx->stats;
     { TimedLaunch t(ctx, WM_K_FC2, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+    ctx->np_next = 2 * ((C + a.bn - 1) / a.bn);
     return WM_OK;
   }
-  { TimedLaunch t(ctx, WM_K_LN2, s);
-    WM_TRY(wm::launch_layernorm(x, w.ln2_g, w.ln2_b, ctx->h_u, true, (int)M, C, c.ln_eps, s)); }
-  { TimedLaunch t(ctx, WM_K_FC1, s);
-    WM_TRY(gemm_bf16(ctx->tm_u, w.tm_1, ctx->tmc_h, M, 4 * C, C, w.b1, wm::EPI_GELU, s)); }
-  { TimedLaunch t(ctx, WM_K_FC2, s);
-    WM_TRY(gemm_bf16(ctx->tm_h, w.tm_2, tm_x, M, C, 4 * C, w.b2, wm::EPI_RESID_F32, s)); }
+  // LayerNorm 2 folded into FC1 (+ GELU)
+  a = wm::GemmArgs();
+  a.M = (int)M; a.K = C; a.N = 4 * C;
+  a.bn = pick_bn(M, a.N);
+  a.tmA = ctx->tm_xb; a.tmB = w.tm_f1[a.bn == 256]; a.tmC = ctx->tmc_h;
+  a.bias = w.bb_1; a.colsum = w.cs_1; a.stats = ctx->stats; a.np = np2; a.eps = c.ln_eps;
+  a.epi = wm::EPI_LNF_GELU;
+  { TimedLaunch t(ctx, WM_K_FC1, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+  // FC2 + residual, leaving the next block's LayerNorm-1 statistics
+  a = wm::GemmArgs();
+  a.M = (int)M; a.K = 4 * C; a.N = C;
+  a.bn = pick_bn(M, a.N);
+  a.tmA = ctx->tm_h; a.tmB = w.tm_2[a.bn == 256]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
+  a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.x = x; a.stats = ctx->stats;
+  { TimedLaunch t(ctx, WM_K_FC2, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+  ctx->np_next = 2 * ((C + a.bn - 1) / a.bn);
   return WM_OK;
 }
 
 wm_status processor_step(wm_ctx* ctx, float* x, int batch, int which, cudaStream_t s) {
   const int L = which == WM_P6 ? ctx->cfg.blocks_p6 : ctx->cfg.blocks_p1;
-  for (int b = 0; b < L; ++b) WM_TRY(block_forward(ctx, x, batch, which, b, s));
+  for (int b = 0; b < L; ++b) WM_TRY(block_forward(ctx, x, batch, which, b, b == 0, s));
   return WM_OK;
 }
 
@@ -341,6 +393,39 @@ wm_status run_graph(wm_ctx* ctx, const std::vector<uintptr_t>& key, cudaStream_t
   return WM_OK;
 }
 
+// IEEE round-to-nearest-even of a float to bfloat16 (bit pattern).
+uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float bf16_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// LayerNorm folded into a linear layer W [N, C] with bias b:
+//   LN(x) W^T + b = rstd (x W'^T - mean colsum(W')) + (b + W beta),  W' = W diag(gamma).
+// Writes bf16(W') and, from those rounded values, colsum; and b + W beta.
+void fold_layernorm(const float* W, const float* b, const float* gamma, const float* beta, size_t N, size_t C,
+                    uint16_t* wf, float* colsum, float* bias) {
+  for (size_t n = 0; n < N; ++n) {
+    double cs = 0.0, bb = b[n];
+    for (size_t k = 0; k < C; ++k) {
+      const uint16_t q = bf16_bits(W[n * C + k] * gamma[k]);
+      wf[n * C + k] = q;
+      cs += bf16_value(q);
+      bb += (double)W[n * C + k] * beta[k];
+    }
+    colsum[n] = (float)cs;
+    bias[n] = (float)bb;
+  }
+}
+
 wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
   const wm_config& c = ctx->cfg;
   const int nb = c.blocks_p6 + c.blocks_p1;
@@ -353,6 +438,10 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
   const size_t mats = 12 * C * C;  // wqkv + wo + w1 + w2 per block
   WM_CUDA(cudaMalloc(&ctx->d_wh, mats * nb * 2));
   WM_CUDA(cudaMalloc(&ctx->d_wq, 8 * C * C * nb));
+  WM_CUDA(cudaMalloc(&ctx->d_wf, 7 * C * C * nb * 2));
+  WM_CUDA(cudaMalloc(&ctx->d_vf, 14 * C * nb * 4));
+  std::vector<uint16_t> hf(7 * C * C);
+  std::vector<float> hv(14 * C);
   for (int i = 0; i < nb; ++i) {
     const int which = i < c.blocks_p6 ? 0 : 1;
     const float* p = ctx->d_w32 + per * i;
@@ -410,6 +499,37 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
       w.s_w1 = (float)(std::max(aw1, 1e-30) / 448.0);
       w.s_h = (float)(bh / 448.0);
       w.s_w2 = (float)(std::max(aw2, 1e-30) / 448.0);
+    }
+    {
+      const float* hp = host + per * i;
+      const float* g1 = hp;
+      const float* be1 = hp + C;
+      const float* hqkv = hp + 2 * C;
+      const float* hbqkv = hqkv + 3 * C * C;
+      const float* g2 = hp + 6 * C + 4 * C * C;
+      const float* be2 = g2 + C;
+      const float* hw1 = be2 + C;
+      const float* hb1 = hw1 + 4 * C * C;
+      fold_layernorm(hqkv, hbqkv, g1, be1, 3 * C, C, hf.data(), hv.data(), hv.data() + 3 * C);
+      fold_layernorm(hw1, hb1, g2, be2, 4 * C, C, hf.data() + 3 * C * C, hv.data() + 6 * C, hv.data() + 10 * C);
+      w.fqkv = ctx->d_wf + 7 * C * C * i;
+      w.f1 = w.fqkv + 3 * C * C;
+      float* v = ctx->d_vf + 14 * C * i;
+      w.cs_qkv = v;
+      w.bb_qkv = v + 3 * C;
+      w.cs_1 = v + 6 * C;
+      w.bb_1 = v + 10 * C;
+      WM_CUDA(cudaMemcpy(w.fqkv, hf.data(), 7 * C * C * 2, cudaMemcpyHostToDevice));
+      WM_CUDA(cudaMemcpy(v, hv.data(), 14 * C * 4, cudaMemcpyHostToDevice));
+      if (C % 8 == 0) {
+        bool ok = true;
+        for (int k = 0; k < 2; ++k) {
+          const uint32_t box = k ? 256 : 128;
+          ok = ok && wm::make_tmap_bf16(&w.tm_fqkv[k], w.fqkv, 3 * C, C, box);
+          ok = ok && wm::make_tmap_bf16(&w.tm_f1[k], w.f1, 4 * C, C, box);
+        }
+        if (!ok) return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the folded weights");
+      }
     }
     w.q1 = ctx->d_wq + 8 * C * C * i;
     w.q2 = w.q1 + 4 * C * C;
@@ -511,6 +631,8 @@ wm_status wm_destroy(wm_ctx* ctx) {
   cudaFree(ctx->d_w32);
   cudaFree(ctx->d_wh);
   cudaFree(ctx->d_wq);
+  cudaFree(ctx->d_wf);
+  cudaFree(ctx->d_vf);
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_io);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -533,7 +655,7 @@ wm_status wm_block_forward(wm_ctx* ctx, float* latent, int batch, int which, int
   if (block < 0 || block >= (int)ctx->blk[which].size()) return fail(WM_ERR_INVALID_ARG, "block index out of range");
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   WM_TRY(ensure_workspace(ctx, batch));
-  return block_forward(ctx, latent, batch, which, block, (cudaStream_t)stream);
+  return block_forward(ctx, latent, batch, which, block, true, (cudaStream_t)stream);
 }
 
 wm_status wm_processor_step(wm_ctx* ctx, float* latent, int batch, int which, void* stream) {

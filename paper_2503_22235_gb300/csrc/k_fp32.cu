@@ -89,6 +89,59 @@ __global__ void ln_rows_generic(const float* __restrict__ x, const float* __rest
   for (int c = lane; c < C; c += 32) store_val(out + row * C + c, (xr[c] - mean) * rstd * g[c] + b[c]);
 }
 
+// Row statistics: one warp per row, (mean, M2) in FP32 from the row held in
+// registers, plus the bf16 copy of the row.
+template <int V4>
+__global__ void row_stats_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ xb, float* __restrict__ st,
+                                 int M) {
+  const int C = 128 * V4;
+  const int lane = threadIdx.x & 31;
+  const long row = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= M) return;
+  const float4* xr = reinterpret_cast<const float4*>(x + row * C);
+  float4 v[V4];
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < V4; ++i) {
+    v[i] = xr[lane + 32 * i];
+    s += (v[i].x + v[i].y) + (v[i].z + v[i].w);
+  }
+  const float mean = warp_sum(s) / C;
+  float q = 0.f;
+#pragma unroll
+  for (int i = 0; i < V4; ++i) {
+    float a = v[i].x - mean, bb = v[i].y - mean, c = v[i].z - mean, d = v[i].w - mean;
+    q += (a * a + bb * bb) + (c * c + d * d);
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[i].x, v[i].y), p1 = __floats2bfloat162_rn(v[i].z, v[i].w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t*>(&p0);
+    u.y = *reinterpret_cast<uint32_t*>(&p1);
+    *reinterpret_cast<uint2*>(xb + row * C + 4 * (lane + 32 * i)) = u;
+  }
+  const float m2 = warp_sum(q);
+  if (lane == 0) {
+    st[2 * row] = mean;
+    st[2 * row + 1] = m2;
+  }
+}
+
+wm_status launch_row_stats(const float* x, __nv_bfloat16* xb, float* stats, int M, int C, cudaStream_t s) {
+  if (M <= 0) return WM_OK;
+  const int warps = 8;
+  dim3 grid((M + warps - 1) / warps), block(32 * warps);
+  switch (C) {
+    case 128: row_stats_kernel<1><<<grid, block, 0, s>>>(x, xb, stats, M); break;
+    case 256: row_stats_kernel<2><<<grid, block, 0, s>>>(x, xb, stats, M); break;
+    case 384: row_stats_kernel<3><<<grid, block, 0, s>>>(x, xb, stats, M); break;
+    case 512: row_stats_kernel<4><<<grid, block, 0, s>>>(x, xb, stats, M); break;
+    case 768: row_stats_kernel<6><<<grid, block, 0, s>>>(x, xb, stats, M); break;
+    case 1024: row_stats_kernel<8><<<grid, block, 0, s>>>(x, xb, stats, M); break;
+    default: return fail(WM_ERR_INVALID_ARG, "row statistics need C in {128, 256, 384, 512, 768, 1024}");
+  }
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
 // LayerNorm rows to e4m3: one warp per row, FP32 statistics as above, output
 // e4m3(LN(x) * inv_scale) with round-to-nearest-even and saturation.
 template <int V4>

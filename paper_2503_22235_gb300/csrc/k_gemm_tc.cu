@@ -24,18 +24,18 @@ namespace wm {
 namespace tc {
 
 constexpr int BM = 128;
-constexpr int BK = 64;                 // bf16 elements per k-slice = one 128-byte swizzle row
 constexpr int BKB = 128;               // bytes per k-slice row (bf16: 64 elements, e4m3: 128)
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
 
-template <int BN>
+template <int BN, bool DUAL = false>   // DUAL: a second (bf16) staging tile per epilogue warp
 struct Cfg {
   static constexpr int A_BYTES = BM * BKB;
   static constexpr int B_BYTES = BN * BKB;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int STAGES = (BN >= 256) ? 4 : 6;
-  static constexpr int EPI_BYTES = NUM_EPI_WARPS * 4096;     // one 32x32 staging tile per epilogue warp
+  static constexpr int STAGES = (BN >= 256) ? (DUAL ? 3 : 4) : (DUAL ? 5 : 6);
+  static constexpr int EPI_STRIDE = DUAL ? 6144 : 4096;     // per epilogue warp: 32x32 fp32 (+ 32x32 bf16)
+  static constexpr int EPI_BYTES = NUM_EPI_WARPS * EPI_STRIDE;
   static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;   // + alignment slack
   static constexpr int TMEM_COLS = 2 * BN;                   // two accumulators
 };
@@ -149,7 +149,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+// GELU(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)) with erf from Abramowitz &
+// Stegun, Handbook of Mathematical Functions, formula 7.1.26 (Hastings):
+//   erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),
+//   t = 1 / (1 + p x), x >= 0, |error| <= 1.5e-7,
+// odd in x. Used for the bf16 / e4m3 outputs, whose rounding (>= 2^-9
+// relative) dwarfs that error; the reciprocal and 2^x run on the MUFU unit.
+__device__ __forceinline__ float gelu_erf(float z) {
+  const float x = fabsf(z) * 0.70710678118654752f;
+  float t;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, x, 1.f)));
+  float poly = fmaf(1.061405429f, t, -1.453152027f);
+  poly = fmaf(poly, t, 1.421413741f);
+  poly = fmaf(poly, t, -0.284496736f);
+  poly = fmaf(poly, t, 0.254829592f);
+  poly *= t;
+  float e;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-1.4426950408889634f * x * x));
+  const float erf_abs = fmaf(-poly, e, 1.f);
+  const float erf_z = copysignf(erf_abs, z);
+  return 0.5f * z * (1.f + erf_z);
+}
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
@@ -208,13 +228,17 @@ __device__ __forceinline__ void stage_row(uint8_t* buf, const float (&x)[32], in
   }
 }
 
-template <int BN, int EPI, bool F8>
+template <int BN, int EPI, bool F8, bool DUAL = false>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                        const __grid_constant__ CUtensorMap tmC, int M, int N, int K, const float* __restrict__ bias,
-                        float alpha, float out_scale, int* __restrict__ status) {
+                        const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmC2, int M,
+                        int N, int K, const EpiArgs e, int* __restrict__ status) {
+  const float* __restrict__ bias = e.bias;
+  const float alpha = e.alpha, out_scale = e.out_scale;
+  constexpr bool kResLN = (EPI == EPI_RESID_LN);
+  constexpr bool kLNF = (EPI == EPI_LNF_STORE || EPI == EPI_LNF_GELU);
   constexpr int BKE = F8 ? 128 : 64;     // elements per k-slice
-  using CF = Cfg<BN>;
+  using CF = Cfg<BN, DUAL>;
   constexpr int STAGES = CF::STAGES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
@@ -334,8 +358,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     // -------------------------------------------------------- epilogue
     const int quarter = warp & 3;                 // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;             // which half of the BN columns
-    uint8_t* ebuf = smem + STAGES * CF::STAGE_BYTES + (warp - 2) * 4096;
+    uint8_t* ebuf = smem + STAGES * CF::STAGE_BYTES + (warp - 2) * CF::EPI_STRIDE;
     const uint32_t ebuf32 = smem_u32(ebuf);
+    uint8_t* ebuf2 = ebuf + 4096;                 // EPI_RESID_LN: the bf16 copy's staging tile
+    const uint32_t ebuf2_32 = ebuf32 + 4096;
     int it = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
       const int buf = it & 1;
@@ -348,8 +374,40 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_after();
       const int m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
       const int row0 = m0 + quarter * 32;
+      const int m = row0 + lane;
       const uint32_t tbase = tmem_base + (uint32_t)(buf * BN) + ((uint32_t)(quarter * 32) << 16);
       const int c_begin = half * (BN / 2), c_end = (half + 1) * (BN / 2);
+      // LayerNorm folded into this GEMM: merge the row's partial (mean, M2)
+      // pairs (equal counts K / np each) into its mean and 1/sqrt(var + eps)
+      float ln_mean = 0.f, ln_rstd = 0.f;
+      if constexpr (kLNF) {
+        if (m < M) {
+          const float* st = e.stats + (size_t)m * e.np * 2;
+          float mu = 0.f;
+          for (int i = 0; i < e.np; ++i) mu += st[2 * i];
+          mu /= (float)e.np;
+          const float cnt = (float)K / (float)e.np;
+          float m2 = 0.f;
+          for (int i = 0; i < e.np; ++i) {
+            const float d = st[2 * i] - mu;
+            m2 += st[2 * i + 1] + cnt * d * d;
+          }
+          ln_mean = mu;
+          ln_rstd = rsqrtf(m2 / (float)K + e.eps);
+        }
+      }
+      // residual epilogue with row statistics: running Welford (count, mean, M2)
+      float wn = 0.f, wmean = 0.f, wm2 = 0.f;
+      float4 xa[kResLN ? 8 : 1];
+      if constexpr (kResLN) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xa[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row0 < M && m < M && n0 + c_begin < N) {
+          const float4* xo = reinterpret_cast<const float4*>(e.x + (size_t)m * N + n0 + c_begin);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xa[q] = xo[q];
+        }
+      }
 #pragma unroll 1
       for (int c = c_begin; c < c_end; c += 32) {
         float v[32];
@@ -362,16 +420,57 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         const int n = n0 + c;
         if (row0 >= M || n >= N) continue;   // whole chunk outside the output (warp-uniform)
+        float lcs[kLNF ? 32 : 1], lbb[kLNF ? 32 : 1];
+        if constexpr (kLNF) {   // column vectors of this chunk (N % 32 == 0 here)
+          const float4* c4 = reinterpret_cast<const float4*>(e.colsum + n);
+          const float4* b4 = reinterpret_cast<const float4*>(bias + n);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 a = __ldg(c4 + q), b = __ldg(b4 + q);
+            lcs[4 * q] = a.x; lcs[4 * q + 1] = a.y; lcs[4 * q + 2] = a.z; lcs[4 * q + 3] = a.w;
+            lbb[4 * q] = b.x; lbb[4 * q + 1] = b.y; lbb[4 * q + 2] = b.z; lbb[4 * q + 3] = b.w;
+          }
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           if constexpr (F8) v[j] *= alpha;
-          v[j] += (bias && n + j < N) ? __ldg(bias + n + j) : 0.f;
-          if constexpr (EPI == EPI_GELU || EPI == EPI_GELU_F8) v[j] = gelu_erf(v[j]);
+          if constexpr (kLNF) {
+            v[j] = fmaf(ln_rstd, fmaf(-ln_mean, lcs[j], v[j]), lbb[j]);
+          } else {
+            v[j] += (bias && n + j < N) ? __ldg(bias + n + j) : 0.f;
+          }
+          if constexpr (EPI == EPI_GELU || EPI == EPI_GELU_F8 || EPI == EPI_LNF_GELU) v[j] = gelu_erf(v[j]);
           if constexpr (EPI == EPI_GELU_F8) v[j] *= out_scale;
+        }
+        if constexpr (kResLN) {
+          // x_new = x_old + acc + bias (x_old loaded one chunk ahead), then the
+          // chunk's mean / M2 merged into the row's (Chan et al.)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            v[4 * q] += xa[q].x; v[4 * q + 1] += xa[q].y; v[4 * q + 2] += xa[q].z; v[4 * q + 3] += xa[q].w;
+          }
+          if (c + 32 < c_end && m < M) {
+            const float4* xo = reinterpret_cast<const float4*>(e.x + (size_t)m * N + n + 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xa[q] = xo[q];
+          }
+          float cs = 0.f;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) cs += v[j];
+          const float cm = cs * (1.f / 32.f);
+          float cq = 0.f;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) cq += (v[j] - cm) * (v[j] - cm);
+          const float nt = wn + 32.f, d = cm - wmean;
+          wmean += d * (32.f / nt);
+          wm2 += cq + d * d * (wn * 32.f / nt);
+          wn = nt;
         }
         if (lane == 0) bulk_wait_read_all();   // the previous chunk's store has left the staging tile
         __syncwarp();
-        stage_row<EPI>(ebuf, v, lane);
+        if constexpr (kResLN) stage_row<EPI_STORE_F32>(ebuf, v, lane);
+        else if constexpr (kLNF) stage_row<EPI_STORE>(ebuf, v, lane);
+        else stage_row<EPI>(ebuf, v, lane);
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
@@ -380,6 +479,29 @@ __global__ void __launch_bounds__(THREADS, 1)
           else
             tma_store_2d(&tmC, ebuf32, n, row0);
           bulk_commit();
+        }
+        if constexpr (kResLN) {
+          // the bf16 copy of x_new for the next LayerNorm-folded GEMM: its own
+          // staging tile (DUAL), or the fp32 one once its store has read it
+          if constexpr (!DUAL) {
+            if (lane == 0) bulk_wait_read_all();
+            __syncwarp();
+          }
+          stage_row<EPI_STORE>(DUAL ? ebuf2 : ebuf, v, lane);
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&tmC2, DUAL ? ebuf2_32 : ebuf32, n, row0);
+            bulk_commit();
+          }
+        }
+      }
+      if constexpr (kResLN) {
+        if (row0 < M && m < M && wn > 0.f) {
+          const int part = (n0 / BN) * 2 + half;
+          float* st = e.stats + ((size_t)m * (2 * num_n) + part) * 2;
+          st[0] = wmean;
+          st[1] = wm2;
         }
       }
     }
@@ -395,22 +517,30 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-template <int BN, int EPI, bool F8>
+template <int BN, int EPI, bool F8, bool DUAL = false>
 static wm_status launch_one(const GemmArgs& a, cudaStream_t s) {
-  using CF = Cfg<BN>;
-  auto kern = gemm_bf16_tc_kernel<BN, EPI, F8>;
+  using CF = Cfg<BN, DUAL>;
+  auto kern = gemm_bf16_tc_kernel<BN, EPI, F8, DUAL>;
   const int tiles = ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  kern<<<grid, THREADS, CF::SMEM, s>>>(a.tmA, a.tmB, a.tmC, a.M, a.N, a.K, a.bias, a.alpha, a.out_scale,
-                                       device_status_word());
+  EpiArgs e;
+  e.bias = a.bias;
+  e.colsum = a.colsum;
+  e.x = a.x;
+  e.stats = a.stats;
+  e.np = a.np;
+  e.eps = a.eps;
+  e.alpha = a.alpha;
+  e.out_scale = a.out_scale;
+  kern<<<grid, THREADS, CF::SMEM, s>>>(a.tmA, a.tmB, a.tmC, a.tmC2, a.M, a.N, a.K, e, device_status_word());
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
-template <int BN, int EPI, bool F8>
+template <int BN, int EPI, bool F8, bool DUAL = false>
 static wm_status set_attr() {
-  WM_CUDA(cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, EPI, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               Cfg<BN>::SMEM));
+  WM_CUDA(cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, EPI, F8, DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               Cfg<BN, DUAL>::SMEM));
   return WM_OK;
 }
 
@@ -422,9 +552,15 @@ static wm_status set_attrs_bn() {
   chk(set_attr<BN, EPI_GELU, false>());
   chk(set_attr<BN, EPI_RESID_F32, false>());
   chk(set_attr<BN, EPI_STORE_F32, false>());
+  chk(set_attr<BN, EPI_RESID_LN, false>());
+  chk(set_attr<BN, EPI_RESID_LN, false, true>());
+  chk(set_attr<BN, EPI_LNF_STORE, false>());
+  chk(set_attr<BN, EPI_LNF_GELU, false>());
   chk(set_attr<BN, EPI_GELU_F8, true>());
   chk(set_attr<BN, EPI_RESID_F32, true>());
   chk(set_attr<BN, EPI_STORE_F32, true>());
+  chk(set_attr<BN, EPI_RESID_LN, true>());
+  chk(set_attr<BN, EPI_RESID_LN, true, true>());
   return st;
 }
 
@@ -435,6 +571,9 @@ static wm_status launch_bn(const GemmArgs& a, cudaStream_t s) {
       case EPI_GELU_F8: return launch_one<BN, EPI_GELU_F8, true>(a, s);
       case EPI_RESID_F32: return launch_one<BN, EPI_RESID_F32, true>(a, s);
       case EPI_STORE_F32: return launch_one<BN, EPI_STORE_F32, true>(a, s);
+      case EPI_RESID_LN:
+        // short K: the epilogue dominates, give it a second staging tile (one stage fewer)
+        return a.K <= 1024 ? launch_one<BN, EPI_RESID_LN, true, true>(a, s) : launch_one<BN, EPI_RESID_LN, true>(a, s);
       default: return fail(WM_ERR_INVALID_ARG, "unsupported epilogue for the e4m3 GEMM");
     }
   }
@@ -443,6 +582,10 @@ static wm_status launch_bn(const GemmArgs& a, cudaStream_t s) {
     case EPI_GELU: return launch_one<BN, EPI_GELU, false>(a, s);
     case EPI_RESID_F32: return launch_one<BN, EPI_RESID_F32, false>(a, s);
     case EPI_STORE_F32: return launch_one<BN, EPI_STORE_F32, false>(a, s);
+    case EPI_RESID_LN:
+      return a.K <= 1024 ? launch_one<BN, EPI_RESID_LN, false, true>(a, s) : launch_one<BN, EPI_RESID_LN, false>(a, s);
+    case EPI_LNF_STORE: return launch_one<BN, EPI_LNF_STORE, false>(a, s);
+    case EPI_LNF_GELU: return launch_one<BN, EPI_LNF_GELU, false>(a, s);
     default: return fail(WM_ERR_INVALID_ARG, "unsupported epilogue for the bf16 GEMM");
   }
 }
@@ -457,6 +600,11 @@ wm_status prepare_gemm_tc() {
 
 wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0) return WM_OK;
+  if (a.epi == EPI_RESID_LN && (a.N % a.bn != 0 || !a.x || !a.stats))
+    return fail(WM_ERR_INVALID_ARG, "residual+statistics epilogue needs N % tile == 0, x and stats");
+  if ((a.epi == EPI_LNF_STORE || a.epi == EPI_LNF_GELU) &&
+      (!a.stats || !a.colsum || !a.bias || a.np < 1 || a.N % 32 != 0))
+    return fail(WM_ERR_INVALID_ARG, "LayerNorm-folded epilogue needs stats, colsum, bias, np >= 1, N % 32 == 0");
   if (a.K <= 0 || a.K % (a.f8 ? 16 : 8) != 0) return fail(WM_ERR_INVALID_ARG, "tcgen05 GEMM needs K > 0 and 16-byte rows");
   if (a.bn == 256) return tc::launch_bn<256>(a, s);
   if (a.bn == 128) return tc::launch_bn<128>(a, s);

@@ -36,6 +36,21 @@ enum Epilogue : int {
   EPI_RESID_F32 = 2,   // out(float) += acc + bias
   EPI_STORE_F32 = 3,   // out(float) = acc + bias
   EPI_GELU_F8 = 4,     // out(e4m3) = GELU(alpha * acc + bias) * out_scale, RNE, saturating
+  EPI_RESID_LN = 5,    // x(float) += acc + bias; also writes bf16(x) (tmC2) and per-row partial
+                       // (mean, M2) over each half tile into stats [M][2 * N/BN][2]
+  EPI_LNF_STORE = 6,   // LayerNorm folded: out(bf16) = rstd (acc - mean colsum) + bias, where mean
+                       // and rstd come from the np partials per row in stats
+  EPI_LNF_GELU = 7,    // as EPI_LNF_STORE, then GELU
+};
+
+struct EpiArgs {
+  const float* bias;
+  const float* colsum;  // LayerNorm-folded epilogues: per-column sum of the folded bf16 weights
+  float* x;             // EPI_RESID_LN: the fp32 residual (read, then rewritten through tmC)
+  float* stats;         // EPI_RESID_LN writes, EPI_LNF_* read
+  int np;               // EPI_LNF_*: partials per row
+  float eps;            // EPI_LNF_*: LayerNorm epsilon
+  float alpha, out_scale;
 };
 
 int num_sms();
@@ -50,6 +65,9 @@ wm_status prepare_na_bf16();
 wm_status launch_layernorm(const float* x, const float* g, const float* b, void* out, bool out_bf16, int M,
                            int C, float eps, cudaStream_t s);
 // LayerNorm with e4m3 output: out = e4m3(LN(x) * inv_scale), RNE, saturating.
+// Row statistics for the first LayerNorm-folded GEMM of a processor call:
+// xb = bf16(x) and stats[m] = (mean, M2) of row m (one partial per row).
+wm_status launch_row_stats(const float* x, __nv_bfloat16* xb, float* stats, int M, int C, cudaStream_t s);
 wm_status launch_layernorm_e4m3(const float* x, const float* g, const float* b, uint8_t* out, int M, int C,
                                 float eps, float inv_scale, cudaStream_t s);
 wm_status launch_sgemm(const float* A, const float* W, const float* bias, float* out, int M, int N, int K,
@@ -75,9 +93,15 @@ bool make_tmap_out_e4m3(CUtensorMap* map, const void* base, uint64_t rows, uint6
 struct GemmArgs {
   CUtensorMap tmA;     // A [M, K], box 128 rows x 128 bytes
   CUtensorMap tmB;     // W [N, K], box BN rows x 128 bytes
-  CUtensorMap tmC;     // output [M, N]: bf16 (EPI_STORE / EPI_GELU), e4m3 (EPI_GELU_F8), fp32 otherwise
+  CUtensorMap tmC;     // output [M, N]: bf16 (EPI_STORE / EPI_GELU / EPI_LNF_*), e4m3 (EPI_GELU_F8), fp32 otherwise
+  CUtensorMap tmC2;    // EPI_RESID_LN: bf16 copy of the new residual [M, N] (make_tmap_out, bf16)
   int M, N, K;
   const float* bias;
+  const float* colsum = nullptr;
+  float* x = nullptr;
+  float* stats = nullptr;
+  int np = 0;
+  float eps = 0.f;
   int epi;
   int bn;              // 128 or 256 (tmB box rows must match)
   bool f8 = false;     // A and W are e4m3 (kind::f8f6f4); otherwise bf16 (kind::f16)
