@@ -326,6 +326,7 @@ def run_ours(args):
 
     if not args.no_batch:
         out["batch_uneven_small"] = batch_bench(wm, torch, dev)
+        out.update(hourly_ensemble_bench(wm, torch, dev))
 
     if not args.no_serve and rank == 0:
         out["serve"] = serve_bench(wm, torch, n_requests=args.serve_requests)
@@ -402,6 +403,66 @@ def batch_bench(wm, torch, dev, reps=3):
         for name in ("fp8mlp", "bf16"):
             res[f"{name}_vs_fp32_rel_l2_by_lead"] = {str(t): wm.wm_rel_l2(a, b)
                                                      for t, a, b in zip(leads, outs[name], outs["fp32"])}
+    finally:
+        wm.wm_destroy(ctx)
+    return res
+
+
+def hourly_ensemble_bench(wm, torch, dev, full_members=8, reps=2):
+    """Hourly outputs to 14 days from one state (small latent), and ensembles:
+    8 full-size members through one six-hour step, 64 small members through
+    the 14-day rollout, each as one batched rollout."""
+    res = {}
+    s = synth.SMALL
+    p6, p1 = synth.processor_weights(s, seed=0)
+    ctx = wm.wm_create_from_host(wm.make_config(s, wm.WM_PREC_BF16, max_batch=64), synth.pack_weights(p6, p1))
+    try:
+        x = torch.from_numpy(synth.latent(s, 1, seed=1)).to(dev)
+        out = torch.empty((337,) + tuple(x.shape[1:]), device=dev)
+        wm.wm_rollout_hourly(ctx, x, 336, out, 16)            # capture + first replay
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            wm.wm_rollout_hourly(ctx, x, 336, out, 16)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res["hourly_small_14d"] = {"workload": "337 hourly latents 0..336 h from one 4x24x48x128 state, "
+                                               "56 six-hour anchors + 280 batched one-hour steps",
+                                   "ms_per_forecast_set": ms, "forecast_sets_per_s": 1e3 / ms}
+        ens = torch.from_numpy(synth.latent(s, 64, seed=100)).to(dev)
+        work = ens.clone()
+        wm.wm_latent_rollout(ctx, work, 336)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            work.copy_(ens)
+            wm.wm_latent_rollout(ctx, work, 336)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res["ensemble_small_14d"] = {"workload": "64 members 4x24x48x128, 336 h each, one graph",
+                                     "member_forecasts_per_s": 64e3 / ms}
+    finally:
+        wm.wm_destroy(ctx)
+    f = synth.FULL
+    p6, p1 = synth.processor_weights(f, seed=0)
+    ctx = wm.wm_create_from_host(wm.make_config(f, wm.WM_PREC_BF16, max_batch=full_members),
+                                 synth.pack_weights(p6, p1))
+    try:
+        ens = torch.from_numpy(synth.latent(f, full_members, seed=100)).to(dev)
+        wm.wm_processor_step(ctx, ens, wm.WM_P6)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            wm.wm_processor_step(ctx, ens, wm.WM_P6)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res["ensemble_full_6h"] = {"workload": f"{full_members} members 9x90x180x768, one six-hour step as one batch",
+                                   "ms_per_step": ms, "member_forecasts_per_s": full_members * 1e3 / ms}
     finally:
         wm.wm_destroy(ctx)
     return res

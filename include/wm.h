@@ -137,6 +137,16 @@ wm_status wm_forecast_host(wm_ctx* ctx, const float* host_in, float* host_out, i
  * single-request rollout bit for bit). n >= 1; leads >= 0. */
 wm_status wm_rollout_batch(wm_ctx* ctx, float* const* latents, const int* lead_hours, int n, void* stream);
 
+/* Every hourly lead time 0..max_lead from one initial state (the hourly
+ * forecasts of Section 3.1): out[t] (device, max_lead + 1 contiguous float32
+ * latents) = the rollout of x (device, one latent) to t hours. By the greedy
+ * schedule (Section 2.1) lead 6k + r is r one-hour steps after the k-th
+ * six-hour anchor, so the anchors form one chain of six-hour steps and the
+ * one-hour branches of all anchors advance together as batched steps of at
+ * most max_batch latents. Each out[t] equals wm_latent_rollout(x, t) bit for
+ * bit. Replayed from a CUDA graph captured per (x, out, max_lead, max_batch). */
+wm_status wm_rollout_hourly(wm_ctx* ctx, const float* x, int max_lead, float* out, int max_batch, void* stream);
+
 /* Greedy schedule of Section 2.1 (pure host): n6 = T div 6, n1 = T mod 6. */
 wm_status wm_schedule(int lead_hours, int* n6, int* n1);
 

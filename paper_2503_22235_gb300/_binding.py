@@ -46,6 +46,7 @@ _SIGS = {
     "wm_forecast_host": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
     "wm_rollout_batch": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_c_int), _c_int, _vp]),
     "wm_schedule": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "wm_rollout_hourly": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _vp]),
     "wm_rel_l2": (_c_int, [_vp, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp]),
     "wm_rel_l2_noalloc": (_c_int, [_vp, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp]),
     "wm_device_status": (_c_int, []),
@@ -178,6 +179,11 @@ def wm_rollout_batch(ctx, latents, lead_hours, stream=None):
     ptrs = (_vp * n)(*[_ptr(t) for t in latents])
     leads = (_c_int * n)(*[int(t) for t in lead_hours])
     _check(lib().wm_rollout_batch(ctx, ptrs, leads, n, _stream(stream)))
+
+
+def wm_rollout_hourly(ctx, x, max_lead, out, max_batch=8, stream=None):
+    """out: device tensor holding max_lead + 1 latents; out[t] = rollout of x to t hours."""
+    _check(lib().wm_rollout_hourly(ctx, _ptr(x), int(max_lead), _ptr(out), int(max_batch), _stream(stream)))
 
 
 def wm_schedule(lead_hours: int) -> tuple[int, int]:

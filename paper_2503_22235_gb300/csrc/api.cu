@@ -804,6 +804,46 @@ wm_status wm_timing_end(wm_ctx* ctx, double* ms_by_kind, int* launches_by_kind) 
   return WM_OK;
 }
 
+wm_status wm_rollout_hourly(wm_ctx* ctx, const float* x, int max_lead, float* out, int max_batch, void* stream) {
+  if (!ctx || !x || !out || max_lead < 0 || max_batch < 1) return fail(WM_ERR_INVALID_ARG, "bad hourly arguments");
+  WM_TRY(check_compute(ctx, x, 1));
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  const size_t lat = (size_t)ctx->N * ctx->cfg.C;
+  const int K = max_lead / 6;
+  WM_TRY(ensure_workspace(ctx, std::max(1, std::min(max_batch, K + 1))));
+  WM_TRY(ensure_buffer(&ctx->d_stage, &ctx->stage_cap, lat * std::min(max_batch, K + 1)));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<uintptr_t> key = {3, (uintptr_t)x, (uintptr_t)out, (uintptr_t)max_lead, (uintptr_t)max_batch,
+                                (uintptr_t)ctx->cfg.precision};
+  return run_graph(ctx, key, s, [&](cudaStream_t st) -> wm_status {
+    if (out != x) WM_CUDA(cudaMemcpyAsync(out, x, lat * 4, cudaMemcpyDeviceToDevice, st));
+    // the six-hour anchors: out[6k] = P6(out[6(k-1)])
+    for (int k = 1; k <= K; ++k) {
+      WM_CUDA(cudaMemcpyAsync(out + (size_t)6 * k * lat, out + (size_t)6 * (k - 1) * lat, lat * 4,
+                              cudaMemcpyDeviceToDevice, st));
+      WM_TRY(processor_step(ctx, out + (size_t)6 * k * lat, 1, WM_P6, st));
+    }
+    // the one-hour branches of every anchor advance together: out[6k + r] = P1(out[6k + r - 1])
+    std::vector<int> ks;
+    for (int r = 1; r <= 5; ++r) {
+      ks.clear();
+      for (int k = 0; k <= K; ++k)
+        if (6 * k + r <= max_lead) ks.push_back(k);
+      for (size_t b0 = 0; b0 < ks.size(); b0 += max_batch) {
+        const int g = (int)std::min<size_t>(max_batch, ks.size() - b0);
+        for (int j = 0; j < g; ++j)
+          WM_CUDA(cudaMemcpyAsync(ctx->d_stage + (size_t)j * lat, out + (size_t)(6 * ks[b0 + j] + r - 1) * lat,
+                                  lat * 4, cudaMemcpyDeviceToDevice, st));
+        WM_TRY(processor_step(ctx, ctx->d_stage, g, WM_P1, st));
+        for (int j = 0; j < g; ++j)
+          WM_CUDA(cudaMemcpyAsync(out + (size_t)(6 * ks[b0 + j] + r) * lat, ctx->d_stage + (size_t)j * lat,
+                                  lat * 4, cudaMemcpyDeviceToDevice, st));
+      }
+    }
+    return WM_OK;
+  });
+}
+
 wm_status wm_rel_l2(const float* a, const float* b, size_t n, double* out, void* stream) {
   if (!a || !b || !out) return fail(WM_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
