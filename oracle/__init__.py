@@ -5,5 +5,6 @@ import this package. The GPU library never depends on it.
 """
 from .wm_oracle import (  # noqa: F401
     axis_window, block, block_fp8mlp, e4m3_decode, e4m3_round, fp8_mlp_scales, block_at_tokens, gelu, greedy_schedule, layer_norm, linear,
-    neighbor_index, neighborhood_attention, processor, rel_l2, rollout,
+    neighbor_index, neighborhood_attention, processor, rel_l2, rollout, rope_angles, rope_pairs,
+    rope_rotate,
 )

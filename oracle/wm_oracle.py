@@ -169,6 +169,57 @@ def neighborhood_attention(q, k, v, heads, nbr, return_weights=False, chunk=1024
     return (o, wts) if return_weights else o
 
 
+# ------------------------------------------------- rotary position embedding --
+# Appendix A.2 states that tokens carry rotary position embeddings (RoFormer)
+# but gives neither the split of the head dimension over the three axes nor
+# the frequencies. Reading used here: the dh/2 rotation pairs (dims 2p, 2p+1)
+# of every head are split into level, latitude and longitude groups (sizes
+# n_lev, n_lat, n_lon with n_lon = ceil(P/3), n_lat = ceil((P - n_lon)/2),
+# n_lev = the rest), in that order. Pair m of an axis with positions
+# 0..n-1 rotates by angle pos * w_m with
+#   level, latitude:  w_m = 10000^(-m / n_axis)        (RoFormer frequencies)
+#   longitude:        w_m = 2 pi (m + 1) / W             (harmonics of the circle,
+#                     so a rotation depends on longitude differences mod W)
+# q and k are rotated after the QKV projection; v is not.
+
+def rope_pairs(dh: int):
+    """(n_lev, n_lat, n_lon) rotation pairs per axis for head dimension dh."""
+    P = dh // 2
+    n_lon = -(-P // 3)
+    n_lat = -(-(P - n_lon) // 2)
+    return P - n_lon - n_lat, n_lat, n_lon
+
+
+def rope_angles(D, H, W, dh):
+    """[N, dh/2] rotation angle of every (token, pair)."""
+    n_lev, n_lat, n_lon = rope_pairs(dh)
+    lev = np.arange(D, dtype=np.float64)
+    lat = np.arange(H, dtype=np.float64)
+    lon = np.arange(W, dtype=np.float64)
+    ang = np.zeros((D, H, W, dh // 2))
+    for m in range(n_lev):
+        ang[:, :, :, m] = lev[:, None, None] * 10000.0 ** (-m / n_lev)
+    for m in range(n_lat):
+        ang[:, :, :, n_lev + m] = lat[None, :, None] * 10000.0 ** (-m / n_lat)
+    for m in range(n_lon):
+        ang[:, :, :, n_lev + n_lat + m] = lon[None, None, :] * (2.0 * np.pi * (m + 1) / W)
+    return ang.reshape(D * H * W, dh // 2)
+
+
+def rope_rotate(t, heads, angles):
+    """Rotate pairs (2p, 2p+1) of every head of t [B, N, C] by angles [N, dh/2]."""
+    t = np.asarray(t, np.float64)
+    B, N, C = t.shape
+    dh = C // heads
+    x = t.reshape(B, N, heads, dh // 2, 2)
+    c = np.cos(angles)[None, :, None, :]
+    s = np.sin(angles)[None, :, None, :]
+    out = np.empty_like(x)
+    out[..., 0] = x[..., 0] * c - x[..., 1] * s
+    out[..., 1] = x[..., 0] * s + x[..., 1] * c
+    return out.reshape(B, N, C)
+
+
 # ------------------------------------------------------ block / processor --
 
 def _f64(w):
@@ -188,6 +239,9 @@ def block(x, w, shape):
     u = layer_norm(xf, w["ln1_g"], w["ln1_b"], shape.ln_eps)
     qkv = linear(u, w["wqkv"], w["bqkv"])
     q, k, v = qkv[..., :C], qkv[..., C:2 * C], qkv[..., 2 * C:]
+    if getattr(shape, "rope", False):
+        ang = rope_angles(shape.D, shape.H, shape.W, C // shape.heads)
+        q, k = rope_rotate(q, shape.heads, ang), rope_rotate(k, shape.heads, ang)
     o = neighborhood_attention(q, k, v, shape.heads, nbr)
     x1 = xf + linear(o, w["wo"], w["bo"])
     # MLP half
@@ -220,6 +274,10 @@ def block_at_tokens(x, w, shape, tokens):
     local_tok = np.array([pos[int(t)] for t in tokens], dtype=np.int64)
     u = layer_norm(xf[:, needed], w["ln1_g"], w["ln1_b"], shape.ln_eps)
     qkv = linear(u, w["wqkv"], w["bqkv"])
+    if getattr(shape, "rope", False):
+        ang = rope_angles(shape.D, shape.H, shape.W, C // shape.heads)[needed]
+        qkv = np.concatenate([rope_rotate(qkv[..., :C], shape.heads, ang),
+                              rope_rotate(qkv[..., C:2 * C], shape.heads, ang), qkv[..., 2 * C:]], axis=-1)
     q = qkv[:, local_tok, :C]
     k, v = qkv[..., C:2 * C], qkv[..., 2 * C:]
     # queries first in a [B, S + ...] layout: neighborhood_attention reads q[:, :S]

@@ -77,6 +77,7 @@ class Shape:
     blocks_p1: int = 4
     lon_periodic: bool = True
     ln_eps: float = 1e-5
+    rope: bool = False          # 3D rotary position embedding on q and k
 
     @property
     def N(self) -> int:

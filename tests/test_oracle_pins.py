@@ -6,6 +6,7 @@ definition, or brute force on a tiny grid. A plausible slip in the oracle (a
 dropped bias, a wrong sign, a transposed weight, an off-by-one window) breaks
 at least one of them.
 """
+import dataclasses
 import math
 import os
 
@@ -401,3 +402,62 @@ def test_fp8_block_without_rounding_is_the_block():
     q = orc.block_fp8mlp(x, w, TINY)
     err = orc.rel_l2(q, orc.block(x, w, TINY))
     assert 1e-4 < err < 5e-2     # E4M3 keeps 3 mantissa bits
+
+
+# ------------------------------------------------------------------ RoPE ---
+
+ROPE = synth.Shape(D=3, H=5, W=7, C=24, heads=2, kd=3, kh=3, kw=5, rope=True)
+
+
+def test_rope_pair_split_covers_the_head():
+    for dh in (8, 16, 24, 32, 48, 64):
+        a, b, c = orc.rope_pairs(dh)
+        assert a + b + c == dh // 2 and min(a, b, c) >= 1 and c >= b >= a
+
+
+def test_rope_rotation_matches_complex_multiplication():
+    rng = np.random.default_rng(2)
+    t = rng.standard_normal((1, 3 * 5 * 7, 24))
+    ang = orc.rope_angles(3, 5, 7, 12)
+    got = orc.rope_rotate(t, 2, ang)
+    z = (t[..., 0::2] + 1j * t[..., 1::2]).reshape(1, -1, 2, 6) * np.exp(1j * ang)[None, :, None, :]
+    ref = np.stack([z.real, z.imag], -1).reshape(1, -1, 24)
+    assert np.max(np.abs(got - ref)) < 1e-12
+    assert np.allclose(np.linalg.norm(got, axis=-1), np.linalg.norm(t, axis=-1))
+
+
+def test_rope_scores_depend_only_on_relative_position():
+    # q at p, k at p' and q at p + s, k at p' + s give the same rotated dot
+    # product; along longitude the shift is taken modulo W
+    rng = np.random.default_rng(3)
+    D, H, W, dh = 4, 6, 7, 12
+    ang = orc.rope_angles(D, H, W, dh).reshape(D, H, W, -1)
+    q, k = rng.standard_normal((2, dh))
+
+    def score(p, pp):
+        a = orc.rope_rotate(q[None, None], 1, ang[p][None])[0, 0]
+        b = orc.rope_rotate(k[None, None], 1, ang[pp][None])[0, 0]
+        return a @ b
+
+    base = score((1, 2, 3), (2, 0, 5))
+    assert abs(score((2, 3, 3), (3, 1, 5)) - base) < 1e-12          # level and latitude shift
+    assert abs(score((1, 2, 6), (2, 0, (5 + 3) % W)) - base) < 1e-12  # longitude shift, wrapped
+    assert abs(score((1, 2, 3), (2, 1, 5)) - base) > 1e-6            # a different offset differs
+
+
+def test_rope_block_keeps_longitude_roll_equivariance_and_breaks_flip():
+    x = synth.latent(ROPE, 1, seed=4)
+    w = synth.block_weights(ROPE.C, 0, 0, 0, stress=True)
+    y = orc.block(x, w, ROPE)
+    for s in (1, 4):
+        assert np.max(np.abs(orc.block(np.roll(x, s, axis=3), w, ROPE) - np.roll(y, s, axis=3))) < 1e-12
+    assert orc.rel_l2(orc.block(np.flip(x, axis=2), w, ROPE), np.flip(y, axis=2)) > 1e-4
+    assert orc.rel_l2(y, orc.block(x, w, dataclasses.replace(ROPE, rope=False))) > 1e-4
+
+
+def test_rope_block_at_tokens_matches_full_block():
+    x = synth.latent(ROPE, 1, seed=5)
+    w = synth.block_weights(ROPE.C, 0, 1, 0, stress=True)
+    toks = np.array([0, 11, 52, ROPE.N - 1])
+    full = orc.block(x, w, ROPE).reshape(1, -1, ROPE.C)
+    assert np.max(np.abs(orc.block_at_tokens(x, w, ROPE, toks) - full[:, toks])) < 1e-12
