@@ -303,6 +303,27 @@ def run_ours(args):
                              "bf16_vs_fp32_rel_l2": err, "speedup_bf16": fp32_ms / ms_per_step}
         del xa, xb, xc
 
+    # ---------------- FP8-MLP precision on the same step
+    if not args.no_fp32:
+        xa = torch.from_numpy(x0).to(dev)
+        xb = torch.from_numpy(x0).to(dev)
+        wm.wm_set_precision(ctx, wm.WM_PREC_BF16_FP8MLP)
+        wm.wm_processor_step(ctx, xa, wm.WM_P6)              # warm-up (tunes nothing new)
+        xa.copy_(torch.from_numpy(x0).to(dev))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wm.wm_processor_step(ctx, xa, wm.WM_P6)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f8_ms = e0.elapsed_time(e1)
+        wm.wm_set_precision(ctx, wm.WM_PREC_FP32)
+        wm.wm_processor_step(ctx, xb, wm.WM_P6)
+        wm.wm_set_precision(ctx, wm.WM_PREC_BF16)
+        torch.cuda.synchronize()
+        out["fp8mlp"] = {"value": 1e3 / f8_ms, "unit": UNIT, "ms_per_step": f8_ms,
+                         "fp8mlp_vs_fp32_rel_l2": wm.wm_rel_l2(xa, xb)}
+        del xa, xb
+
     # ---------------- end to end through the host-buffer C-ABI call
     if not args.no_e2e:
         hin = torch.from_numpy(x0).pin_memory()

@@ -67,6 +67,11 @@ typedef struct {
   float ln_eps;            /* LayerNorm epsilon (the processor uses 1e-5) */
   int precision;           /* wm_precision used by the compute calls */
   int max_batch;           /* initial workspace capacity in latents (grown on demand) */
+  int rope;                /* 1: 3D rotary position embedding on q and k (Appendix A.2). The head's dh/2
+                              dimension pairs (2p, 2p+1) are split into level, latitude and longitude
+                              groups, n_lon = ceil(P/3), n_lat = ceil((P - n_lon)/2), n_lev = P - n_lon - n_lat;
+                              pair m of an axis rotates by pos * w_m with w_m = 10000^(-m/n_axis) for
+                              level and latitude and w_m = 2 pi (m + 1) / W for longitude. 0: none. */
 } wm_config;
 
 typedef struct wm_ctx wm_ctx;

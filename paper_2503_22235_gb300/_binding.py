@@ -32,7 +32,8 @@ class WmError(RuntimeError):
 class wm_config(ctypes.Structure):
     _fields_ = [("D", _c_int), ("H", _c_int), ("W", _c_int), ("C", _c_int), ("heads", _c_int),
                 ("kd", _c_int), ("kh", _c_int), ("kw", _c_int), ("blocks_p6", _c_int), ("blocks_p1", _c_int),
-                ("lon_periodic", _c_int), ("ln_eps", _c_float), ("precision", _c_int), ("max_batch", _c_int)]
+                ("lon_periodic", _c_int), ("ln_eps", _c_float), ("precision", _c_int), ("max_batch", _c_int),
+                ("rope", _c_int)]
 
 
 _SIGS = {
@@ -127,7 +128,7 @@ def make_config(shape, precision=WM_PREC_BF16, max_batch=1) -> wm_config:
     """wm_config from an object with D, H, W, C, heads, kd, kh, kw, blocks_p6, blocks_p1, lon_periodic, ln_eps."""
     return wm_config(shape.D, shape.H, shape.W, shape.C, shape.heads, shape.kd, shape.kh, shape.kw,
                      shape.blocks_p6, shape.blocks_p1, int(bool(shape.lon_periodic)), float(shape.ln_eps),
-                     int(precision), int(max_batch))
+                     int(precision), int(max_batch), int(bool(getattr(shape, "rope", False))))
 
 
 # ------------------------------------------------------------------ context ---

@@ -52,6 +52,9 @@ struct wm_ctx {
   bf16* d_wh = nullptr;
   uint8_t* d_wq = nullptr;   // e4m3 W1, W2 per block
   bf16* d_wf = nullptr;      // LayerNorm-folded bf16 Wqkv, W1 per block
+  float2* d_rope_tab = nullptr;       // rotary embedding cos/sin tables (level, latitude, longitude)
+  wm::RopeArgs* d_rope = nullptr;     // device copy of rope_host (pointers into d_rope_tab)
+  wm::RopeArgs rope_host{};
   float* d_vf = nullptr;     // their column sums and folded biases
   std::vector<BlockW> blk[2];
   // workspace for cap32 (FP32 path) / cap16 (BF16 path) latents
@@ -97,6 +100,9 @@ wm_status validate(const wm_config* c) {
   if (c->kd > c->D || c->kh > c->H || c->kw > c->W)
     return fail(WM_ERR_INVALID_ARG, "a window is larger than its axis");
   if (c->blocks_p6 < 1 || c->blocks_p1 < 1) return fail(WM_ERR_INVALID_ARG, "each processor needs >= 1 block");
+  if (c->rope != 0 && c->rope != 1) return fail(WM_ERR_INVALID_ARG, "rope must be 0 or 1");
+  if (c->rope && ((c->C / c->heads) % 2 != 0 || c->C / c->heads < 6))
+    return fail(WM_ERR_INVALID_ARG, "rotary embedding needs an even head dimension >= 6");
   if (c->precision < WM_PREC_FP32 || c->precision > WM_PREC_BF16_FP8MLP)
     return fail(WM_ERR_INVALID_ARG, "unknown precision");
   if (!(c->ln_eps >= 0.f)) return fail(WM_ERR_INVALID_ARG, "ln_eps must be >= 0");
@@ -257,7 +263,8 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
     { TimedLaunch t(ctx, WM_K_LN1, s);
       WM_TRY(wm::launch_layernorm(x, w.ln1_g, w.ln1_b, ctx->f_u, false, (int)M, C, c.ln_eps, s)); }
     { TimedLaunch t(ctx, WM_K_QKV, s);
-      WM_TRY(wm::launch_sgemm(ctx->f_u, w.wqkv, w.bqkv, ctx->f_qkv, (int)M, 3 * C, C, wm::EPI_STORE_F32, s)); }
+      WM_TRY(wm::launch_sgemm(ctx->f_u, w.wqkv, w.bqkv, ctx->f_qkv, (int)M, 3 * C, C, wm::EPI_STORE_F32, s));
+      if (c.rope) WM_TRY(wm::launch_rope_f32(ctx->f_qkv, M, ctx->d_rope, ctx->rope_host, s)); }
     { TimedLaunch t(ctx, WM_K_ATTN, s);
       WM_TRY(wm::launch_na_f32(ctx->f_qkv, ctx->f_o, batch, c.D, c.H, c.W, C, c.heads, c.kd, c.kh, c.kw, per, s)); }
     { TimedLaunch t(ctx, WM_K_PROJ, s);
@@ -290,6 +297,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   a.tmA = ctx->tm_xb; a.tmB = w.tm_fqkv[a.bn == 256]; a.tmC = ctx->tmc_qkv;
   a.bias = w.bb_qkv; a.colsum = w.cs_qkv; a.stats = ctx->stats; a.np = ctx->np_next; a.eps = c.ln_eps;
   a.epi = wm::EPI_LNF_STORE;
+  a.rope = c.rope ? ctx->d_rope : nullptr;
   { TimedLaunch t(ctx, WM_K_QKV, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
   { TimedLaunch t(ctx, WM_K_ATTN, s);
     WM_TRY(wm::launch_na_bf16(ctx->h_qkv, ctx->h_o, batch, c.D, c.H, c.W, C, c.heads, c.kd, c.kh, c.kw, per, s)); }
@@ -390,6 +398,41 @@ wm_status run_graph(wm_ctx* ctx, const std::vector<uintptr_t>& key, cudaStream_t
     it = ctx->graphs.emplace(key, ex).first;
   }
   WM_CUDA(cudaGraphLaunch(it->second, stream));
+  return WM_OK;
+}
+
+// Rotary embedding tables: pair m of an axis at position pos has angle
+// pos * w_m (w_m = 10000^(-m/n) for level and latitude, 2 pi (m + 1) / W for
+// longitude); stored as (cos, sin) computed in double.
+wm_status build_rope(wm_ctx* ctx) {
+  const wm_config& c = ctx->cfg;
+  const int dh = c.C / c.heads, P = dh / 2;
+  const int n_lon = (P + 2) / 3;
+  const int n_lat = (P - n_lon + 1) / 2;
+  const int n_lev = P - n_lon - n_lat;
+  const int npos[3] = {c.D, c.H, c.W};
+  const int npair[3] = {n_lev, n_lat, n_lon};
+  std::vector<float2> tab;
+  size_t off[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    off[ax] = tab.size();
+    for (int pos = 0; pos < npos[ax]; ++pos)
+      for (int m = 0; m < npair[ax]; ++m) {
+        const double w = ax < 2 ? std::pow(10000.0, -(double)m / npair[ax]) : 2.0 * M_PI * (m + 1) / c.W;
+        const double a = pos * w;
+        tab.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+      }
+  }
+  WM_CUDA(cudaMalloc(&ctx->d_rope_tab, tab.size() * sizeof(float2)));
+  WM_CUDA(cudaMemcpy(ctx->d_rope_tab, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  wm::RopeArgs& R = ctx->rope_host;
+  for (int ax = 0; ax < 3; ++ax) {
+    R.tab[ax] = ctx->d_rope_tab + off[ax];
+    R.n[ax] = npair[ax];
+  }
+  R.D = c.D; R.H = c.H; R.W = c.W; R.C = c.C; R.dh = dh;
+  WM_CUDA(cudaMalloc(&ctx->d_rope, sizeof(wm::RopeArgs)));
+  WM_CUDA(cudaMemcpy(ctx->d_rope, &R, sizeof(wm::RopeArgs), cudaMemcpyHostToDevice));
   return WM_OK;
 }
 
@@ -588,6 +631,7 @@ wm_status wm_create_from_host(const wm_config* cfg, const float* weights, size_t
   cudaGetDevice(&ctx->device);
   ctx->N = (long)cfg->D * cfg->H * cfg->W;
   wm_status st = upload_weights(ctx, weights, n_floats);
+  if (st == WM_OK && cfg->rope) st = build_rope(ctx);
   if (st == WM_OK) st = ensure_workspace(ctx, ctx->cfg.max_batch);
   if (st == WM_OK && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     st = fail(WM_ERR_CUDA, "cudaStreamCreate failed");
@@ -633,6 +677,8 @@ wm_status wm_destroy(wm_ctx* ctx) {
   cudaFree(ctx->d_wq);
   cudaFree(ctx->d_wf);
   cudaFree(ctx->d_vf);
+  cudaFree(ctx->d_rope_tab);
+  cudaFree(ctx->d_rope);
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_io);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);

@@ -3,6 +3,8 @@
 // so that a block matches the float64 oracle to ~1e-6 relative L2.
 #include <cuda_fp8.h>
 
+#include <algorithm>
+
 #include "wm_internal.cuh"
 
 namespace wm {
@@ -347,6 +349,37 @@ wm_status launch_sgemm(const float* A, const float* W, const float* bias, float*
     sgemm_kernel<true><<<grid, block, 0, s>>>(A, W, bias, out, M, N, K, epi);
   else
     sgemm_kernel<false><<<grid, block, 0, s>>>(A, W, bias, out, M, N, K, epi);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+// ------------------------------------------------------- rotary embedding ----
+// One thread per (token, rotation pair) of q and of k in an fp32 qkv [M, 3C].
+__global__ void rope_f32_kernel(float* __restrict__ qkv, long M, const RopeArgs* __restrict__ R) {
+  const int P = R->C / 2;
+  const long total = M * 2 * P;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long m = i / (2 * P);
+    const int r = (int)(i % (2 * P));   // pair index over q (r < P) then k
+    const int col = 2 * (r % P) + (r >= P ? R->C : 0);
+    const int p = (col % R->C) % R->dh / 2;
+    const int tok = (int)(m % ((long)R->D * R->H * R->W));
+    const int pos[3] = {tok / (R->H * R->W), (tok / R->W) % R->H, tok % R->W};
+    const int ax = p < R->n[0] ? 0 : (p < R->n[0] + R->n[1] ? 1 : 2);
+    const int pm = p - (ax > 0 ? R->n[0] : 0) - (ax > 1 ? R->n[1] : 0);
+    const float2 cs = R->tab[ax][pos[ax] * R->n[ax] + pm];
+    float* v = qkv + m * 3L * R->C + col;
+    const float a0 = v[0], a1 = v[1];
+    v[0] = a0 * cs.x - a1 * cs.y;
+    v[1] = a0 * cs.y + a1 * cs.x;
+  }
+}
+
+wm_status launch_rope_f32(float* qkv, long M, const RopeArgs* rope_dev, const RopeArgs& rope_host, cudaStream_t s) {
+  if (M <= 0) return WM_OK;
+  const long total = M * rope_host.C;
+  const int blocks = (int)std::min<long>((total + 255) / 256, (long)num_sms() * 16);
+  rope_f32_kernel<<<blocks, 256, 0, s>>>(qkv, M, rope_dev);
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }

@@ -442,6 +442,26 @@ __global__ void __launch_bounds__(THREADS, 1)
           if constexpr (EPI == EPI_GELU || EPI == EPI_GELU_F8 || EPI == EPI_LNF_GELU) v[j] = gelu_erf(v[j]);
           if constexpr (EPI == EPI_GELU_F8) v[j] *= out_scale;
         }
+        if constexpr (EPI == EPI_LNF_STORE) {
+          if (e.rope != nullptr) {
+            const RopeArgs& R = *e.rope;
+            if (n < 2 * R.C && m < M) {
+              // rotary embedding of q / k: this row's token position, then per pair
+              const int tok = m % (R.D * R.H * R.W);
+              const int pos[3] = {tok / (R.H * R.W), (tok / R.W) % R.H, tok % R.W};
+#pragma unroll
+              for (int jp = 0; jp < 16; ++jp) {
+                const int p = ((n + 2 * jp) % R.C) % R.dh / 2;
+                const int ax = p < R.n[0] ? 0 : (p < R.n[0] + R.n[1] ? 1 : 2);
+                const int pm = p - (ax > 0 ? R.n[0] : 0) - (ax > 1 ? R.n[1] : 0);
+                const float2 cs = __ldg(R.tab[ax] + pos[ax] * R.n[ax] + pm);
+                const float a0 = v[2 * jp], a1 = v[2 * jp + 1];
+                v[2 * jp] = a0 * cs.x - a1 * cs.y;
+                v[2 * jp + 1] = a0 * cs.y + a1 * cs.x;
+              }
+            }
+          }
+        }
         if constexpr (kResLN) {
           // x_new = x_old + acc + bias (x_old loaded one chunk ahead), then the
           // chunk's mean / M2 merged into the row's (Chan et al.)
@@ -532,6 +552,7 @@ static wm_status launch_one(const GemmArgs& a, cudaStream_t s) {
   e.eps = a.eps;
   e.alpha = a.alpha;
   e.out_scale = a.out_scale;
+  e.rope = a.rope;
   kern<<<grid, THREADS, CF::SMEM, s>>>(a.tmA, a.tmB, a.tmC, a.tmC2, a.M, a.N, a.K, e, device_status_word());
   WM_CUDA(cudaGetLastError());
   return WM_OK;

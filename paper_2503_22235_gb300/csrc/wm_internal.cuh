@@ -43,6 +43,7 @@ enum Epilogue : int {
   EPI_LNF_GELU = 7,    // as EPI_LNF_STORE, then GELU
 };
 
+struct RopeArgs;
 struct EpiArgs {
   const float* bias;
   const float* colsum;  // LayerNorm-folded epilogues: per-column sum of the folded bf16 weights
@@ -51,6 +52,15 @@ struct EpiArgs {
   int np;               // EPI_LNF_*: partials per row
   float eps;            // EPI_LNF_*: LayerNorm epsilon
   float alpha, out_scale;
+  const struct RopeArgs* rope;   // EPI_LNF_STORE: rotate q and k (columns < 2C) when non-null
+};
+
+// 3D rotary position embedding tables (device): for each axis, cos/sin of
+// pos * w_m as float2, [positions][pairs of that axis].
+struct RopeArgs {
+  const float2* tab[3];  // level, latitude, longitude
+  int n[3];              // pairs per axis (n_lev, n_lat, n_lon)
+  int D, H, W, C, dh;
 };
 
 int num_sms();
@@ -107,7 +117,10 @@ struct GemmArgs {
   bool f8 = false;     // A and W are e4m3 (kind::f8f6f4); otherwise bf16 (kind::f16)
   float alpha = 1.f;   // e4m3 only: accumulator scale (product of the operand scales)
   float out_scale = 1.f;  // EPI_GELU_F8: 1 / output scale
+  const RopeArgs* rope = nullptr;  // device pointer; EPI_LNF_STORE rotates q and k
 };
+// Rotate q and k in an fp32 qkv [M, 3C] (the FP32 plain path).
+wm_status launch_rope_f32(float* qkv, long M, const RopeArgs* rope_dev, const RopeArgs& rope_host, cudaStream_t s);
 wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
 
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,

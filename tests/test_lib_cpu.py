@@ -36,7 +36,7 @@ def test_schedule_rejects_negative_lead():
 
 def _cfg(**kw):
     base = dict(D=4, H=24, W=48, C=128, heads=4, kd=3, kh=5, kw=5, blocks_p6=8, blocks_p1=4, lon_periodic=1,
-                ln_eps=1e-5, precision=wm.WM_PREC_BF16, max_batch=1)
+                ln_eps=1e-5, precision=wm.WM_PREC_BF16, max_batch=1, rope=0)
     base.update(kw)
     return wm.wm_config(*[base[f] for f, _ in wm.wm_config._fields_])
 
