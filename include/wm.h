@@ -280,10 +280,25 @@ wm_status wm_fp8_scales(wm_ctx* ctx, int which, int block, float* out);
 
 /* 3D neighborhood attention on qkv [batch*D*H*W, 3C] (q | k | v, each head-major)
  * -> out [batch*D*H*W, C]. precision FP32: float32 in/out; BF16: bfloat16 in/out
- * (BF16 requires dh = C/heads in {16, 32, 48, 64}). */
+ * (BF16 requires dh = C/heads in {16, 32, 48, 64}).
+ * variant (BF16 only; FP32 takes 0): WM_NA_AUTO uses the plan tuned for this
+ * shape, else the arithmetic family fixed for it, else the default. Otherwise
+ * one of WM_NA_QK_CHUNK8, WM_NA_QK_CHUNK4, WM_NA_KQ picks the arithmetic
+ * family, optionally OR-ed with WM_NA_PER_TILE or WM_NA_PERSISTENT to pick
+ * the kernel kind (else the kind is chosen by a heuristic). Families round
+ * differently (order of the softmax sums); the kernel kind and CTA shape do
+ * not change any result. */
+enum {
+  WM_NA_AUTO = 0,
+  WM_NA_QK_CHUNK8 = 1,   /* S = Q K^T, 16 queries per warp, softmax update every 8 key groups */
+  WM_NA_QK_CHUNK4 = 2,   /* as above, update every 4 key groups */
+  WM_NA_KQ = 3,          /* S^T = K Q^T, 8 queries per warp, update every 8 key groups */
+  WM_NA_PER_TILE = 4,    /* one CTA per query tile */
+  WM_NA_PERSISTENT = 8   /* persistent CTAs with a producer warp */
+};
 wm_status wm_op_neighborhood_attention(const void* qkv, void* out, int batch, int D, int H, int W, int C,
                                        int heads, int kd, int kh, int kw, int lon_periodic, int precision,
-                                       void* stream);
+                                       int variant, void* stream);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,8 @@ WM_OK, WM_ERR_INVALID_ARG, WM_ERR_OOM, WM_ERR_CUDA, WM_ERR_TIMEOUT, WM_ERR_BUSY,
 WM_P6, WM_P1 = 0, 1
 WM_PREC_FP32, WM_PREC_BF16, WM_PREC_BF16_FP8MLP = 0, 1, 2
 EPI_STORE, EPI_GELU, EPI_RESID_F32, EPI_STORE_F32, EPI_GELU_F8 = 0, 1, 2, 3, 4
+WM_NA_AUTO, WM_NA_QK_CHUNK8, WM_NA_QK_CHUNK4, WM_NA_KQ = 0, 1, 2, 3
+WM_NA_PER_TILE, WM_NA_PERSISTENT = 4, 8
 
 _c_int, _c_float, _vp, _sz = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
 
@@ -65,7 +67,7 @@ _SIGS = {
     "wm_server_stop": (_c_int, [_vp]),
     "wm_op_layernorm": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_float, _vp]),
     "wm_op_linear": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_int, _c_int, _c_int, _vp]),
-    "wm_op_neighborhood_attention": (_c_int, [_vp, _vp] + [_c_int] * 11 + [_vp]),
+    "wm_op_neighborhood_attention": (_c_int, [_vp, _vp] + [_c_int] * 12 + [_vp]),
     "wm_op_linear_e4m3": (_c_int, [_vp, _vp, _c_float, _vp, _vp, _c_float, _c_int, _c_int, _c_int, _c_int, _vp]),
     "wm_op_layernorm_e4m3": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_float, _c_float, _vp]),
     "wm_fp8_scales": (_c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_c_float)]),
@@ -300,9 +302,10 @@ def wm_op_linear(A, W, bias, out, precision, epilogue, stream=None):
 
 
 def wm_op_neighborhood_attention(qkv, out, batch, D, H, W, C, heads, kd, kh, kw, lon_periodic, precision,
-                                 stream=None):
+                                 variant=0, stream=None):
     _check(lib().wm_op_neighborhood_attention(_ptr(qkv), _ptr(out), batch, D, H, W, C, heads, kd, kh, kw,
-                                              int(bool(lon_periodic)), int(precision), _stream(stream)))
+                                              int(bool(lon_periodic)), int(precision), int(variant),
+                                              _stream(stream)))
 
 
 def wm_op_linear_e4m3(A, W, alpha, bias, out, out_scale, epilogue, stream=None):

@@ -996,7 +996,8 @@ wm_status wm_op_linear_e4m3(const void* A, const void* W, float alpha, const flo
 }
 
 wm_status wm_op_neighborhood_attention(const void* qkv, void* out, int batch, int D, int H, int W, int C, int heads,
-                                       int kd, int kh, int kw, int lon_periodic, int precision, void* stream) {
+                                       int kd, int kh, int kw, int lon_periodic, int precision, int variant,
+                                       void* stream) {
   wm_config c{};
   c.D = D; c.H = H; c.W = W; c.C = C; c.heads = heads; c.kd = kd; c.kh = kh; c.kw = kw;
   c.blocks_p6 = c.blocks_p1 = 1;
@@ -1005,11 +1006,16 @@ wm_status wm_op_neighborhood_attention(const void* qkv, void* out, int batch, in
   if (!qkv || !out || batch < 0) return fail(WM_ERR_INVALID_ARG, "bad attention arguments");
   WM_TRY(wm::prepare_kernels());
   cudaStream_t s = (cudaStream_t)stream;
-  if (precision == WM_PREC_FP32)
+  if (precision == WM_PREC_FP32) {
+    if (variant != WM_NA_AUTO) return fail(WM_ERR_INVALID_ARG, "the FP32 attention has one variant (WM_NA_AUTO)");
     return wm::launch_na_f32((const float*)qkv, (float*)out, batch, D, H, W, C, heads, kd, kh, kw, lon_periodic != 0, s);
+  }
   if (precision != WM_PREC_BF16) return fail(WM_ERR_INVALID_ARG, "attention precision must be FP32 or BF16");
   if (C % 8 != 0) return fail(WM_ERR_INVALID_ARG, "BF16 attention needs C % 8 == 0");
-  return wm::launch_na_bf16((const bf16*)qkv, (bf16*)out, batch, D, H, W, C, heads, kd, kh, kw, lon_periodic != 0, s);
+  if (variant < 0 || variant > 15 || (variant & 12) == 12 || (variant != 0 && (variant & 3) == 0))
+    return fail(WM_ERR_INVALID_ARG, "bad attention variant");
+  return wm::launch_na_bf16((const bf16*)qkv, (bf16*)out, batch, D, H, W, C, heads, kd, kh, kw, lon_periodic != 0, s,
+                            variant);
 }
 
 }  // extern "C"

@@ -17,7 +17,9 @@
 #include <array>
 #include <cstdio>
 #include <string>
+#include <type_traits>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -36,6 +38,8 @@ struct Params {
   int log2span;           // columns of a warp's key rectangle = 1 << log2span (8, 16 or 32)
   int tiles_w;
   int nbuf;               // slab ring depth of the persistent kernel (2 or 3)
+  int slab;               // elements between the K and V slabs (and between ring buffers / 2); multiple of 64
+  int tma;                // persistent kernel: non-wrapping slabs by one tensor copy each for K and V
   float scale_log2;       // log2(e) / sqrt(dh)
 };
 
@@ -75,6 +79,12 @@ __device__ __forceinline__ float ex2(float x) {
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&p);
+}
+
+// First 128-byte aligned address at or after p (the launch adds 128 bytes).
+__device__ __forceinline__ __nv_bfloat16* align128(__nv_bfloat16* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  return p + (((128u - (a & 127u)) & 127u) >> 1);
 }
 
 // ----------------------------------------------------------------------------
@@ -358,17 +368,242 @@ __device__ __forceinline__ void warp_end(const WarpQ<DH, LS>& q, const Params& p
 }
 
 // ---------------------------------------------------------------------------
+// Transposed formulation: a warp owns 8 queries (a WH x WW patch with
+// WH * WW = 8) and computes S^T = K Q^T with 16 keys on the MMA's M side and
+// the 8 queries on N, so the warp's key rectangle (the union of 8 windows) is
+// smaller. Thread (g, t4) holds keys g and g + 8 of each 16-key group for
+// queries 2 t4 and 2 t4 + 1. Row maxima and sums reduce over the 8 lanes that
+// share t4. P^T is re-packed as bf16 8x8 blocks and transposed in registers
+// (movmatrix) into the B operand of O^T += V^T P^T; V^T comes from the V slab
+// by ldmatrix.trans.
+
+__device__ __forceinline__ uint32_t movmatrix_t(uint32_t a) {
+  uint32_t d;
+  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(d) : "r"(a));
+  return d;
+}
+
+template <int DH, int LS>
+struct WarpQT {
+  static constexpr int KC = DH / 16, MD = DH / 16;
+  uint32_t qb[KC][2];     // Q^T B fragments (query g)
+  float o[MD][4];         // O^T: (dh g / g+8 of tile md) x (query 2t4 / 2t4+1)
+  float mrow[2], lrow[2]; // queries 2t4, 2t4+1
+  int rlo[2];
+  float cbias[2][2][2];   // [group parity][query k][key row i = g / g + 8]
+  int wr0, wc0, nkeys, ngroups;
+  int qh, qw;             // query g (the one this thread stores)
+  bool qvalid, live;
+};
+
+template <int DH, int LS>
+__device__ __forceinline__ void warp_begin_t(WarpQT<DH, LS>& q, const Params& p, const Tile& T, int warp, int lane) {
+  constexpr int KC = DH / 16, MD = DH / 16;
+  constexpr int smask = (1 << LS) - 1;
+  const int g = lane >> 2, t4 = lane & 3;
+  const int H = p.H, W = p.W;
+  const int rh = p.kh / 2, rw = p.kw / 2;
+  const int wy = warp / p.NWW, wx = warp % p.NWW;
+  const int wh0 = T.h0 + wy * p.WH, ww0 = T.w0 + wx * p.WW;
+  q.live = (wh0 < H) && (ww0 < W);
+  q.wr0 = clampi(min(wh0, H - 1) - rh, 0, H - p.kh) - T.hs0;
+  const int wr1 = clampi(min(wh0 + p.WH - 1, H - 1) - rh, 0, H - p.kh) + p.kh - T.hs0;
+  q.wc0 = p.periodic ? (ww0 - T.w0) : (clampi(min(ww0, W - 1) - rw, 0, W - p.kw) - T.ws0);
+  q.nkeys = (wr1 - q.wr0) << LS;
+  q.ngroups = (q.nkeys + 15) / 16;
+  // the thread's two softmax queries (columns 2 t4, 2 t4 + 1)
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int qi = 2 * t4 + k;
+    const int hc = min(wh0 + qi / p.WW, H - 1), wc = min(ww0 + qi % p.WW, W - 1);
+    q.rlo[k] = clampi(hc - rh, 0, H - p.kh) - T.hs0 - q.wr0;
+    const int qsc = p.periodic ? (wc - T.w0) : (clampi(wc - rw, 0, W - p.kw) - T.ws0);
+    const uint32_t colmask = (0xFFFFFFFFu >> (32 - p.kw)) << max(qsc - q.wc0, 0);
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int col = (hf * 16 + g + 8 * i) & smask;
+        q.cbias[hf][k][i] = ((colmask >> col) & 1u) ? 0.f : -INFINITY;
+      }
+  }
+  // the query this thread loads and stores: query g
+  q.qh = wh0 + g / p.WW;
+  q.qw = ww0 + g % p.WW;
+  q.qvalid = (q.qh < H) && (q.qw < W);
+  const long N = (long)p.D * H * W;
+  const long C3 = 3L * p.C;
+  const long tok = ((long)T.d * H + min(q.qh, H - 1)) * W + min(q.qw, W - 1);
+  const __nv_bfloat16* q0 = p.qkv + ((long)T.b * N + tok) * C3 + T.head * DH;
+#pragma unroll
+  for (int kc = 0; kc < KC; ++kc) {
+    q.qb[kc][0] = *reinterpret_cast<const uint32_t*>(q0 + kc * 16 + 2 * t4);
+    q.qb[kc][1] = *reinterpret_cast<const uint32_t*>(q0 + kc * 16 + 8 + 2 * t4);
+  }
+#pragma unroll
+  for (int md = 0; md < MD; ++md) q.o[md][0] = q.o[md][1] = q.o[md][2] = q.o[md][3] = 0.f;
+  q.mrow[0] = q.mrow[1] = -INFINITY;
+  q.lrow[0] = q.lrow[1] = 0.f;
+}
+
+template <int DH, int LS, int GCH>
+__device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p, uint32_t sK32, uint32_t sV32,
+                                             int lane) {
+  constexpr int DHP = DH + 8, KC = DH / 16, MD = DH / 16;
+  constexpr int smask = (1 << LS) - 1;
+  const int WC = p.WC;
+  const int mi = lane >> 3;
+  const int g = lane >> 2;
+  for (int g0 = 0; g0 < q.ngroups; g0 += GCH) {
+    float s[GCH][4];
+#pragma unroll
+    for (int gi = 0; gi < GCH; ++gi) {
+      s[gi][0] = s[gi][1] = s[gi][2] = s[gi][3] = 0.f;
+      if (g0 + gi < q.ngroups) {
+        int jk = (g0 + gi) * 16 + (mi & 1) * 8 + (lane & 7);
+        if (jk >= q.nkeys) jk = 0;
+        const int krow = (q.wr0 + (jk >> LS)) * WC + q.wc0 + (jk & smask);
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc) {
+          uint32_t a0, a1, a2, a3;
+          ldsm_x4(sK32 + (uint32_t)((krow * DHP + kc * 16 + (mi >> 1) * 8) * 2), a0, a1, a2, a3);
+          mma_bf16(s[gi], a0, a1, a2, a3, q.qb[kc][0], q.qb[kc][1]);
+        }
+      }
+    }
+    // mask + scale, per-query chunk max
+    float mx[2] = {-INFINITY, -INFINITY};
+#pragma unroll
+    for (int gi = 0; gi < GCH; ++gi) {
+      const int gg = g0 + gi;
+      const bool live = gg < q.ngroups;
+      const int half = (LS == 5) ? (gg & 1) : 0;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int row = (gg * 16 + 8 * i + g) >> LS;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const bool rok = live && ((unsigned)(row - q.rlo[k]) < (unsigned)p.kh);
+          const float v = rok ? fmaf(s[gi][2 * i + k], p.scale_log2, q.cbias[half][k][i]) : -INFINITY;
+          s[gi][2 * i + k] = v;
+          mx[k] = fmaxf(mx[k], v);
+        }
+      }
+    }
+    float mref[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], 4));
+      mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], 8));
+      mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], 16));
+      const float mnew = fmaxf(q.mrow[k], mx[k]);
+      mref[k] = (mnew == -INFINITY) ? 0.f : mnew;
+      const float alpha = ex2(q.mrow[k] - mref[k]);
+      q.mrow[k] = mnew;
+      q.lrow[k] *= alpha;
+#pragma unroll
+      for (int md = 0; md < MD; ++md) {
+        q.o[md][k] *= alpha;
+        q.o[md][2 + k] *= alpha;
+      }
+    }
+    float lsum[2] = {0.f, 0.f};
+#pragma unroll
+    for (int gi = 0; gi < GCH; ++gi) {
+      if (g0 + gi >= q.ngroups) break;
+      float pr[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) pr[e] = ex2(s[gi][e] - mref[e & 1]);
+      lsum[0] += pr[0] + pr[2];
+      lsum[1] += pr[1] + pr[3];
+      // P^T blocks (keys 0-7 / 8-15 x queries) transposed into the B operand
+      const uint32_t b0 = movmatrix_t(pack_bf16(pr[0], pr[1]));
+      const uint32_t b1 = movmatrix_t(pack_bf16(pr[2], pr[3]));
+      int jv = (g0 + gi) * 16 + (mi >> 1) * 8 + (lane & 7);
+      if (jv >= q.nkeys) jv = 0;
+      const int vrow = (q.wr0 + (jv >> LS)) * WC + q.wc0 + (jv & smask);
+#pragma unroll
+      for (int md = 0; md < MD; ++md) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4_t(sV32 + (uint32_t)((vrow * DHP + md * 16 + (mi & 1) * 8) * 2), a0, a1, a2, a3);
+        mma_bf16(q.o[md], a0, a1, a2, a3, b0, b1);
+      }
+    }
+    q.lrow[0] += lsum[0];
+    q.lrow[1] += lsum[1];
+  }
+}
+
+template <int DH, int LS>
+__device__ __forceinline__ void warp_end_t(const WarpQT<DH, LS>& q, const Params& p, const Tile& T, int lane) {
+  constexpr int MD = DH / 16;
+  const int t4 = lane & 3;
+  float inv[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float l = q.lrow[k];
+    l += __shfl_xor_sync(0xffffffffu, l, 4);
+    l += __shfl_xor_sync(0xffffffffu, l, 8);
+    l += __shfl_xor_sync(0xffffffffu, l, 16);
+    inv[k] = 1.f / l;
+  }
+  const long N = (long)p.D * p.H * p.W;
+  __nv_bfloat16* orow = p.out + ((long)T.b * N + ((long)T.d * p.H + min(q.qh, p.H - 1)) * p.W +
+                                 min(q.qw, p.W - 1)) * p.C + T.head * DH;
+#pragma unroll
+  for (int md = 0; md < MD; ++md) {
+    // (dh rows x queries) blocks transposed to (query g, dh 2 t4 .. 2 t4 + 1)
+    const uint32_t lo = movmatrix_t(pack_bf16(q.o[md][0] * inv[0], q.o[md][1] * inv[1]));
+    const uint32_t hi = movmatrix_t(pack_bf16(q.o[md][2] * inv[0], q.o[md][3] * inv[1]));
+    if (q.qvalid) {
+      *reinterpret_cast<uint32_t*>(orow + md * 16 + 2 * t4) = lo;
+      *reinterpret_cast<uint32_t*>(orow + md * 16 + 8 + 2 * t4) = hi;
+    }
+  }
+}
+
+// The two arithmetic families behind one interface for the kernels.
+template <int DH, int LS, int GCH>
+struct ArithS {
+  using State = WarpQ<DH, LS>;
+  static __device__ __forceinline__ void begin(State& q, const Params& p, const Tile& T, int w, int l) {
+    warp_begin<DH, LS>(q, p, T, w, l);
+  }
+  static __device__ __forceinline__ void level(State& q, const Params& p, uint32_t k, uint32_t v, int l) {
+    warp_level<DH, LS, GCH>(q, p, k, v, l);
+  }
+  static __device__ __forceinline__ void end(const State& q, const Params& p, const Tile& T, int l) {
+    warp_end<DH, LS>(q, p, T, l);
+  }
+};
+template <int DH, int LS, int GCH>
+struct ArithT {
+  using State = WarpQT<DH, LS>;
+  static __device__ __forceinline__ void begin(State& q, const Params& p, const Tile& T, int w, int l) {
+    warp_begin_t<DH, LS>(q, p, T, w, l);
+  }
+  static __device__ __forceinline__ void level(State& q, const Params& p, uint32_t k, uint32_t v, int l) {
+    warp_level_t<DH, LS, GCH>(q, p, k, v, l);
+  }
+  static __device__ __forceinline__ void end(const State& q, const Params& p, const Tile& T, int l) {
+    warp_end_t<DH, LS>(q, p, T, l);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Kernel A: one CTA per tile; all threads load a level (cp.async, double
 // buffered), then all warps consume it; one CTA-wide barrier per level.
-template <int DH, int LS, int GCH, int MAXT>
+template <int DH, int LS, int GCH, int MAXT, bool TR = false>
 __global__ void __launch_bounds__(MAXT, 1) na_bf16_kernel(const Params p) {
+  using A = typename std::conditional<TR, ArithT<DH, LS, GCH>, ArithS<DH, LS, GCH>>::type;
   constexpr int DHP = DH + 8;
-  extern __shared__ __align__(16) __nv_bfloat16 sm[];
+  extern __shared__ __align__(128) __nv_bfloat16 sm_raw[];
+  __nv_bfloat16* sm = align128(sm_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const Tile T = make_tile(p, blockIdx.x);
-  const int slab = p.HRmax * p.WC * DHP;
-  WarpQ<DH, LS> q;
-  warp_begin<DH, LS>(q, p, T, warp, lane);
+  const int slab = p.slab;
+  typename A::State q;
+  A::begin(q, p, T, warp, lane);
   load_level<DH>(p, T, T.ld0, sm, slab, tid, blockDim.x);
   cp_async_commit();
   for (int li = 0; li < p.kd; ++li) {
@@ -377,10 +612,10 @@ __global__ void __launch_bounds__(MAXT, 1) na_bf16_kernel(const Params p) {
     cp_async_wait<1>();
     __syncthreads();
     const uint32_t sK32 = (uint32_t)__cvta_generic_to_shared(sm + (size_t)(li & 1) * 2 * slab);
-    if (q.live) warp_level<DH, LS, GCH>(q, p, sK32, sK32 + (uint32_t)slab * 2, lane);
+    if (q.live) A::level(q, p, sK32, sK32 + (uint32_t)slab * 2, lane);
     __syncthreads();
   }
-  if (q.live) warp_end<DH, LS>(q, p, T, lane);
+  if (q.live) A::end(q, p, T, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,16 +647,19 @@ __device__ __forceinline__ bool na_mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
-template <int DH, int LS, int GCH, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) na_bf16_pipe_kernel(const Params p, int ntiles, int* status) {
+template <int DH, int LS, int GCH, int MAXT, bool TR = false>
+__global__ void __launch_bounds__(MAXT, 1)
+    na_bf16_pipe_kernel(const Params p, int ntiles, int* status, const __grid_constant__ CUtensorMap tm_kv) {
+  using A = typename std::conditional<TR, ArithT<DH, LS, GCH>, ArithS<DH, LS, GCH>>::type;
   constexpr int DHP = DH + 8;
-  extern __shared__ __align__(16) __nv_bfloat16 sm[];
+  extern __shared__ __align__(128) __nv_bfloat16 sm_raw[];
+  __nv_bfloat16* sm = align128(sm_raw);
   __shared__ __align__(8) uint64_t full_bar[3];
   __shared__ __align__(8) uint64_t empty_bar[3];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int NW = p.NWH * p.NWW;      // consumer warps
   const int NBUF = p.nbuf;
-  const int slab = p.HRmax * p.WC * DHP;
+  const int slab = p.slab;
   if (tid == 0) {
     for (int i = 0; i < NBUF; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full_bar[i])), "r"(32) : "memory");
@@ -433,32 +671,62 @@ __global__ void __launch_bounds__(MAXT, 1) na_bf16_pipe_kernel(const Params p, i
 
   if (warp == NW) {
     // ------------------------------------------------------------- producer
+    // A slab whose longitudes do not wrap around the grid is one tensor copy
+    // for K and one for V (box = DH + 8 channels x WC x HRmax, which is the
+    // padded slab layout; the extra channels and rows are never read). A
+    // wrapping slab is copied 16 bytes at a time with cp.async. Either way
+    // the 32 lanes arrive on full[b] once.
+    if (p.tma && lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm_kv) : "memory");
+    const uint32_t box_bytes = (uint32_t)(p.HRmax * p.WC * DHP * 2);
     int it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const Tile T = make_tile(p, t);
-      for (int li = 0; li < p.kd; ++li, ++it) {
+      const bool bulk = p.tma && !(p.periodic && (T.ws0 < 0 || T.ws0 + p.WC > p.W));
+      for (int li = 0; li < p.kd; ++li) {
         const int buf = it % NBUF;
         const uint32_t ph = (uint32_t)(it / NBUF) & 1u;
         if (!na_mbar_wait(&empty_bar[buf], ph ^ 1u)) {
           ok = false;
           break;
         }
-        load_level<DH>(p, T, T.ld0 + li, sm + (size_t)buf * 2 * slab, slab, lane, 32);
-        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(&full_bar[buf]))
-                     : "memory");
+        const uint32_t fb = smem_addr(&full_bar[buf]);
+        __nv_bfloat16* dst = sm + (size_t)buf * 2 * slab;
+        if (bulk) {
+          if (lane == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * box_bytes)
+                         : "memory");
+            const int c0 = p.C + T.head * DH, lev = T.b * p.D + T.ld0 + li;
+#pragma unroll
+            for (int kv = 0; kv < 2; ++kv)
+              asm volatile(
+                  "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                  "[%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_addr(dst + (size_t)kv * slab)),
+                  "l"((uint64_t)&tm_kv), "r"(fb), "r"(c0 + kv * p.C), "r"(T.ws0), "r"(T.hs0), "r"(lev)
+                  : "memory");
+          } else {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fb) : "memory");
+          }
+        } else {
+          load_level<DH>(p, T, T.ld0 + li, dst, slab, lane, 32);
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(fb) : "memory");
+        }
+        ++it;
       }
     }
     if (!ok) atomicExch(status, (int)WM_ERR_TIMEOUT);
-    asm volatile("cp.async.wait_all;" ::: "memory");   // own copies land before this warp leaves
+    // own copies land before this warp leaves (the consumers may have given up)
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    for (int j = max(it - NBUF, 0); j < it; ++j)
+      if (!na_mbar_wait(&full_bar[j % NBUF], (uint32_t)(j / NBUF) & 1u)) atomicExch(status, (int)WM_ERR_TIMEOUT);
     return;
   }
   // ------------------------------------------------------------- consumers
   int it = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile T = make_tile(p, t);
-    WarpQ<DH, LS> q;
-    warp_begin<DH, LS>(q, p, T, warp, lane);
+    typename A::State q;
+    A::begin(q, p, T, warp, lane);
     for (int li = 0; li < p.kd; ++li, ++it) {
       const int buf = it % NBUF;
       const uint32_t ph = (uint32_t)(it / NBUF) & 1u;
@@ -467,31 +735,40 @@ __global__ void __launch_bounds__(MAXT, 1) na_bf16_pipe_kernel(const Params p, i
         return;
       }
       const uint32_t sK32 = smem_addr(sm + (size_t)buf * 2 * slab);
-      if (q.live) warp_level<DH, LS, GCH>(q, p, sK32, sK32 + (uint32_t)slab * 2, lane);
+      if (q.live) A::level(q, p, sK32, sK32 + (uint32_t)slab * 2, lane);
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty_bar[buf])) : "memory");
     }
-    if (q.live) warp_end<DH, LS>(q, p, T, lane);
+    if (q.live) A::end(q, p, T, lane);
   }
 }
 
 }  // namespace na
 
+template <int DH, bool TR>
+static wm_status prep_dh_family(int lim) {
+  constexpr int G = TR ? 8 : 4;   // the transposed family has one chunk size
+  if (!TR) {
+    WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 3, 8, 384>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 4, 8, 384>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 5, 8, 384>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 3, 8, 288>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 4, 8, 288>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 5, 8, 288>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  }
+  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 3, G, 512, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 4, G, 512, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 5, G, 512, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 3, G, 512, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 4, G, 512, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 5, G, 512, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  return WM_OK;
+}
+
 template <int DH>
 static wm_status prep_dh(int lim) {
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 3, 8, 384>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 4, 8, 384>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 5, 8, 384>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 3, 4, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 4, 4, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_kernel<DH, 5, 4, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 3, 8, 288>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 4, 8, 288>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 5, 8, 288>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 3, 4, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 4, 4, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  WM_CUDA(cudaFuncSetAttribute(na::na_bf16_pipe_kernel<DH, 5, 4, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  return WM_OK;
+  wm_status st = prep_dh_family<DH, false>(lim);
+  return st == WM_OK ? prep_dh_family<DH, true>(lim) : st;
 }
 
 static constexpr int kNaSmemLimit = 220 * 1024;   // dynamic smem the launcher may ask for
@@ -513,31 +790,43 @@ static int pow2span(int v) {
 
 namespace {
 
+// Arithmetic family of a plan: the formulation (S = Q K^T with 16 queries
+// per warp, or S^T = K Q^T with 8) and the softmax chunk. Both change the
+// rounding of a query's result, so a problem shape keeps the family it was
+// first tuned with; the CTA shape and the kernel kind do not.
 struct NaPlan {
   int NWH, NWW;  // consumer warp grid of a CTA (query tile = NWH*WH x NWW*WW)
   int kind;      // 0: one CTA per tile, CTA-wide barrier per level; 1: persistent producer/consumer
   int nbuf;      // slab buffers (kind 0: 2; kind 1: 2 or 3)
-  int gch;       // 16-key groups scored per softmax update (8, or 4 for 16-warp CTAs)
+  int gch;       // 16-key groups scored per softmax update
+  int tr;        // 1: transposed formulation
+  int WH, WW, span;   // warp patch and key-rectangle width (fixed by tr and the window)
 };
+
+int family(const NaPlan& pl) { return pl.gch | (pl.tr << 8); }
 
 using NaKey = std::array<int, 11>;
 std::mutex g_na_mu;
 std::map<NaKey, NaPlan> g_na_plans;  // autotuned plans
 std::map<NaKey, double> g_na_ms;     // their measured time per launch
-std::map<NaKey, int> g_na_gch;       // softmax chunk fixed per shape (key with B = 0) at its first tuning
+std::map<NaKey, int> g_na_family;    // arithmetic family fixed per shape (key with B = 0) at its first tuning
 std::string g_na_log;                 // every candidate's time, for the report
 
 NaKey na_key(int B, int D, int H, int W, int C, int heads, int kd, int kh, int kw, bool per) {
   return NaKey{B, D, H, W, C, heads, kd, kh, kw, per ? 1 : 0, 0};
 }
 
-// Warp patch (WH x WW queries) with the fewest issued keys per query per
-// level; fixed by the window alone, so a query's arithmetic (its key
-// rectangle and the order it is walked in) never depends on the CTA plan.
-bool warp_patch(int kh, int kw, int* WH, int* WW, int* span) {
-  const int cand[5][2] = {{1, 16}, {2, 8}, {4, 4}, {8, 2}, {16, 1}};
+// Warp patch (WH x WW queries; 16 queries, or 8 for the transposed
+// formulation) with the fewest issued keys per level; fixed by the window
+// alone, so a query's arithmetic (its key rectangle and the order it is
+// walked in) never depends on the CTA plan.
+bool warp_patch(int tr, int kh, int kw, int* WH, int* WW, int* span) {
+  static const int c16[5][2] = {{1, 16}, {2, 8}, {4, 4}, {8, 2}, {16, 1}};
+  static const int c8[4][2] = {{1, 8}, {2, 4}, {4, 2}, {8, 1}};
+  const int (*cand)[2] = tr ? c8 : c16;
+  const int n = tr ? 4 : 5;
   int best = -1, best_cost = 1 << 30;
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < n; ++i) {
     if (cand[i][1] + kw - 1 > 32) continue;
     const int cost = (cand[i][0] + kh - 1) * pow2span(cand[i][1] + kw - 1);
     if (cost < best_cost) {
@@ -552,61 +841,68 @@ bool warp_patch(int kh, int kw, int* WH, int* WW, int* span) {
   return true;
 }
 
-size_t plan_smem(const NaPlan& pl, int WH, int WW, int span, int kh, int H, int dh) {
-  const int hr = std::min(pl.NWH * WH + kh - 1, H);
-  const int wc = (pl.NWW - 1) * WW + span;
-  return (size_t)pl.nbuf * 2 * hr * wc * (dh + 8) * 2;
+// Elements of one K (or V) slab, rounded up to 128 bytes.
+int plan_slab(const NaPlan& pl, int kh, int H, int dh) {
+  const int hr = std::min(pl.NWH * pl.WH + kh - 1, H);
+  const int wc = (pl.NWW - 1) * pl.WW + pl.span;
+  return (hr * wc * (dh + 8) + 63) / 64 * 64;
 }
 
-// Candidate plans. gch = 0 allows both chunk sizes; otherwise only plans
-// with that chunk size (the chunk size changes where the online softmax
-// rescales, hence the rounding, so it is fixed per problem shape).
-std::vector<NaPlan> na_candidates(int WH, int WW, int span, int kh, int H, int dh, int gch) {
+// Dynamic shared memory of a plan: the slab ring plus 128 bytes of alignment slack.
+size_t plan_smem(const NaPlan& pl, int kh, int H, int dh) {
+  return (size_t)pl.nbuf * 2 * plan_slab(pl, kh, H, dh) * 2 + 128;
+}
+
+// Candidate plans of one arithmetic family (fam = 0: every family).
+std::vector<NaPlan> na_candidates(int kh, int kw, int H, int dh, int fam) {
   std::vector<NaPlan> out;
-  if (gch != 4) {
+  int WH, WW, span;
+  auto add = [&](int nwh, int nww, int kind, int nbuf, int gch, int tr) {
+    NaPlan pl{nwh, nww, kind, nbuf, gch, tr, WH, WW, span};
+    if (plan_smem(pl, kh, H, dh) <= (size_t)kNaSmemLimit) out.push_back(pl);
+  };
+  if ((fam == 0 || fam == 8) && warp_patch(0, kh, kw, &WH, &WW, &span)) {
     for (int nw : {8, 12})
-      for (int nwh = 1; nwh <= nw; ++nwh) {
-        if (nw % nwh) continue;
-        NaPlan pl{nwh, nw / nwh, 0, 2, 8};
-        if (plan_smem(pl, WH, WW, span, kh, H, dh) <= (size_t)kNaSmemLimit) out.push_back(pl);
-      }
+      for (int nwh = 1; nwh <= nw; ++nwh)
+        if (nw % nwh == 0) add(nwh, nw / nwh, 0, 2, 8, 0);
     for (int nbuf : {2, 3})
-      for (int nwh = 1; nwh <= 8; nwh *= 2) {
-        NaPlan pl{nwh, 8 / nwh, 1, nbuf, 8};
-        if (plan_smem(pl, WH, WW, span, kh, H, dh) <= (size_t)kNaSmemLimit) out.push_back(pl);
-      }
+      for (int nwh = 1; nwh <= 8; nwh *= 2) add(nwh, 8 / nwh, 1, nbuf, 8, 0);
   }
-  if (gch != 8) {
-    for (int nwh = 1; nwh <= 16; nwh *= 2) {
-      NaPlan pl{nwh, 16 / nwh, 0, 2, 4};
-      if (plan_smem(pl, WH, WW, span, kh, H, dh) <= (size_t)kNaSmemLimit) out.push_back(pl);
-    }
+  if ((fam == 0 || fam == 4) && warp_patch(0, kh, kw, &WH, &WW, &span)) {
+    for (int nwh = 1; nwh <= 16; nwh *= 2) add(nwh, 16 / nwh, 0, 2, 4, 0);
     for (int nw : {12, 15})
       for (int nbuf : {2, 3})
-        for (int nwh = 1; nwh <= nw; ++nwh) {
-          if (nw % nwh) continue;
-          NaPlan pl{nwh, nw / nwh, 1, nbuf, 4};
-          if (plan_smem(pl, WH, WW, span, kh, H, dh) <= (size_t)kNaSmemLimit) out.push_back(pl);
-        }
+        for (int nwh = 1; nwh <= nw; ++nwh)
+          if (nw % nwh == 0) add(nwh, nw / nwh, 1, nbuf, 4, 0);
+  }
+  if ((fam == 0 || fam == (8 | 256)) && warp_patch(1, kh, kw, &WH, &WW, &span)) {
+    for (int nw : {8, 16})
+      for (int nwh = 1; nwh <= nw; nwh *= 2) add(nwh, nw / nwh, 0, 2, 8, 1);
+    for (int nw : {8, 12, 15})
+      for (int nbuf : {2, 3})
+        for (int nwh = 1; nwh <= nw; ++nwh)
+          if (nw % nwh == 0) add(nwh, nw / nwh, 1, nbuf, 8, 1);
   }
   return out;
 }
 
-// Heuristic when no tuned plan exists: fewest staged keys per query times
+// Heuristic when no tuned plan exists, among the plans of family `fam` (and
+// kernel kind `kind`, unless it is -1): fewest staged keys per query times
 // tile waste; persistent plans are preferred when the tile count gives every
 // SM several tiles.
-NaPlan na_heuristic(int B, int D, int H, int W, int heads, int WH, int WW, int span, int kh, int dh) {
-  NaPlan best{0, 0, 0, 2, 8};
+NaPlan na_heuristic(int B, int D, int H, int W, int heads, int kh, int kw, int dh, int fam, int kind) {
+  NaPlan best{};
   double best_score = 1e30;
-  for (const NaPlan& pl : na_candidates(WH, WW, span, kh, H, dh, 8)) {
-    const int TH = pl.NWH * WH, TW = pl.NWW * WW;
+  for (const NaPlan& pl : na_candidates(kh, kw, H, dh, fam)) {
+    if (kind >= 0 && pl.kind != kind) continue;
+    const int TH = pl.NWH * pl.WH, TW = pl.NWW * pl.WW;
     const int th = (H + TH - 1) / TH, tw = (W + TW - 1) / TW;
-    const int hr = std::min(TH + kh - 1, H), wc = (pl.NWW - 1) * WW + span;
+    const int hr = std::min(TH + kh - 1, H), wc = (pl.NWW - 1) * pl.WW + pl.span;
     const long ctas = (long)th * tw * D * B * heads;
     double score = (double)hr * wc / (TH * TW) * ((double)th * TH / H) * ((double)tw * TW / W);
     if (ctas < num_sms()) score *= (double)num_sms() / ctas;   // idle SMs
-    if (pl.kind == 1) score *= (ctas >= 4L * num_sms()) ? 0.8 : 1.5;
-    score /= std::sqrt((double)(pl.NWH * pl.NWW) / 8.0);      // more warps hide more latency
+    if (pl.kind == 1 && kind < 0) score *= (ctas >= 4L * num_sms()) ? 0.8 : 1.5;
+    score /= std::sqrt((double)(pl.NWH * pl.NWW * pl.WH * pl.WW) / 128.0);   // more warps hide more latency
     if (score < best_score) {
       best_score = score;
       best = pl;
@@ -615,70 +911,76 @@ NaPlan na_heuristic(int B, int D, int H, int W, int heads, int WH, int WW, int s
   return best;
 }
 
+template <int DH, int LS, int G, int MT, bool TR>
+void launch_tile(const na::Params& p, long ntiles, int smem, cudaStream_t s) {
+  na::na_bf16_kernel<DH, LS, G, MT, TR><<<(unsigned)ntiles, 32 * p.NWH * p.NWW, smem, s>>>(p);
+}
+
+template <int DH, int LS, int G, int MT, bool TR>
+void launch_pipe(const na::Params& p, const CUtensorMap& tm, long ntiles, int smem, cudaStream_t s) {
+  const int grid = (int)std::min<long>(ntiles, num_sms());
+  na::na_bf16_pipe_kernel<DH, LS, G, MT, TR>
+      <<<grid, 32 * (p.NWH * p.NWW + 1), smem, s>>>(p, (int)ntiles, device_status_word(), tm);
+}
+
+template <int DH, int LS>
+void launch_family(const NaPlan& pl, const na::Params& p, const CUtensorMap& tm, long ntiles, int smem,
+                   cudaStream_t s) {
+  if (pl.tr) {
+    if (pl.kind == 0) launch_tile<DH, LS, 8, 512, true>(p, ntiles, smem, s);
+    else launch_pipe<DH, LS, 8, 512, true>(p, tm, ntiles, smem, s);
+  } else if (pl.gch == 4) {
+    if (pl.kind == 0) launch_tile<DH, LS, 4, 512, false>(p, ntiles, smem, s);
+    else launch_pipe<DH, LS, 4, 512, false>(p, tm, ntiles, smem, s);
+  } else {
+    if (pl.kind == 0) launch_tile<DH, LS, 8, 384, false>(p, ntiles, smem, s);
+    else launch_pipe<DH, LS, 8, 288, false>(p, tm, ntiles, smem, s);
+  }
+}
+
 template <int DH>
-wm_status launch_plan(const NaPlan& pl, na::Params p, int WH, int WW, int span, cudaStream_t s) {
-  p.WH = WH;
-  p.WW = WW;
+wm_status launch_plan(const NaPlan& pl, na::Params p, cudaStream_t s) {
+  p.WH = pl.WH;
+  p.WW = pl.WW;
   p.log2span = 0;
-  while ((1 << p.log2span) < span) ++p.log2span;
+  while ((1 << p.log2span) < pl.span) ++p.log2span;
   p.NWH = pl.NWH;
   p.NWW = pl.NWW;
   p.nbuf = pl.nbuf;
   p.HRmax = std::min(p.NWH * p.WH + p.kh - 1, p.H);
-  p.WC = (p.NWW - 1) * p.WW + span;
+  p.WC = (p.NWW - 1) * p.WW + pl.span;
   const int TH = p.NWH * p.WH, TW = p.NWW * p.WW;
   const int tiles_h = (p.H + TH - 1) / TH;
   p.tiles_w = (p.W + TW - 1) / TW;
   p.scale_log2 = 1.4426950408889634f / sqrtf((float)DH);
   const long ntiles = (long)tiles_h * p.tiles_w * p.D * p.B * p.heads;
   if (ntiles > (1L << 30)) return fail(WM_ERR_INVALID_ARG, "too many attention tiles");
-  const int smem = (int)plan_smem(pl, WH, WW, span, p.kh, p.H, DH);
-  if (pl.kind == 0 && pl.gch == 8) {
-    dim3 grid((unsigned)ntiles), block(32 * p.NWH * p.NWW);
-    switch (p.log2span) {
-      case 3: na::na_bf16_kernel<DH, 3, 8, 384><<<grid, block, smem, s>>>(p); break;
-      case 4: na::na_bf16_kernel<DH, 4, 8, 384><<<grid, block, smem, s>>>(p); break;
-      case 5: na::na_bf16_kernel<DH, 5, 8, 384><<<grid, block, smem, s>>>(p); break;
-      default: return fail(WM_ERR_INVALID_ARG, "unsupported key rectangle width");
-    }
-  } else if (pl.kind == 0) {
-    dim3 grid((unsigned)ntiles), block(32 * p.NWH * p.NWW);
-    switch (p.log2span) {
-      case 3: na::na_bf16_kernel<DH, 3, 4, 512><<<grid, block, smem, s>>>(p); break;
-      case 4: na::na_bf16_kernel<DH, 4, 4, 512><<<grid, block, smem, s>>>(p); break;
-      case 5: na::na_bf16_kernel<DH, 5, 4, 512><<<grid, block, smem, s>>>(p); break;
-      default: return fail(WM_ERR_INVALID_ARG, "unsupported key rectangle width");
-    }
-  } else {
-    const int grid = (int)std::min<long>(ntiles, num_sms());
-    dim3 block(32 * (p.NWH * p.NWW + 1));
-    int* st = device_status_word();
-    if (pl.gch == 8) {
-      switch (p.log2span) {
-        case 3: na::na_bf16_pipe_kernel<DH, 3, 8, 288><<<grid, block, smem, s>>>(p, (int)ntiles, st); break;
-        case 4: na::na_bf16_pipe_kernel<DH, 4, 8, 288><<<grid, block, smem, s>>>(p, (int)ntiles, st); break;
-        case 5: na::na_bf16_pipe_kernel<DH, 5, 8, 288><<<grid, block, smem, s>>>(p, (int)ntiles, st); break;
-        default: return fail(WM_ERR_INVALID_ARG, "unsupported key rectangle width");
-      }
-    } else {
-      switch (p.log2span) {
-        case 3: na::na_bf16_pipe_kernel<DH, 3, 4, 512><<<grid, block, smem, s>>>(p, (int)ntiles, st); break;
-        case 4: na::na_bf16_pipe_kernel<DH, 4, 4, 512><<<grid, block, smem, s>>>(p, (int)ntiles, st); break;
-        case 5: na::na_bf16_pipe_kernel<DH, 5, 4, 512><<<grid, block, smem, s>>>(p, (int)ntiles, st); break;
-        default: return fail(WM_ERR_INVALID_ARG, "unsupported key rectangle width");
-      }
-    }
+  const int nthreads = 32 * (p.NWH * p.NWW + (pl.kind == 1 ? 1 : 0));
+  const int maxt = (pl.tr || pl.gch == 4) ? 512 : (pl.kind == 0 ? 384 : 288);
+  if (nthreads > maxt) return fail(WM_ERR_INVALID_ARG, "attention plan exceeds its kernel's thread limit");
+  const int smem = (int)plan_smem(pl, p.kh, p.H, DH);
+  p.slab = plan_slab(pl, p.kh, p.H, DH);
+  // The persistent kernel copies non-wrapping slabs with the tensor engine.
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof tm);
+  p.tma = pl.kind == 1 && make_tmap_qkv_slab(&tm, p.qkv, 3ull * p.C, p.W, p.H, (uint64_t)p.D * p.B, DH + 8, p.WC,
+                                              p.HRmax) ? 1 : 0;
+  switch (p.log2span) {
+    case 3: launch_family<DH, 3>(pl, p, tm, ntiles, smem, s); break;
+    case 4: launch_family<DH, 4>(pl, p, tm, ntiles, smem, s); break;
+    case 5: launch_family<DH, 5>(pl, p, tm, ntiles, smem, s); break;
+    default: return fail(WM_ERR_INVALID_ARG, "unsupported key rectangle width");
   }
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
-wm_status launch_with(const NaPlan& pl, const na::Params& p, int dh, int WH, int WW, int span, cudaStream_t s) {
+wm_status launch_with(const NaPlan& pl, const na::Params& p, int dh, cudaStream_t s) {
   switch (dh) {
-    case 16: return launch_plan<16>(pl, p, WH, WW, span, s);
-    case 32: return launch_plan<32>(pl, p, WH, WW, span, s);
-    case 48: return launch_plan<48>(pl, p, WH, WW, span, s);
-    case 64: return launch_plan<64>(pl, p, WH, WW, span, s);
+    case 16: return launch_plan<16>(pl, p, s);
+    case 32: return launch_plan<32>(pl, p, s);
+    case 48: return launch_plan<48>(pl, p, s);
+    case 64: return launch_plan<64>(pl, p, s);
     default: return fail(WM_ERR_INVALID_ARG, "BF16 attention needs head dim 16, 32, 48 or 64");
   }
 }
@@ -696,57 +998,59 @@ na::Params make_params(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int 
 }  // namespace
 
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C, int heads,
-                         int kd, int kh, int kw, bool periodic, cudaStream_t s) {
+                         int kd, int kh, int kw, bool periodic, cudaStream_t s, int variant) {
   if (B <= 0) return WM_OK;
+  if ((reinterpret_cast<uintptr_t>(qkv) | reinterpret_cast<uintptr_t>(out)) & 15)
+    return fail(WM_ERR_INVALID_ARG, "BF16 attention needs 16-byte aligned qkv and out");
   const int dh = C / heads;
   int WH, WW, span;
-  if (!warp_patch(kh, kw, &WH, &WW, &span))
+  if (!warp_patch(0, kh, kw, &WH, &WW, &span))
     return fail(WM_ERR_INVALID_ARG, "longitude window too wide for the BF16 attention kernel");
-  NaPlan pl{0, 0, 0, 2, 8};
-  int gch = 8;
-  {
+  NaPlan pl{};
+  int fam = 8, kind = -1;
+  if (variant != 0) {
+    static const int fams[4] = {0, 8, 4, 8 | 256};
+    fam = fams[variant & 3];
+    kind = (variant & 4) ? 0 : (variant & 8) ? 1 : -1;
+  } else {
     std::lock_guard<std::mutex> lk(g_na_mu);
     auto it = g_na_plans.find(na_key(B, D, H, W, C, heads, kd, kh, kw, periodic));
     if (it != g_na_plans.end()) pl = it->second;
-    auto ig = g_na_gch.find(na_key(0, D, H, W, C, heads, kd, kh, kw, periodic));
-    if (ig != g_na_gch.end()) gch = ig->second;
+    auto ig = g_na_family.find(na_key(0, D, H, W, C, heads, kd, kh, kw, periodic));
+    if (ig != g_na_family.end()) fam = ig->second;
   }
-  if (!pl.NWH) {
-    pl = na_heuristic(B, D, H, W, heads, WH, WW, span, kh, dh);
-    if (gch == 4) {   // keep the shape's chunk size: the widest 16-warp plan that fits
-      for (const NaPlan& c : na_candidates(WH, WW, span, kh, H, dh, 4)) pl = c;
-    }
-  }
+  if (!pl.NWH) pl = na_heuristic(B, D, H, W, heads, kh, kw, dh, fam, kind);
   if (!pl.NWH) return fail(WM_ERR_INVALID_ARG, "attention window too large for the BF16 attention kernel");
-  return launch_with(pl, make_params(qkv, out, B, D, H, W, C, heads, kd, kh, kw, periodic), dh, WH, WW, span, s);
+  return launch_with(pl, make_params(qkv, out, B, D, H, W, C, heads, kd, kh, kw, periodic), dh, s);
 }
 
 // Time every candidate CTA plan for this shape (1 warm-up + 3 timed launches
 // each, CUDA events on `s`) and keep the fastest for later launches. The
-// outputs are written to `out`; results do not depend on the plan.
+// outputs are written to `out`; results depend only on the arithmetic family,
+// which the first tuning of a shape fixes for every later batch size.
 wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
                            int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s, double* best_ms) {
   const int dh = C / heads;
   int WH, WW, span;
-  if (!warp_patch(kh, kw, &WH, &WW, &span)) return fail(WM_ERR_INVALID_ARG, "window too wide");
+  if (!warp_patch(0, kh, kw, &WH, &WW, &span)) return fail(WM_ERR_INVALID_ARG, "window too wide");
   const na::Params p = make_params(qkv, out, B, D, H, W, C, heads, kd, kh, kw, periodic);
   cudaEvent_t e0, e1;
   WM_CUDA(cudaEventCreate(&e0));
   WM_CUDA(cudaEventCreate(&e1));
-  NaPlan best{0, 0, 0, 2, 8};
+  NaPlan best{};
   float best_t = 1e30f;
   wm_status st = WM_OK;
-  int gch_fixed = 0;
+  int fam_fixed = 0;
   {
     std::lock_guard<std::mutex> lk(g_na_mu);
-    auto ig = g_na_gch.find(na_key(0, D, H, W, C, heads, kd, kh, kw, periodic));
-    if (ig != g_na_gch.end()) gch_fixed = ig->second;
+    auto ig = g_na_family.find(na_key(0, D, H, W, C, heads, kd, kh, kw, periodic));
+    if (ig != g_na_family.end()) fam_fixed = ig->second;
   }
-  for (const NaPlan& pl : na_candidates(WH, WW, span, kh, H, dh, gch_fixed)) {
-    st = launch_with(pl, p, dh, WH, WW, span, s);
+  for (const NaPlan& pl : na_candidates(kh, kw, H, dh, fam_fixed)) {
+    st = launch_with(pl, p, dh, s);
     if (st != WM_OK) break;
     cudaEventRecord(e0, s);
-    for (int r = 0; r < 3 && st == WM_OK; ++r) st = launch_with(pl, p, dh, WH, WW, span, s);
+    for (int r = 0; r < 3 && st == WM_OK; ++r) st = launch_with(pl, p, dh, s);
     cudaEventRecord(e1, s);
     if (st != WM_OK) break;
     if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -756,9 +1060,10 @@ wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, 
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     {
-      char line[160];
-      std::snprintf(line, sizeof line, "  candidate B=%d %s warps=%dx%d buffers=%d chunk=%d: %.3f ms\n", B,
-                    pl.kind ? "persistent" : "per-tile", pl.NWH, pl.NWW, pl.nbuf, pl.gch, ms / 3.0);
+      char line[200];
+      std::snprintf(line, sizeof line, "  candidate B=%d %s %s warps=%dx%d patch=%dx%d buffers=%d chunk=%d: %.3f ms\n",
+                    B, pl.tr ? "K.Q^T" : "Q.K^T", pl.kind ? "persistent" : "per-tile", pl.NWH, pl.NWW, pl.WH, pl.WW,
+                    pl.nbuf, pl.gch, ms / 3.0);
       std::lock_guard<std::mutex> lk(g_na_mu);
       g_na_log += line;
     }
@@ -774,7 +1079,7 @@ wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, 
     std::lock_guard<std::mutex> lk(g_na_mu);
     g_na_plans[na_key(B, D, H, W, C, heads, kd, kh, kw, periodic)] = best;
     g_na_ms[na_key(B, D, H, W, C, heads, kd, kh, kw, periodic)] = best_t / 3.0;
-    g_na_gch.emplace(na_key(0, D, H, W, C, heads, kd, kh, kw, periodic), best.gch);
+    g_na_family.emplace(na_key(0, D, H, W, C, heads, kd, kh, kw, periodic), family(best));
   }
   if (best_ms) *best_ms = best_t / 3.0;
   return WM_OK;
@@ -788,10 +1093,10 @@ std::string describe_na_plans() {
     const NaPlan& pl = kv.second;
     char line[256];
     std::snprintf(line, sizeof line,
-                  "attention B=%d D=%d H=%d W=%d C=%d heads=%d window=%dx%dx%d periodic=%d -> %s warps=%dx%d "
-                  "buffers=%d chunk=%d %.3f ms\n",
-                  k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8], k[9],
-                  pl.kind ? "persistent" : "per-tile", pl.NWH, pl.NWW, pl.nbuf, pl.gch, g_na_ms[k]);
+                  "attention B=%d D=%d H=%d W=%d C=%d heads=%d window=%dx%dx%d periodic=%d -> %s %s warps=%dx%d "
+                  "patch=%dx%d buffers=%d chunk=%d %.3f ms\n",
+                  k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8], k[9], pl.tr ? "K.Q^T" : "Q.K^T",
+                  pl.kind ? "persistent" : "per-tile", pl.NWH, pl.NWW, pl.WH, pl.WW, pl.nbuf, pl.gch, g_na_ms[k]);
     out += line;
   }
   return out + g_na_log;

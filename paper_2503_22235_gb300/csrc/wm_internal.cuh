@@ -86,6 +86,11 @@ wm_status launch_na_f32(const float* qkv, float* out, int B, int D, int H, int W
                         int kh, int kw, bool periodic, cudaStream_t s);
 
 // ------------------------------------------------------------ bf16 path ----
+// 4D map over a qkv buffer [DB = batch * levels][H][W][C3] (bf16) whose box
+// is (box_c channels, box_w longitudes, box_h latitudes, 1 level): one
+// attention key slab. Out-of-range elements read as zero.
+bool make_tmap_qkv_slab(CUtensorMap* map, const void* qkv, uint64_t C3, uint64_t W, uint64_t H, uint64_t DB,
+                        uint32_t box_c, uint32_t box_w, uint32_t box_h);
 // TMA descriptor of a row-major bf16 matrix [rows, cols] (cols contiguous),
 // box = box_rows x 64 columns, 128-byte swizzle.
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows);
@@ -123,8 +128,9 @@ struct GemmArgs {
 wm_status launch_rope_f32(float* qkv, long M, const RopeArgs* rope_dev, const RopeArgs& rope_host, cudaStream_t s);
 wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
 
+// variant: WM_NA_* of wm.h (0 = tuned plan / the shape's fixed family).
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
-                         int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s);
+                         int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s, int variant = 0);
 // One line per autotuned attention shape: the plan chosen and its time.
 std::string describe_na_plans();
 // Times the candidate CTA plans of the attention kernel for this exact shape

@@ -153,18 +153,62 @@ def test_neighborhood_attention_fp32(case):
     assert rel(host(out).reshape(B, -1, C), ref) < 1e-6
 
 
-@pytest.mark.parametrize("case", NA_CASES)
-def test_neighborhood_attention_bf16(case):
+_NA_REF = {}
+
+
+def _na_bf16_ref(case):
+    """Oracle attention on the bf16-rounded inputs of `case` (cached per case)."""
+    if case not in _NA_REF:
+        B, D, H, W, C, heads, kd, kh, kw, per = case
+        q = bf16_round(_na_inputs(B, D, H, W, C, 2))
+        nbr = orc.neighbor_index(D, H, W, kd, kh, kw, per)
+        _NA_REF[case] = orc.neighborhood_attention(q[..., :C], q[..., C:2 * C], q[..., 2 * C:], heads, nbr)
+    return _NA_REF[case]
+
+
+def _na_bf16_run(case, variant):
     B, D, H, W, C, heads, kd, kh, kw, per = case
     qkv = _na_inputs(B, D, H, W, C, 2)
     out = torch.empty(B * D * H * W, C, device=CUDA, dtype=torch.bfloat16)
     wm.wm_op_neighborhood_attention(dev(qkv, torch.bfloat16), out, B, D, H, W, C, heads, kd, kh, kw, per,
-                                    wm.WM_PREC_BF16)
-    q = bf16_round(qkv)
-    nbr = orc.neighbor_index(D, H, W, kd, kh, kw, per)
-    ref = orc.neighborhood_attention(q[..., :C], q[..., C:2 * C], q[..., 2 * C:], heads, nbr)
-    err = rel(host(out).reshape(B, -1, C), ref)
+                                    wm.WM_PREC_BF16, variant)
+    torch.cuda.synchronize()
+    return out
+
+
+NA_VARIANTS = [wm.WM_NA_AUTO] + [fam | kind for fam in (wm.WM_NA_QK_CHUNK8, wm.WM_NA_QK_CHUNK4, wm.WM_NA_KQ)
+                                 for kind in (wm.WM_NA_PER_TILE, wm.WM_NA_PERSISTENT)]
+
+
+@pytest.mark.parametrize("variant", NA_VARIANTS)
+@pytest.mark.parametrize("case", NA_CASES)
+def test_neighborhood_attention_bf16(case, variant):
+    B, C = case[0], case[4]
+    out = _na_bf16_run(case, variant)
+    err = rel(host(out).reshape(B, -1, C), _na_bf16_ref(case))
     assert err < 1e-2, err
+
+
+@pytest.mark.parametrize("fam", [wm.WM_NA_QK_CHUNK8, wm.WM_NA_QK_CHUNK4, wm.WM_NA_KQ])
+@pytest.mark.parametrize("case", NA_CASES[2:5])
+def test_neighborhood_attention_kernel_kind_does_not_change_results(case, fam):
+    """Within one arithmetic family the per-tile and the persistent kernel,
+    with any CTA shape, produce bit-identical outputs."""
+    a = _na_bf16_run(case, fam | wm.WM_NA_PER_TILE)
+    b = _na_bf16_run(case, fam | wm.WM_NA_PERSISTENT)
+    assert torch.equal(a, b)
+
+
+def test_neighborhood_attention_rejects_bad_variants():
+    case = NA_CASES[0]
+    for v in (-1, 16, wm.WM_NA_PER_TILE, wm.WM_NA_KQ | 12):
+        with pytest.raises(wm.WmError):
+            _na_bf16_run(case, v)
+    B, D, H, W, C, heads, kd, kh, kw, per = case
+    out = torch.empty(B * D * H * W, C, device=CUDA)
+    with pytest.raises(wm.WmError):
+        wm.wm_op_neighborhood_attention(dev(_na_inputs(B, D, H, W, C, 1)), out, B, D, H, W, C, heads, kd, kh, kw,
+                                        per, wm.WM_PREC_FP32, wm.WM_NA_KQ)
 
 
 # ------------------------------------------------------- block / processor ---
