@@ -81,6 +81,44 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&p);
 }
 
+// Paired FP32 arithmetic (f32x2 instructions: one instruction, two lanes,
+// each rounded exactly as the scalar instruction) and a three-input max.
+__device__ __forceinline__ uint64_t pack_f2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+// (d0, d1) = (a0, a1) * b2 + c2
+__device__ __forceinline__ void fma_f2(float& d0, float& d1, float a0, float a1, uint64_t b2, uint64_t c2) {
+  asm("{\n .reg .b64 ra, rd;\n mov.b64 ra, {%2, %3};\n fma.rn.f32x2 rd, ra, %4, %5;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "l"(b2), "l"(c2));
+}
+// (d0, d1) = (a0, a1) - b2
+__device__ __forceinline__ void sub_f2(float& d0, float& d1, float a0, float a1, uint64_t b2) {
+  asm("{\n .reg .b64 ra, rd;\n mov.b64 ra, {%2, %3};\n sub.rn.f32x2 rd, ra, %4;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "l"(b2));
+}
+// (d0, d1) = (a0, a1) + (b0, b1)
+__device__ __forceinline__ void add_f2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n add.rn.f32x2 rd, ra, rb;\n"
+      " mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+// (x0, x1) *= b2
+__device__ __forceinline__ void mul_f2(float& x0, float& x1, uint64_t b2) {
+  asm("{\n .reg .b64 ra, rd;\n mov.b64 ra, {%2, %3};\n mul.rn.f32x2 rd, ra, %4;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(x0), "=f"(x1)
+      : "f"(x0), "f"(x1), "l"(b2));
+}
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 // First 128-byte aligned address at or after p (the launch adds 128 bytes).
 __device__ __forceinline__ __nv_bfloat16* align128(__nv_bfloat16* p) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
@@ -166,7 +204,7 @@ struct WarpQ {
   float o[ND][4];
   float mrow[2], lrow[2];
   int rlo[2];
-  float cbias[2][2][2][2];
+  uint64_t cbias[2][2][2];   // [half][n8 block][row]: packed (0 or -inf) pair for entries 2 t4, 2 t4 + 1
   int wr0, wc0, nkeys, ngroups;
   int qh[2], qw[2];
   bool qvalid[2];
@@ -210,12 +248,15 @@ __device__ __forceinline__ void warp_begin(WarpQ<DH, LS>& q, const Params& p, co
 #pragma unroll
     for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr)
+      for (int rr = 0; rr < 2; ++rr) {
+        float cb[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int col = (hf * 16 + nb * 8 + 2 * t4 + e) & smask;
-          q.cbias[hf][nb][rr][e] = ((colmask[rr] >> col) & 1u) ? 0.f : -INFINITY;
+          cb[e] = ((colmask[rr] >> col) & 1u) ? 0.f : -INFINITY;
         }
+        q.cbias[hf][nb][rr] = pack_f2(cb[0], cb[1]);
+      }
   const long N = (long)p.D * H * W;
   const long C3 = 3L * p.C;
   const __nv_bfloat16* base = p.qkv + (long)T.b * N * C3;
@@ -267,7 +308,9 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
     // column j & smask. The column of each accumulator entry depends on the
     // group only through (g & 1) for 32-wide rectangles, so the column test
     // is a precomputed additive bias (0 or -inf); the row test is one
-    // unsigned compare per n8 block.
+    // unsigned compare per n8 block. Entries 2 t4 and 2 t4 + 1 of a row go
+    // through the paired instructions together.
+    const uint64_t scale2 = pack_f2(p.scale_log2, p.scale_log2);
     float gmx[GCH][2];
 #pragma unroll
     for (int gi = 0; gi < GCH; ++gi) {
@@ -280,33 +323,35 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
         for (int rr = 0; rr < 2; ++rr) {
           const bool rok = live && ((unsigned)(row - q.rlo[rr]) < (unsigned)p.kh);
           const int half = (LS == 5) ? (gg & 1) : 0;
-          const float cb0 = q.cbias[half][nb][rr][0], cb1 = q.cbias[half][nb][rr][1];
-          s[gi][nb][2 * rr] = rok ? fmaf(s[gi][nb][2 * rr], p.scale_log2, cb0) : -INFINITY;
-          s[gi][nb][2 * rr + 1] = rok ? fmaf(s[gi][nb][2 * rr + 1], p.scale_log2, cb1) : -INFINITY;
+          float t0, t1;
+          fma_f2(t0, t1, s[gi][nb][2 * rr], s[gi][nb][2 * rr + 1], scale2, q.cbias[half][nb][rr]);
+          s[gi][nb][2 * rr] = rok ? t0 : -INFINITY;
+          s[gi][nb][2 * rr + 1] = rok ? t1 : -INFINITY;
         }
       }
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr)
-        gmx[gi][rr] = fmaxf(fmaxf(s[gi][0][2 * rr], s[gi][0][2 * rr + 1]), fmaxf(s[gi][1][2 * rr], s[gi][1][2 * rr + 1]));
+        gmx[gi][rr] = max3(max3(s[gi][0][2 * rr], s[gi][0][2 * rr + 1], s[gi][1][2 * rr]), s[gi][1][2 * rr + 1],
+                           -INFINITY);
     }
     float mref[2];
+    uint64_t mref2[2];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {   // tree over the groups, then the quad
-      float mx = fmaxf(fmaxf(gmx[0][rr], gmx[1][rr]), fmaxf(gmx[2][rr], gmx[3][rr]));
+      float mx = max3(max3(gmx[0][rr], gmx[1][rr], gmx[2][rr]), gmx[3][rr], -INFINITY);
       if constexpr (GCH == 8)
-        mx = fmaxf(mx, fmaxf(fmaxf(gmx[4][rr], gmx[5][rr]), fmaxf(gmx[6][rr], gmx[7][rr])));
+        mx = max3(max3(mx, gmx[4][rr], gmx[5][rr]), gmx[6][rr], gmx[7][rr]);
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
       const float mnew = fmaxf(q.mrow[rr], mx);
       mref[rr] = (mnew == -INFINITY) ? 0.f : mnew;
+      mref2[rr] = pack_f2(mref[rr], mref[rr]);
       const float alpha = ex2(q.mrow[rr] - mref[rr]);
+      const uint64_t alpha2 = pack_f2(alpha, alpha);
       q.mrow[rr] = mnew;
       q.lrow[rr] *= alpha;
 #pragma unroll
-      for (int nd = 0; nd < ND; ++nd) {
-        q.o[nd][2 * rr] *= alpha;
-        q.o[nd][2 * rr + 1] *= alpha;
-      }
+      for (int nd = 0; nd < ND; ++nd) mul_f2(q.o[nd][2 * rr], q.o[nd][2 * rr + 1], alpha2);
     }
     // P = exp2(S - m), row sums (per thread; quad-reduced at the end), O += P V
     float lsum[GCH][2];
@@ -320,9 +365,17 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
 #pragma unroll
       for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) pr[nb][e] = ex2(s[gi][nb][e] - mref[e >> 1]);
-      lsum[gi][0] = (pr[0][0] + pr[0][1]) + (pr[1][0] + pr[1][1]);
-      lsum[gi][1] = (pr[0][2] + pr[0][3]) + (pr[1][2] + pr[1][3]);
+        for (int rr = 0; rr < 2; ++rr) {
+          float d0, d1;
+          sub_f2(d0, d1, s[gi][nb][2 * rr], s[gi][nb][2 * rr + 1], mref2[rr]);
+          pr[nb][2 * rr] = ex2(d0);
+          pr[nb][2 * rr + 1] = ex2(d1);
+        }
+      // lsum[r] = (pr[0][2r] + pr[0][2r+1]) + (pr[1][2r] + pr[1][2r+1]), both rows at once
+      float a0, a1, b0, b1;
+      add_f2(a0, a1, pr[0][0], pr[0][2], pr[0][1], pr[0][3]);
+      add_f2(b0, b1, pr[1][0], pr[1][2], pr[1][1], pr[1][3]);
+      add_f2(lsum[gi][0], lsum[gi][1], a0, a1, b0, b1);
       const uint32_t pa0 = pack_bf16(pr[0][0], pr[0][1]);
       const uint32_t pa1 = pack_bf16(pr[0][2], pr[0][3]);
       const uint32_t pa2 = pack_bf16(pr[1][0], pr[1][1]);
@@ -338,11 +391,19 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
         mma_bf16(q.o[nd + 1], pa0, pa1, pa2, pa3, b2, b3);
       }
     }
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-      float t = (lsum[0][rr] + lsum[1][rr]) + (lsum[2][rr] + lsum[3][rr]);
-      if constexpr (GCH == 8) t += (lsum[4][rr] + lsum[5][rr]) + (lsum[6][rr] + lsum[7][rr]);
-      q.lrow[rr] += t;
+    {
+      float t0, t1, u0, u1;
+      add_f2(t0, t1, lsum[0][0], lsum[0][1], lsum[1][0], lsum[1][1]);
+      add_f2(u0, u1, lsum[2][0], lsum[2][1], lsum[3][0], lsum[3][1]);
+      add_f2(t0, t1, t0, t1, u0, u1);
+      if constexpr (GCH == 8) {
+        float v0, v1, w0, w1;
+        add_f2(v0, v1, lsum[4][0], lsum[4][1], lsum[5][0], lsum[5][1]);
+        add_f2(w0, w1, lsum[6][0], lsum[6][1], lsum[7][0], lsum[7][1]);
+        add_f2(v0, v1, v0, v1, w0, w1);
+        add_f2(t0, t1, t0, t1, v0, v1);
+      }
+      add_f2(q.lrow[0], q.lrow[1], q.lrow[0], q.lrow[1], t0, t1);
     }
   }
 }
@@ -454,19 +515,28 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
   const int WC = p.WC;
   const int mi = lane >> 3;
   const int g = lane >> 2;
+  // shared-memory byte offset of rectangle key j (keys past the rectangle
+  // read key 0: they are masked)
+  auto key_off = [&](int j) -> uint32_t {
+    if (j >= q.nkeys) j = 0;
+    return (uint32_t)(((q.wr0 + (j >> LS)) * WC + q.wc0 + (j & smask)) * (DHP * 2));
+  };
+  const int lk = (mi & 1) * 8 + (lane & 7);            // key row this lane addresses in a K ldmatrix
+  const int lv = (mi >> 1) * 8 + (lane & 7);           // ... in a V ldmatrix.trans
+  const uint32_t kc0 = sK32 + (uint32_t)((mi >> 1) * 16), vc0 = sV32 + (uint32_t)((mi & 1) * 16);
   for (int g0 = 0; g0 < q.ngroups; g0 += GCH) {
+    // Groups past the rectangle (in the last chunk) skip all their work
+    // behind uniform branches; they would only contribute -inf to the max.
     float s[GCH][4];
 #pragma unroll
     for (int gi = 0; gi < GCH; ++gi) {
-      s[gi][0] = s[gi][1] = s[gi][2] = s[gi][3] = 0.f;
       if (g0 + gi < q.ngroups) {
-        int jk = (g0 + gi) * 16 + (mi & 1) * 8 + (lane & 7);
-        if (jk >= q.nkeys) jk = 0;
-        const int krow = (q.wr0 + (jk >> LS)) * WC + q.wc0 + (jk & smask);
+        s[gi][0] = s[gi][1] = s[gi][2] = s[gi][3] = 0.f;
+        const uint32_t ka = kc0 + key_off((g0 + gi) * 16 + lk);
 #pragma unroll
         for (int kc = 0; kc < KC; ++kc) {
           uint32_t a0, a1, a2, a3;
-          ldsm_x4(sK32 + (uint32_t)((krow * DHP + kc * 16 + (mi >> 1) * 8) * 2), a0, a1, a2, a3);
+          ldsm_x4(ka + kc * 32, a0, a1, a2, a3);
           mma_bf16(s[gi], a0, a1, a2, a3, q.qb[kc][0], q.qb[kc][1]);
         }
       }
@@ -476,17 +546,18 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
 #pragma unroll
     for (int gi = 0; gi < GCH; ++gi) {
       const int gg = g0 + gi;
-      const bool live = gg < q.ngroups;
-      const int half = (LS == 5) ? (gg & 1) : 0;
+      if (gg < q.ngroups) {
+        const int half = (LS == 5) ? (gg & 1) : 0;
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int row = (gg * 16 + 8 * i + g) >> LS;
+        for (int i = 0; i < 2; ++i) {
+          const int row = (gg * 16 + 8 * i + g) >> LS;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const bool rok = live && ((unsigned)(row - q.rlo[k]) < (unsigned)p.kh);
-          const float v = rok ? fmaf(s[gi][2 * i + k], p.scale_log2, q.cbias[half][k][i]) : -INFINITY;
-          s[gi][2 * i + k] = v;
-          mx[k] = fmaxf(mx[k], v);
+          for (int k = 0; k < 2; ++k) {
+            const bool rok = (unsigned)(row - q.rlo[k]) < (unsigned)p.kh;
+            const float v = rok ? fmaf(s[gi][2 * i + k], p.scale_log2, q.cbias[half][k][i]) : -INFINITY;
+            s[gi][2 * i + k] = v;
+            mx[k] = fmaxf(mx[k], v);
+          }
         }
       }
     }
@@ -510,23 +581,22 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
     float lsum[2] = {0.f, 0.f};
 #pragma unroll
     for (int gi = 0; gi < GCH; ++gi) {
-      if (g0 + gi >= q.ngroups) break;
-      float pr[4];
+      if (g0 + gi < q.ngroups) {
+        float pr[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) pr[e] = ex2(s[gi][e] - mref[e & 1]);
-      lsum[0] += pr[0] + pr[2];
-      lsum[1] += pr[1] + pr[3];
-      // P^T blocks (keys 0-7 / 8-15 x queries) transposed into the B operand
-      const uint32_t b0 = movmatrix_t(pack_bf16(pr[0], pr[1]));
-      const uint32_t b1 = movmatrix_t(pack_bf16(pr[2], pr[3]));
-      int jv = (g0 + gi) * 16 + (mi >> 1) * 8 + (lane & 7);
-      if (jv >= q.nkeys) jv = 0;
-      const int vrow = (q.wr0 + (jv >> LS)) * WC + q.wc0 + (jv & smask);
+        for (int e = 0; e < 4; ++e) pr[e] = ex2(s[gi][e] - mref[e & 1]);
+        lsum[0] += pr[0] + pr[2];
+        lsum[1] += pr[1] + pr[3];
+        // P^T blocks (keys 0-7 / 8-15 x queries) transposed into the B operand
+        const uint32_t b0 = movmatrix_t(pack_bf16(pr[0], pr[1]));
+        const uint32_t b1 = movmatrix_t(pack_bf16(pr[2], pr[3]));
+        const uint32_t va = vc0 + key_off((g0 + gi) * 16 + lv);
 #pragma unroll
-      for (int md = 0; md < MD; ++md) {
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4_t(sV32 + (uint32_t)((vrow * DHP + md * 16 + (mi & 1) * 8) * 2), a0, a1, a2, a3);
-        mma_bf16(q.o[md], a0, a1, a2, a3, b0, b1);
+        for (int md = 0; md < MD; ++md) {
+          uint32_t a0, a1, a2, a3;
+          ldsm_x4_t(va + md * 32, a0, a1, a2, a3);
+          mma_bf16(q.o[md], a0, a1, a2, a3, b0, b1);
+        }
       }
     }
     q.lrow[0] += lsum[0];
