@@ -171,6 +171,46 @@ __device__ __forceinline__ float gelu_erf(float z) {
   return 0.5f * z * (1.f + erf_z);
 }
 
+// gelu_erf on two values with paired instructions; every lane rounds exactly
+// as gelu_erf does (same operations, same order; the polynomial is carried
+// negated, with negated coefficients, which is exact).
+__device__ __forceinline__ void gelu_erf2(float& z0, float& z1) {
+  const uint64_t k_isqrt2 = pack_f2(0.70710678118654752f, 0.70710678118654752f);
+  const uint64_t k_p = pack_f2(0.3275911f, 0.3275911f), k_one = pack_f2(1.f, 1.f);
+  const uint64_t k_a5 = pack_f2(-1.061405429f, -1.061405429f), k_a4 = pack_f2(1.453152027f, 1.453152027f);
+  const uint64_t k_a3 = pack_f2(-1.421413741f, -1.421413741f), k_a2 = pack_f2(0.284496736f, 0.284496736f);
+  const uint64_t k_a1 = pack_f2(-0.254829592f, -0.254829592f);
+  const uint64_t k_nl2e = pack_f2(-1.4426950408889634f, -1.4426950408889634f), k_half = pack_f2(0.5f, 0.5f);
+  float x0 = fabsf(z0), x1 = fabsf(z1);
+  mul_f2(x0, x1, k_isqrt2);
+  float d0, d1;
+  fma_f2(d0, d1, x0, x1, k_p, k_one);
+  float t0, t1;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t0) : "f"(d0));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t1) : "f"(d1));
+  const uint64_t t2 = pack_f2(t0, t1);
+  float p0, p1;   // -poly
+  fma_f2(p0, p1, t0, t1, k_a5, k_a4);
+  fma_f2(p0, p1, p0, p1, t2, k_a3);
+  fma_f2(p0, p1, p0, p1, t2, k_a2);
+  fma_f2(p0, p1, p0, p1, t2, k_a1);
+  mul_f2(p0, p1, t2);
+  float y0 = x0, y1 = x1;
+  mul_f2(y0, y1, k_nl2e);
+  mul_f2(y0, y1, pack_f2(x0, x1));
+  float e0, e1;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e0) : "f"(y0));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(y1));
+  float r0, r1;
+  fma_f2(r0, r1, p0, p1, pack_f2(e0, e1), k_one);
+  r0 = copysignf(r0, z0);
+  r1 = copysignf(r1, z1);
+  float o0, o1;
+  add_f2(o0, o1, 1.f, 1.f, r0, r1);
+  mul_f2(z0, z1, k_half);
+  mul_f2(z0, z1, pack_f2(o0, o1));
+}
+
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
@@ -431,16 +471,24 @@ __global__ void __launch_bounds__(THREADS, 1)
             lbb[4 * q] = b.x; lbb[4 * q + 1] = b.y; lbb[4 * q + 2] = b.z; lbb[4 * q + 3] = b.w;
           }
         }
+        if constexpr (kLNF) {
+          // rstd (acc - mean colsum) + b', then GELU, two columns per instruction
+          const uint64_t nmean2 = pack_f2(-ln_mean, -ln_mean), rstd2 = pack_f2(ln_rstd, ln_rstd);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if constexpr (F8) v[j] *= alpha;
-          if constexpr (kLNF) {
-            v[j] = fmaf(ln_rstd, fmaf(-ln_mean, lcs[j], v[j]), lbb[j]);
-          } else {
-            v[j] += (bias && n + j < N) ? __ldg(bias + n + j) : 0.f;
+          for (int j = 0; j < 32; j += 2) {
+            float t0, t1;
+            fma_f2(t0, t1, lcs[j], lcs[j + 1], nmean2, pack_f2(v[j], v[j + 1]));
+            fma_f2(v[j], v[j + 1], t0, t1, rstd2, pack_f2(lbb[j], lbb[j + 1]));
+            if constexpr (EPI == EPI_LNF_GELU) gelu_erf2(v[j], v[j + 1]);
           }
-          if constexpr (EPI == EPI_GELU || EPI == EPI_GELU_F8 || EPI == EPI_LNF_GELU) v[j] = gelu_erf(v[j]);
-          if constexpr (EPI == EPI_GELU_F8) v[j] *= out_scale;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if constexpr (F8) v[j] *= alpha;
+            v[j] += (bias && n + j < N) ? __ldg(bias + n + j) : 0.f;
+            if constexpr (EPI == EPI_GELU || EPI == EPI_GELU_F8) v[j] = gelu_erf(v[j]);
+            if constexpr (EPI == EPI_GELU_F8) v[j] *= out_scale;
+          }
         }
         if constexpr (EPI == EPI_LNF_STORE) {
           if (e.rope != nullptr) {

@@ -30,6 +30,44 @@ int* device_status_word();
 // Upper bound on any single device-side spin-wait (nanoseconds).
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;
 
+// Paired FP32 arithmetic (f32x2 instructions: one instruction, two lanes,
+// each rounded exactly as the scalar instruction) and a three-input max.
+__device__ __forceinline__ uint64_t pack_f2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+// (d0, d1) = (a0, a1) * b2 + c2
+__device__ __forceinline__ void fma_f2(float& d0, float& d1, float a0, float a1, uint64_t b2, uint64_t c2) {
+  asm("{\n .reg .b64 ra, rd;\n mov.b64 ra, {%2, %3};\n fma.rn.f32x2 rd, ra, %4, %5;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "l"(b2), "l"(c2));
+}
+// (d0, d1) = (a0, a1) - b2
+__device__ __forceinline__ void sub_f2(float& d0, float& d1, float a0, float a1, uint64_t b2) {
+  asm("{\n .reg .b64 ra, rd;\n mov.b64 ra, {%2, %3};\n sub.rn.f32x2 rd, ra, %4;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "l"(b2));
+}
+// (d0, d1) = (a0, a1) + (b0, b1)
+__device__ __forceinline__ void add_f2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n add.rn.f32x2 rd, ra, rb;\n"
+      " mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+// (x0, x1) *= b2
+__device__ __forceinline__ void mul_f2(float& x0, float& x1, uint64_t b2) {
+  asm("{\n .reg .b64 ra, rd;\n mov.b64 ra, {%2, %3};\n mul.rn.f32x2 rd, ra, %4;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(x0), "=f"(x1)
+      : "f"(x0), "f"(x1), "l"(b2));
+}
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 enum Epilogue : int {
   EPI_STORE = 0,       // out = acc + bias (fp32 path: float; bf16 path: bfloat16)
   EPI_GELU = 1,        // out = GELU(acc + bias)
