@@ -29,8 +29,18 @@ What the paper fixes, and the readings taken where it is silent:
 * Silent, read as PyTorch defaults: LayerNorm with biased variance, eps 1e-5,
   affine; exact erf GELU; softmax scale 1/sqrt(d_head); all linear layers
   carry a bias; no relative-position bias; dilation 1.
-* Appendix A.2 also names rotary position embeddings; the processor built
-  here does not use them (no axis split or frequencies are given).
+* Appendix A.2 also names rotary position embeddings without an axis split
+  or frequencies: an optional 3D rotary embedding (``Shape.rope``) splits the
+  rotation pairs over level / latitude / longitude (see ``rope_pairs``).
+* Section 2.1 and Appendix A.2, encoder and decoder: convolution layers map
+  the 0.25-degree grid to the 2-degree latent and back, with 2 NA blocks of
+  hidden width 1024 on the latent side; constants are concatenated with the
+  input. Readings (the layer list is not given): the convolutions are patch
+  embeddings with kernel = stride (pd levels x 8 x 8 pixels for the
+  atmosphere, zero-padded at the top to a multiple of pd levels; 8 x 8 for
+  surface + constants), the surface is the last latent level, a linear map
+  joins width 1024 to the processor's width, the decoder mirrors it with
+  transposed convolutions (kernel = stride); ResNet blocks are not built.
 
 Parity status: every function below is pinned by ``tests/test_oracle_pins.py``
 (closed forms, library special cases, invariants, brute force on tiny grids,
@@ -399,3 +409,69 @@ def rel_l2(y, y_ref) -> float:
     y = np.asarray(y, np.float64).ravel()
     y_ref = np.asarray(y_ref, np.float64).ravel()
     return float(np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref))
+
+
+# ------------------------------------------------------- encoder / decoder --
+# Shapes: synth.Codec. Atmosphere [levels, H0, W0, v_atm], surface input
+# [H0, W0, v_sfc_in], constants [H0, W0, n_const]; latent [D, H, W, C] with
+# D = level_pad / pd + 1 (surface last), H = H0 / p, W = W0 / p.
+
+def codec_patches_atm(atm, cd):
+    """[D-1, H, W, pd*p*p*v_atm]: each token's input patch, ordered (level, row, column, variable).
+
+    The atmosphere is zero-padded at the top (lowest level indices) to
+    level_pad levels, so padded level i holds input level i - (level_pad - levels).
+    """
+    atm = np.asarray(atm, np.float64)
+    pad = np.zeros((cd.level_pad, cd.H0, cd.W0, cd.v_atm))
+    pad[cd.level_pad - cd.levels:] = atm
+    t = pad.reshape(cd.D - 1, cd.pd, cd.H, cd.p, cd.W, cd.p, cd.v_atm)
+    return t.transpose(0, 2, 4, 1, 3, 5, 6).reshape(cd.D - 1, cd.H, cd.W, cd.k_atm)
+
+
+def codec_patches_sfc(sfc, const, cd):
+    """[H, W, p*p*(v_sfc_in + n_const)]: surface fields then constants per pixel, ordered (row, column, channel)."""
+    x = np.concatenate([np.asarray(sfc, np.float64), np.asarray(const, np.float64)], axis=-1)
+    c = x.shape[-1]
+    return x.reshape(cd.H, cd.p, cd.W, cd.p, c).transpose(0, 2, 1, 3, 4).reshape(cd.H, cd.W, cd.p * cd.p * c)
+
+
+def codec_unpatch_atm(y, cd):
+    """Inverse layout of codec_patches_atm: [D-1, H, W, k_atm] -> [levels, H0, W0, v_atm] (padding dropped)."""
+    t = np.asarray(y, np.float64).reshape(cd.D - 1, cd.H, cd.W, cd.pd, cd.p, cd.p, cd.v_atm)
+    full = t.transpose(0, 3, 1, 4, 2, 5, 6).reshape(cd.level_pad, cd.H0, cd.W0, cd.v_atm)
+    return full[cd.level_pad - cd.levels:]
+
+
+def codec_unpatch_sfc(y, cd):
+    """[H, W, p*p*v_sfc_out] -> [H0, W0, v_sfc_out]."""
+    t = np.asarray(y, np.float64).reshape(cd.H, cd.W, cd.p, cd.p, cd.v_sfc_out)
+    return t.transpose(0, 2, 1, 3, 4).reshape(cd.H0, cd.W0, cd.v_sfc_out)
+
+
+def encode(atm, sfc, const, w, cd):
+    """Physical fields -> latent [D, H, W, C] (Section 2.1, Appendix A.2; readings above).
+
+    Patch embeddings (convolutions with kernel = stride), the encoder's NA
+    blocks at width Ce, then the linear map to the processor's width C.
+    """
+    w64 = {k: v for k, v in w.items() if not k.endswith("blocks")}
+    x = np.empty((cd.D, cd.H, cd.W, cd.Ce))
+    x[:cd.D - 1] = linear(codec_patches_atm(atm, cd), w64["embed_atm_w"], w64["embed_atm_b"])
+    x[cd.D - 1] = linear(codec_patches_sfc(sfc, const, cd), w64["embed_sfc_w"], w64["embed_sfc_b"])
+    x = processor(x[None], w["enc_blocks"], cd.block_shape())[0]
+    return linear(x, w64["enc_out_w"], w64["enc_out_b"])
+
+
+def decode(latent, w, cd):
+    """Latent [D, H, W, C] -> (atmosphere [levels, H0, W0, v_atm], surface [H0, W0, v_sfc_out]).
+
+    The linear map to width Ce, the decoder's NA blocks, then transposed
+    convolutions with kernel = stride (one linear map per token, its outputs
+    laid out over the token's pixels).
+    """
+    x = linear(latent, w["dec_in_w"], w["dec_in_b"])
+    x = processor(x[None], w["dec_blocks"], cd.block_shape())[0]
+    atm = codec_unpatch_atm(linear(x[:cd.D - 1], w["unembed_atm_w"], w["unembed_atm_b"]), cd)
+    sfc = codec_unpatch_sfc(linear(x[cd.D - 1], w["unembed_sfc_w"], w["unembed_sfc_b"]), cd)
+    return atm, sfc

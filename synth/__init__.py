@@ -165,3 +165,150 @@ def write_weight_file(path, shape: Shape, p6, p1) -> None:
         f.write(WEIGHT_MAGIC)
         f.write(struct.pack("<4i", shape.C, len(p6), len(p1), 0))
         f.write(blob.astype("<f4").tobytes())
+
+
+# ----------------------------------------------------------- encoder / decoder
+
+@dataclasses.dataclass(frozen=True)
+class Codec:
+    """Encoder / decoder sizes: the 0.25-degree grid and the patching into the latent.
+
+    Physical fields: atmosphere [levels, H0, W0, v_atm], surface input
+    [H0, W0, v_sfc_in], constants [H0, W0, n_const]; outputs atmosphere
+    [levels, H0, W0, v_atm] and surface [H0, W0, v_sfc_out]. The atmosphere is
+    zero-padded at the top to level_pad levels; a latent token covers pd
+    levels x p x p pixels (atmosphere) or p x p pixels (surface), so the latent
+    has level_pad / pd atmospheric levels plus one surface level.
+    """
+    H0: int
+    W0: int
+    levels: int = 28
+    level_pad: int = 32
+    pd: int = 4
+    p: int = 8
+    v_atm: int = 5
+    v_sfc_in: int = 8
+    v_sfc_out: int = 17
+    n_const: int = 8
+    Ce: int = 1024
+    heads: int = 16
+    kd: int = 5
+    kh: int = 7
+    kw: int = 7
+    blocks: int = 2
+    lon_periodic: bool = True
+    ln_eps: float = 1e-5
+
+    @property
+    def D(self) -> int:
+        return self.level_pad // self.pd + 1
+
+    @property
+    def H(self) -> int:
+        return self.H0 // self.p
+
+    @property
+    def W(self) -> int:
+        return self.W0 // self.p
+
+    @property
+    def k_atm(self) -> int:     # inputs of one atmospheric token
+        return self.pd * self.p * self.p * self.v_atm
+
+    @property
+    def k_sfc(self) -> int:     # inputs of one surface token
+        return self.p * self.p * (self.v_sfc_in + self.n_const)
+
+    @property
+    def n_sfc_out(self) -> int:  # outputs of one surface token
+        return self.p * self.p * self.v_sfc_out
+
+    def block_shape(self) -> Shape:
+        """The NA blocks' shape inside the encoder / decoder (width Ce)."""
+        return Shape(D=self.D, H=self.H, W=self.W, C=self.Ce, heads=self.heads, kd=self.kd, kh=self.kh,
+                     kw=self.kw, blocks_p6=self.blocks, blocks_p1=self.blocks, lon_periodic=self.lon_periodic,
+                     ln_eps=self.ln_eps)
+
+
+# 0.25-degree grid (720 x 1440, the 721st latitude row dropped), 28 pressure
+# levels padded to 32: latent 9 x 90 x 180, encoder / decoder width 1024.
+FULL_CODEC = Codec(H0=720, W0=1440)
+# 192 x 384 grid, 10 levels padded to 12 (4 per token, 3 atmospheric latent
+# levels): latent 4 x 24 x 48
+# with the small latent's window and heads, width 128.
+SMALL_CODEC = Codec(H0=192, W0=384, levels=10, level_pad=12, pd=4, Ce=128, heads=4, kd=3, kh=5, kw=5)
+
+CODEC_TENSORS = ("embed_atm_w", "embed_atm_b", "embed_sfc_w", "embed_sfc_b", "enc_out_w", "enc_out_b",
+                 "dec_in_w", "dec_in_b", "unembed_atm_w", "unembed_atm_b", "unembed_sfc_w", "unembed_sfc_b")
+
+
+def _codec_shapes(cd: Codec, C: int):
+    return {
+        "embed_atm_w": (cd.Ce, cd.k_atm), "embed_atm_b": (cd.Ce,),
+        "embed_sfc_w": (cd.Ce, cd.k_sfc), "embed_sfc_b": (cd.Ce,),
+        "enc_out_w": (C, cd.Ce), "enc_out_b": (C,),
+        "dec_in_w": (cd.Ce, C), "dec_in_b": (cd.Ce,),
+        "unembed_atm_w": (cd.k_atm, cd.Ce), "unembed_atm_b": (cd.k_atm,),
+        "unembed_sfc_w": (cd.n_sfc_out, cd.Ce), "unembed_sfc_b": (cd.n_sfc_out,),
+    }
+
+
+def codec_weights(cd: Codec, C: int, seed: int, stress: bool = False) -> dict:
+    """Encoder / decoder weights for a latent of width C (float32).
+
+    Matrices [out, in], Xavier-uniform; biases 0 (U(+-0.1) with stress).
+    'enc_blocks' / 'dec_blocks': lists of block weight dicts at width Ce
+    (processor ids 2 and 3 of the block generator).
+    """
+    out = {}
+    for tid, (name, shp) in enumerate(_codec_shapes(cd, C).items()):
+        n = int(np.prod(shp))
+        key = stream_key(seed, (3 << 40) | tid)
+        if len(shp) == 2:
+            bound = np.sqrt(6.0 / (shp[0] + shp[1]))
+            vals = (2.0 * uniform(key, n) - 1.0) * bound
+        else:
+            vals = (2.0 * uniform(key, n) - 1.0) * 0.1 if stress else np.zeros(n)
+        out[name] = vals.astype(np.float32).reshape(shp)
+    out["enc_blocks"] = [block_weights(cd.Ce, seed, 2, i, stress) for i in range(cd.blocks)]
+    out["dec_blocks"] = [block_weights(cd.Ce, seed, 3, i, stress) for i in range(cd.blocks)]
+    return out
+
+
+def pack_codec_weights(w: dict) -> np.ndarray:
+    """Flat float32 blob: CODEC_TENSORS in order, then the encoder blocks and
+    the decoder blocks (tensors in BLOCK_TENSORS order)."""
+    parts = [np.ascontiguousarray(w[name], dtype=np.float32).ravel() for name in CODEC_TENSORS]
+    parts.append(pack_weights(w["enc_blocks"], w["dec_blocks"]))
+    return np.concatenate(parts)
+
+
+def codec_inputs(cd: Codec, seed: int):
+    """(atmosphere [levels,H0,W0,v_atm], surface [H0,W0,v_sfc_in], constants [H0,W0,n_const]), float32.
+
+    Fields ~ N(0, 1). Constants in the order of Appendix A.2's list: sin and
+    cos of latitude, sin and cos of longitude (cell centres), land-sea mask
+    (0/1), soil type (integer class 0..7), topography and elevation (N(0, 1));
+    with n_const != 8 the channels after the fourth are N(0, 1).
+    """
+    atm = normal(stream_key(seed, (4 << 40) | 0), cd.levels * cd.H0 * cd.W0 * cd.v_atm)
+    sfc = normal(stream_key(seed, (4 << 40) | 1), cd.H0 * cd.W0 * cd.v_sfc_in)
+    const = np.empty((cd.H0, cd.W0, cd.n_const), dtype=np.float64)
+    lat = np.deg2rad(90.0 - (np.arange(cd.H0) + 0.5) * 180.0 / cd.H0)
+    lon = np.deg2rad((np.arange(cd.W0) + 0.5) * 360.0 / cd.W0)
+    base = [np.sin(lat)[:, None] + 0 * lon[None, :], np.cos(lat)[:, None] + 0 * lon[None, :],
+            0 * lat[:, None] + np.sin(lon)[None, :], 0 * lat[:, None] + np.cos(lon)[None, :]]
+    for c in range(cd.n_const):
+        if c < 4:
+            const[..., c] = base[c]
+        else:
+            u = uniform(stream_key(seed, (4 << 40) | (2 + c)), cd.H0 * cd.W0).reshape(cd.H0, cd.W0)
+            if c == 4:
+                const[..., c] = (u < 0.3).astype(np.float64)
+            elif c == 5:
+                const[..., c] = np.floor(u * 8.0)
+            else:
+                const[..., c] = normal(stream_key(seed, (4 << 40) | (2 + c)), cd.H0 * cd.W0).reshape(cd.H0, cd.W0)
+    return (atm.reshape(cd.levels, cd.H0, cd.W0, cd.v_atm).astype(np.float32),
+            sfc.reshape(cd.H0, cd.W0, cd.v_sfc_in).astype(np.float32),
+            const.astype(np.float32))
