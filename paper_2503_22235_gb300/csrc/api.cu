@@ -281,12 +281,14 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   if (!wm::make_tmap_out(&tm_x, x, (uint64_t)M, (uint64_t)C, true))
     return fail(WM_ERR_INVALID_ARG, "latent pointer must be 16-byte aligned for the BF16 path");
   const bool fp8 = c.precision == WM_PREC_BF16_FP8MLP;
+  // small problems: let each kernel's prologue overlap its predecessor's tail
+  const bool pdl = M <= wm::kPdlMaxTokens;
   // LayerNorm 1, folded into the QKV GEMM. Its row statistics come from the
   // previous block's FC2 epilogue, or from one statistics pass for the first
   // block of a processor call.
   if (first) {
     TimedLaunch t(ctx, WM_K_LN1, s);
-    WM_TRY(wm::launch_row_stats(x, ctx->xb, ctx->stats, (int)M, C, s));
+    WM_TRY(wm::launch_row_stats(x, ctx->xb, ctx->stats, (int)M, C, s, pdl));
     ctx->np_next = 1;
   }
   wm::GemmArgs a;
@@ -298,9 +300,10 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   a.bias = w.bb_qkv; a.colsum = w.cs_qkv; a.stats = ctx->stats; a.np = ctx->np_next; a.eps = c.ln_eps;
   a.epi = wm::EPI_LNF_STORE;
   a.rope = c.rope ? ctx->d_rope : nullptr;
-  { TimedLaunch t(ctx, WM_K_QKV, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+  { TimedLaunch t(ctx, WM_K_QKV, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
   { TimedLaunch t(ctx, WM_K_ATTN, s);
-    WM_TRY(wm::launch_na_bf16(ctx->h_qkv, ctx->h_o, batch, c.D, c.H, c.W, C, c.heads, c.kd, c.kh, c.kw, per, s)); }
+    WM_TRY(wm::launch_na_bf16(ctx->h_qkv, ctx->h_o, batch, c.D, c.H, c.W, C, c.heads, c.kd, c.kh, c.kw, per, s,
+                              0, pdl)); }
   // output projection + residual; in BF16 it also leaves LayerNorm 2's statistics
   a = wm::GemmArgs();
   a.M = (int)M; a.K = C; a.N = C;
@@ -312,27 +315,28 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   } else {
     a.epi = wm::EPI_RESID_LN; a.tmC2 = ctx->tmc_xb; a.x = x; a.stats = ctx->stats;
   }
-  { TimedLaunch t(ctx, WM_K_PROJ, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+  { TimedLaunch t(ctx, WM_K_PROJ, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
   const int np2 = 2 * ((C + a.bn - 1) / a.bn);
   if (fp8) {
     // MLP in e4m3 with static per-tensor scales: u2 / s_u and W1 / s_w1 into
     // FC1 (alpha = s_u s_w1), GELU output / s_h and W2 / s_w2 into FC2
     { TimedLaunch t(ctx, WM_K_LN2, s);
-      WM_TRY(wm::launch_layernorm_e4m3(x, w.ln2_g, w.ln2_b, ctx->q_u, (int)M, C, c.ln_eps, 1.f / w.s_u, s)); }
+      WM_TRY(wm::launch_layernorm_e4m3(x, w.ln2_g, w.ln2_b, ctx->q_u, (int)M, C, c.ln_eps, 1.f / w.s_u, s,
+                                       pdl)); }
     a = wm::GemmArgs();
     a.f8 = true;
     a.M = (int)M; a.K = C; a.N = 4 * C;
     a.bn = pick_bn(M, a.N);
     a.tmA = ctx->tm_qu; a.tmB = w.tm_q1[a.bn == 256]; a.tmC = ctx->tmc_qh;
     a.bias = w.b1; a.epi = wm::EPI_GELU_F8; a.alpha = w.s_u * w.s_w1; a.out_scale = 1.f / w.s_h;
-    { TimedLaunch t(ctx, WM_K_FC1, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+    { TimedLaunch t(ctx, WM_K_FC1, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
     a = wm::GemmArgs();
     a.f8 = true;
     a.M = (int)M; a.K = 4 * C; a.N = C;
     a.bn = pick_bn(M, a.N);
     a.tmA = ctx->tm_qh; a.tmB = w.tm_q2[a.bn == 256]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
     a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.alpha = w.s_h * w.s_w2; a.x = x; a.stats = ctx->stats;
-    { TimedLaunch t(ctx, WM_K_FC2, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+    { TimedLaunch t(ctx, WM_K_FC2, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
     ctx->np_next = 2 * ((C + a.bn - 1) / a.bn);
     return WM_OK;
   }
@@ -343,14 +347,14 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   a.tmA = ctx->tm_xb; a.tmB = w.tm_f1[a.bn == 256]; a.tmC = ctx->tmc_h;
   a.bias = w.bb_1; a.colsum = w.cs_1; a.stats = ctx->stats; a.np = np2; a.eps = c.ln_eps;
   a.epi = wm::EPI_LNF_GELU;
-  { TimedLaunch t(ctx, WM_K_FC1, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+  { TimedLaunch t(ctx, WM_K_FC1, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
   // FC2 + residual, leaving the next block's LayerNorm-1 statistics
   a = wm::GemmArgs();
   a.M = (int)M; a.K = 4 * C; a.N = C;
   a.bn = pick_bn(M, a.N);
   a.tmA = ctx->tm_h; a.tmB = w.tm_2[a.bn == 256]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
   a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.x = x; a.stats = ctx->stats;
-  { TimedLaunch t(ctx, WM_K_FC2, s); WM_TRY(wm::launch_gemm_tc(a, s)); }
+  { TimedLaunch t(ctx, WM_K_FC2, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
   ctx->np_next = 2 * ((C + a.bn - 1) / a.bn);
   return WM_OK;
 }
@@ -605,6 +609,10 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
 }
 
 }  // namespace
+
+namespace wm {
+const wm_config* ctx_config(const wm_ctx* ctx) { return &ctx->cfg; }
+}  // namespace wm
 
 // =================================================================== C ABI ===
 extern "C" {

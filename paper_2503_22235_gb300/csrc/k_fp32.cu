@@ -99,6 +99,8 @@ __global__ void row_stats_kernel(const float* __restrict__ x, __nv_bfloat16* __r
   const int C = 128 * V4;
   const int lane = threadIdx.x & 31;
   const long row = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  pdl_wait();
+  pdl_trigger();
   if (row >= M) return;
   const float4* xr = reinterpret_cast<const float4*>(x + row * C);
   float4 v[V4];
@@ -127,17 +129,18 @@ __global__ void row_stats_kernel(const float* __restrict__ x, __nv_bfloat16* __r
   }
 }
 
-wm_status launch_row_stats(const float* x, __nv_bfloat16* xb, float* stats, int M, int C, cudaStream_t s) {
+wm_status launch_row_stats(const float* x, __nv_bfloat16* xb, float* stats, int M, int C, cudaStream_t s,
+                           bool pdl) {
   if (M <= 0) return WM_OK;
   const int warps = 8;
   dim3 grid((M + warps - 1) / warps), block(32 * warps);
   switch (C) {
-    case 128: row_stats_kernel<1><<<grid, block, 0, s>>>(x, xb, stats, M); break;
-    case 256: row_stats_kernel<2><<<grid, block, 0, s>>>(x, xb, stats, M); break;
-    case 384: row_stats_kernel<3><<<grid, block, 0, s>>>(x, xb, stats, M); break;
-    case 512: row_stats_kernel<4><<<grid, block, 0, s>>>(x, xb, stats, M); break;
-    case 768: row_stats_kernel<6><<<grid, block, 0, s>>>(x, xb, stats, M); break;
-    case 1024: row_stats_kernel<8><<<grid, block, 0, s>>>(x, xb, stats, M); break;
+    case 128: WM_CUDA(launch_pdl(row_stats_kernel<1>, grid, block, 0, s, pdl, x, xb, stats, M)); break;
+    case 256: WM_CUDA(launch_pdl(row_stats_kernel<2>, grid, block, 0, s, pdl, x, xb, stats, M)); break;
+    case 384: WM_CUDA(launch_pdl(row_stats_kernel<3>, grid, block, 0, s, pdl, x, xb, stats, M)); break;
+    case 512: WM_CUDA(launch_pdl(row_stats_kernel<4>, grid, block, 0, s, pdl, x, xb, stats, M)); break;
+    case 768: WM_CUDA(launch_pdl(row_stats_kernel<6>, grid, block, 0, s, pdl, x, xb, stats, M)); break;
+    case 1024: WM_CUDA(launch_pdl(row_stats_kernel<8>, grid, block, 0, s, pdl, x, xb, stats, M)); break;
     default: return fail(WM_ERR_INVALID_ARG, "row statistics need C in {128, 256, 384, 512, 768, 1024}");
   }
   WM_CUDA(cudaGetLastError());
@@ -152,6 +155,8 @@ __global__ void ln_rows_e4m3(const float* __restrict__ x, const float* __restric
   const int C = 128 * V4;
   const int lane = threadIdx.x & 31;
   const long row = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  pdl_wait();
+  pdl_trigger();
   if (row >= M) return;
   const float4* xr = reinterpret_cast<const float4*>(x + row * C);
   float4 v[V4];
@@ -186,17 +191,17 @@ __global__ void ln_rows_e4m3(const float* __restrict__ x, const float* __restric
 }
 
 wm_status launch_layernorm_e4m3(const float* x, const float* g, const float* b, uint8_t* out, int M, int C,
-                                float eps, float inv_scale, cudaStream_t s) {
+                                float eps, float inv_scale, cudaStream_t s, bool pdl) {
   if (M <= 0) return WM_OK;
   const int warps = 8;
   dim3 grid((M + warps - 1) / warps), block(32 * warps);
   switch (C) {
-    case 128: ln_rows_e4m3<1><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
-    case 256: ln_rows_e4m3<2><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
-    case 384: ln_rows_e4m3<3><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
-    case 512: ln_rows_e4m3<4><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
-    case 768: ln_rows_e4m3<6><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
-    case 1024: ln_rows_e4m3<8><<<grid, block, 0, s>>>(x, g, b, out, M, eps, inv_scale); break;
+    case 128: WM_CUDA(launch_pdl(ln_rows_e4m3<1>, grid, block, 0, s, pdl, x, g, b, out, M, eps, inv_scale)); break;
+    case 256: WM_CUDA(launch_pdl(ln_rows_e4m3<2>, grid, block, 0, s, pdl, x, g, b, out, M, eps, inv_scale)); break;
+    case 384: WM_CUDA(launch_pdl(ln_rows_e4m3<3>, grid, block, 0, s, pdl, x, g, b, out, M, eps, inv_scale)); break;
+    case 512: WM_CUDA(launch_pdl(ln_rows_e4m3<4>, grid, block, 0, s, pdl, x, g, b, out, M, eps, inv_scale)); break;
+    case 768: WM_CUDA(launch_pdl(ln_rows_e4m3<6>, grid, block, 0, s, pdl, x, g, b, out, M, eps, inv_scale)); break;
+    case 1024: WM_CUDA(launch_pdl(ln_rows_e4m3<8>, grid, block, 0, s, pdl, x, g, b, out, M, eps, inv_scale)); break;
     default: return fail(WM_ERR_INVALID_ARG, "e4m3 LayerNorm needs C in {128, 256, 384, 512, 768, 1024}");
   }
   WM_CUDA(cudaGetLastError());

@@ -320,6 +320,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = tmem_slot;
+  pdl_wait();      // the previous kernel's outputs (A, x, row statistics) are complete from here on
+  pdl_trigger();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -601,7 +603,8 @@ static wm_status launch_one(const GemmArgs& a, cudaStream_t s) {
   e.alpha = a.alpha;
   e.out_scale = a.out_scale;
   e.rope = a.rope;
-  kern<<<grid, THREADS, CF::SMEM, s>>>(a.tmA, a.tmB, a.tmC, a.tmC2, a.M, a.N, a.K, e, device_status_word());
+  WM_CUDA(launch_pdl(kern, dim3(grid), dim3(THREADS), CF::SMEM, s, a.pdl, a.tmA, a.tmB, a.tmC, a.tmC2, a.M, a.N, a.K, e,
+                     device_status_word()));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }

@@ -634,6 +634,8 @@ __global__ void __launch_bounds__(MAXT, 1) na_bf16_kernel(const Params p) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const Tile T = make_tile(p, blockIdx.x);
   const int slab = p.slab;
+  pdl_wait();      // qkv of the previous kernel is complete from here on
+  pdl_trigger();
   typename A::State q;
   A::begin(q, p, T, warp, lane);
   load_level<DH>(p, T, T.ld0, sm, slab, tid, blockDim.x);
@@ -700,6 +702,8 @@ __global__ void __launch_bounds__(MAXT, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  pdl_wait();      // qkv of the previous kernel is complete from here on
+  pdl_trigger();
 
   if (warp == NW) {
     // ------------------------------------------------------------- producer
@@ -944,34 +948,34 @@ NaPlan na_heuristic(int B, int D, int H, int W, int heads, int kh, int kw, int d
 }
 
 template <int DH, int LS, int G, int MT, bool TR>
-void launch_tile(const na::Params& p, long ntiles, int smem, cudaStream_t s) {
-  na::na_bf16_kernel<DH, LS, G, MT, TR><<<(unsigned)ntiles, 32 * p.NWH * p.NWW, smem, s>>>(p);
+void launch_tile(const na::Params& p, long ntiles, int smem, cudaStream_t s, bool pdl) {
+  launch_pdl(na::na_bf16_kernel<DH, LS, G, MT, TR>, dim3((unsigned)ntiles), dim3(32 * p.NWH * p.NWW), smem, s, pdl, p);
 }
 
 template <int DH, int LS, int G, int MT, bool TR>
-void launch_pipe(const na::Params& p, const CUtensorMap& tm, long ntiles, int smem, cudaStream_t s) {
+void launch_pipe(const na::Params& p, const CUtensorMap& tm, long ntiles, int smem, cudaStream_t s, bool pdl) {
   const int grid = (int)std::min<long>(ntiles, num_sms());
-  na::na_bf16_pipe_kernel<DH, LS, G, MT, TR>
-      <<<grid, 32 * (p.NWH * p.NWW + 1), smem, s>>>(p, (int)ntiles, device_status_word(), tm);
+  launch_pdl(na::na_bf16_pipe_kernel<DH, LS, G, MT, TR>, dim3(grid), dim3(32 * (p.NWH * p.NWW + 1)), smem, s, pdl,
+             p, (int)ntiles, device_status_word(), tm);
 }
 
 template <int DH, int LS>
 void launch_family(const NaPlan& pl, const na::Params& p, const CUtensorMap& tm, long ntiles, int smem,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool pdl) {
   if (pl.tr) {
-    if (pl.kind == 0) launch_tile<DH, LS, 8, 512, true>(p, ntiles, smem, s);
-    else launch_pipe<DH, LS, 8, 512, true>(p, tm, ntiles, smem, s);
+    if (pl.kind == 0) launch_tile<DH, LS, 8, 512, true>(p, ntiles, smem, s, pdl);
+    else launch_pipe<DH, LS, 8, 512, true>(p, tm, ntiles, smem, s, pdl);
   } else if (pl.gch == 4) {
-    if (pl.kind == 0) launch_tile<DH, LS, 4, 512, false>(p, ntiles, smem, s);
-    else launch_pipe<DH, LS, 4, 512, false>(p, tm, ntiles, smem, s);
+    if (pl.kind == 0) launch_tile<DH, LS, 4, 512, false>(p, ntiles, smem, s, pdl);
+    else launch_pipe<DH, LS, 4, 512, false>(p, tm, ntiles, smem, s, pdl);
   } else {
-    if (pl.kind == 0) launch_tile<DH, LS, 8, 384, false>(p, ntiles, smem, s);
-    else launch_pipe<DH, LS, 8, 288, false>(p, tm, ntiles, smem, s);
+    if (pl.kind == 0) launch_tile<DH, LS, 8, 384, false>(p, ntiles, smem, s, pdl);
+    else launch_pipe<DH, LS, 8, 288, false>(p, tm, ntiles, smem, s, pdl);
   }
 }
 
 template <int DH>
-wm_status launch_plan(const NaPlan& pl, na::Params p, cudaStream_t s) {
+wm_status launch_plan(const NaPlan& pl, na::Params p, cudaStream_t s, bool pdl) {
   p.WH = pl.WH;
   p.WW = pl.WW;
   p.log2span = 0;
@@ -998,21 +1002,21 @@ wm_status launch_plan(const NaPlan& pl, na::Params p, cudaStream_t s) {
   p.tma = pl.kind == 1 && make_tmap_qkv_slab(&tm, p.qkv, 3ull * p.C, p.W, p.H, (uint64_t)p.D * p.B, DH + 8, p.WC,
                                               p.HRmax) ? 1 : 0;
   switch (p.log2span) {
-    case 3: launch_family<DH, 3>(pl, p, tm, ntiles, smem, s); break;
-    case 4: launch_family<DH, 4>(pl, p, tm, ntiles, smem, s); break;
-    case 5: launch_family<DH, 5>(pl, p, tm, ntiles, smem, s); break;
+    case 3: launch_family<DH, 3>(pl, p, tm, ntiles, smem, s, pdl); break;
+    case 4: launch_family<DH, 4>(pl, p, tm, ntiles, smem, s, pdl); break;
+    case 5: launch_family<DH, 5>(pl, p, tm, ntiles, smem, s, pdl); break;
     default: return fail(WM_ERR_INVALID_ARG, "unsupported key rectangle width");
   }
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
-wm_status launch_with(const NaPlan& pl, const na::Params& p, int dh, cudaStream_t s) {
+wm_status launch_with(const NaPlan& pl, const na::Params& p, int dh, cudaStream_t s, bool pdl = false) {
   switch (dh) {
-    case 16: return launch_plan<16>(pl, p, s);
-    case 32: return launch_plan<32>(pl, p, s);
-    case 48: return launch_plan<48>(pl, p, s);
-    case 64: return launch_plan<64>(pl, p, s);
+    case 16: return launch_plan<16>(pl, p, s, pdl);
+    case 32: return launch_plan<32>(pl, p, s, pdl);
+    case 48: return launch_plan<48>(pl, p, s, pdl);
+    case 64: return launch_plan<64>(pl, p, s, pdl);
     default: return fail(WM_ERR_INVALID_ARG, "BF16 attention needs head dim 16, 32, 48 or 64");
   }
 }
@@ -1030,7 +1034,7 @@ na::Params make_params(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int 
 }  // namespace
 
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C, int heads,
-                         int kd, int kh, int kw, bool periodic, cudaStream_t s, int variant) {
+                         int kd, int kh, int kw, bool periodic, cudaStream_t s, int variant, bool pdl) {
   if (B <= 0) return WM_OK;
   if ((reinterpret_cast<uintptr_t>(qkv) | reinterpret_cast<uintptr_t>(out)) & 15)
     return fail(WM_ERR_INVALID_ARG, "BF16 attention needs 16-byte aligned qkv and out");
@@ -1053,7 +1057,7 @@ wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, in
   }
   if (!pl.NWH) pl = na_heuristic(B, D, H, W, heads, kh, kw, dh, fam, kind);
   if (!pl.NWH) return fail(WM_ERR_INVALID_ARG, "attention window too large for the BF16 attention kernel");
-  return launch_with(pl, make_params(qkv, out, B, D, H, W, C, heads, kd, kh, kw, periodic), dh, s);
+  return launch_with(pl, make_params(qkv, out, B, D, H, W, C, heads, kd, kh, kw, periodic), dh, s, pdl);
 }
 
 // Time every candidate CTA plan for this shape (1 warm-up + 3 timed launches

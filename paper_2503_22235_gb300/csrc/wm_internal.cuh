@@ -8,10 +8,14 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <utility>
 
 #include "../../include/wm.h"
 
 namespace wm {
+
+// The configuration a context was created with.
+const wm_config* ctx_config(const wm_ctx* ctx);
 
 // ------------------------------------------------------------ errors ----
 void set_error(const std::string& msg);
@@ -29,6 +33,38 @@ int* device_status_word();
 
 // Upper bound on any single device-side spin-wait (nanoseconds).
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;
+
+// Programmatic dependent launch. Kernels of the block chain are launched
+// with launch_pdl: such a kernel may start while its predecessor in the
+// stream is still running, so it runs only its prologue (barrier init, TMEM
+// allocation, descriptor prefetch: nothing that touches global memory) before
+// pdl_wait(), which returns once every earlier grid in the stream has
+// completed and its writes are visible. pdl_trigger() lets the next grid be
+// scheduled as soon as every CTA of this one has issued it (or exited). Both
+// are no-ops for a kernel launched without the attribute. The attribute pays
+// where launch latency and prologues are a visible share of a kernel (small
+// problems); on large batches it was measured slightly slower, so callers
+// enable it only up to kPdlMaxTokens tokens.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+constexpr long kPdlMaxTokens = 65536;
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              bool enable, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = enable ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Paired FP32 arithmetic (f32x2 instructions: one instruction, two lanes,
 // each rounded exactly as the scalar instruction) and a three-input max.
@@ -115,9 +151,10 @@ wm_status launch_layernorm(const float* x, const float* g, const float* b, void*
 // LayerNorm with e4m3 output: out = e4m3(LN(x) * inv_scale), RNE, saturating.
 // Row statistics for the first LayerNorm-folded GEMM of a processor call:
 // xb = bf16(x) and stats[m] = (mean, M2) of row m (one partial per row).
-wm_status launch_row_stats(const float* x, __nv_bfloat16* xb, float* stats, int M, int C, cudaStream_t s);
+wm_status launch_row_stats(const float* x, __nv_bfloat16* xb, float* stats, int M, int C, cudaStream_t s,
+                           bool pdl = false);
 wm_status launch_layernorm_e4m3(const float* x, const float* g, const float* b, uint8_t* out, int M, int C,
-                                float eps, float inv_scale, cudaStream_t s);
+                                float eps, float inv_scale, cudaStream_t s, bool pdl = false);
 wm_status launch_sgemm(const float* A, const float* W, const float* bias, float* out, int M, int N, int K,
                        int epi, cudaStream_t s);
 wm_status launch_na_f32(const float* qkv, float* out, int B, int D, int H, int W, int C, int heads, int kd,
@@ -161,6 +198,7 @@ struct GemmArgs {
   float alpha = 1.f;   // e4m3 only: accumulator scale (product of the operand scales)
   float out_scale = 1.f;  // EPI_GELU_F8: 1 / output scale
   const RopeArgs* rope = nullptr;  // device pointer; EPI_LNF_STORE rotates q and k
+  bool pdl = false;    // launch as a programmatic dependent of the previous kernel
 };
 // Rotate q and k in an fp32 qkv [M, 3C] (the FP32 plain path).
 wm_status launch_rope_f32(float* qkv, long M, const RopeArgs* rope_dev, const RopeArgs& rope_host, cudaStream_t s);
@@ -168,7 +206,8 @@ wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
 
 // variant: WM_NA_* of wm.h (0 = tuned plan / the shape's fixed family).
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
-                         int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s, int variant = 0);
+                         int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s, int variant = 0,
+                         bool pdl = false);
 // One line per autotuned attention shape: the plan chosen and its time.
 std::string describe_na_plans();
 // Times the candidate CTA plans of the attention kernel for this exact shape
