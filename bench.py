@@ -338,6 +338,9 @@ def run_ours(args):
         nbytes = hin.numel() * 4
         out["e2e"] = {"value": ws * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                       "d2h_bytes_per_step": nbytes, "call": "wm_forecast_host(lead 6 h)"}
+    # ---------------- 0.25-degree fields -> 14-day forecast -> fields (encoder, rollout, decoder)
+    if not args.no_fields and rank == 0:
+        out["fields_14d_full"] = fields_bench(wm, torch, dev, ctx, shape)
     out["autotune"] = wm.wm_autotune_report().strip().splitlines()
     wm.wm_destroy(ctx)
 
@@ -358,6 +361,44 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def fields_bench(wm, torch, dev, ctx, shape, lead=336, reps=2):
+    """Encoder + 14-day latent rollout + decoder on the 0.25-degree grid (BF16)."""
+    cd = synth.FULL_CODEC
+    w = synth.codec_weights(cd, shape.C, seed=0)
+    codec = wm.wm_codec_create(wm.make_codec_config(cd, shape.C, wm.WM_PREC_BF16), synth.pack_codec_weights(w))
+    g = torch.Generator(device=dev)
+    g.manual_seed(1)
+    atm = torch.randn(cd.levels, cd.H0, cd.W0, cd.v_atm, device=dev, generator=g)
+    sfc = torch.randn(cd.H0, cd.W0, cd.v_sfc_in, device=dev, generator=g)
+    cst = torch.randn(cd.H0, cd.W0, cd.n_const, device=dev, generator=g)
+    lat = torch.empty(cd.D, cd.H, cd.W, shape.C, device=dev)
+    a_out = torch.empty(cd.levels, cd.H0, cd.W0, cd.v_atm, device=dev)
+    s_out = torch.empty(cd.H0, cd.W0, cd.v_sfc_out, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    enc_ms = timed(lambda: wm.wm_encode(codec, atm, sfc, cst, lat), 3)
+    dec_ms = timed(lambda: wm.wm_decode(codec, lat, a_out, s_out), 3)
+    fc_ms = timed(lambda: wm.wm_forecast_fields(ctx, codec, atm, sfc, cst, lead, lat, a_out, s_out), reps)
+    wm.wm_codec_destroy(codec)
+    return {"workload": f"0.25-degree grid {cd.H0}x{cd.W0}: {cd.v_atm} atmospheric variables x {cd.levels} levels, "
+                        f"{cd.v_sfc_in} surface inputs + {cd.n_const} constants -> {cd.v_sfc_out} surface outputs; "
+                        f"encoder/decoder width {cd.Ce}, {cd.blocks} NA blocks each; lead {lead} h "
+                        f"({lead // 6} six-hour steps); random fields", "precision": "bf16",
+            "encode_ms": enc_ms, "decode_ms": dec_ms, "forecast_s": fc_ms / 1e3,
+            "forecasts_per_s": 1e3 / fc_ms}
 
 
 def small_rollout(wm, torch, dev, reps=3):
@@ -578,6 +619,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-fields", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=120)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -278,6 +278,68 @@ wm_status wm_op_layernorm_e4m3(const float* x, const float* gamma, const float* 
  * the scales do not depend on the batch or the request. */
 wm_status wm_fp8_scales(wm_ctx* ctx, int which, int block, float* out);
 
+/* ------------------------------------------------------------------------
+ * Encoder and decoder (Section 2.1 "Encoder-processor-decoder architecture";
+ * Appendix A.1 variables, A.2 architecture). The paper gives the grid (0.25
+ * degrees -> 2-degree latent), the variables (5 atmospheric on 28 pressure
+ * levels, 8 surface inputs, 17 surface outputs), the constant fields
+ * concatenated with the input, and 2 NA blocks of width 1024 on each side; it
+ * does not list the convolution layers. This library's reading:
+ *   encoder: atmosphere zero-padded at the top (index 0 side) to level_pad
+ *     levels; a strided convolution (kernel = stride = pd levels x p x p
+ *     pixels) of the 5 variables -> Ce channels per latent token; a strided
+ *     convolution (p x p) of surface inputs + constants -> Ce for the last
+ *     latent level; `blocks` NA blocks at width Ce; a linear map Ce -> C.
+ *   decoder: linear C -> Ce; `blocks` NA blocks; transposed convolutions
+ *     (kernel = stride) back to the atmosphere (padding levels dropped) and
+ *     the surface outputs. ResNet blocks are not built.
+ * Physical fields (device, float32, contiguous, channel last):
+ *   atm    [levels][H0][W0][v_atm]      sfc  [H0][W0][v_sfc_in]
+ *   consts [H0][W0][n_const]            atm_out [levels][H0][W0][v_atm]
+ *   sfc_out [H0][W0][v_sfc_out]
+ * Latent: float32 [D][H][W][C], D = level_pad / pd + 1 (surface last),
+ * H = H0 / p, W = W0 / p.
+ * Weights (host float32 blob, n_floats long): matrices [out][in] with the
+ * convolution kernels flattened as (level, row, column, channel):
+ *   embed_atm_w [Ce][pd*p*p*v_atm], embed_atm_b [Ce],
+ *   embed_sfc_w [Ce][p*p*(v_sfc_in+n_const)], embed_sfc_b [Ce],
+ *   enc_out_w [C][Ce], enc_out_b [C], dec_in_w [Ce][C], dec_in_b [Ce],
+ *   unembed_atm_w [pd*p*p*v_atm][Ce], unembed_atm_b [pd*p*p*v_atm],
+ *   unembed_sfc_w [p*p*v_sfc_out][Ce], unembed_sfc_b [p*p*v_sfc_out],
+ *   then the encoder's and the decoder's NA blocks in the processor blob
+ *   layout (wm_create_from_host: encoder blocks first).
+ * ------------------------------------------------------------------------ */
+typedef struct wm_codec wm_codec;
+
+typedef struct {
+  int H0, W0;                  /* physical grid; multiples of p */
+  int levels, level_pad, pd;   /* pressure levels, padded count (multiple of pd, >= levels), levels per token */
+  int p;                       /* pixels per token along latitude and longitude */
+  int v_atm, v_sfc_in, v_sfc_out, n_const;
+  int Ce, heads, kd, kh, kw;   /* NA blocks of the encoder / decoder (window odd, dh = Ce/heads) */
+  int blocks;                  /* NA blocks on each side (>= 1) */
+  int C;                       /* latent width (the processor's C) */
+  int lon_periodic;
+  float ln_eps;
+  int precision;               /* WM_PREC_FP32 or WM_PREC_BF16 */
+} wm_codec_config;
+
+/* Upload weights and allocate the workspace for one field set. Errors:
+ * WM_ERR_INVALID_ARG for inconsistent sizes or a blob of the wrong length,
+ * WM_ERR_OOM, WM_ERR_CUDA. */
+wm_status wm_codec_create(const wm_codec_config* cfg, const float* host_weights, size_t n_floats, wm_codec** out);
+wm_status wm_codec_destroy(wm_codec* codec);
+/* Physical fields -> latent (all device pointers; asynchronous on stream). */
+wm_status wm_encode(wm_codec* codec, const float* atm, const float* sfc, const float* consts, float* latent,
+                    void* stream);
+/* Latent -> physical fields (device pointers; the latent is not modified). */
+wm_status wm_decode(wm_codec* codec, const float* latent, float* atm_out, float* sfc_out, void* stream);
+/* Encode, roll the latent out to lead_hours with ctx's processors (ctx's latent
+ * shape must equal the codec's), decode. latent_ws: device scratch of
+ * D*H*W*C floats owned by the caller. */
+wm_status wm_forecast_fields(wm_ctx* ctx, wm_codec* codec, const float* atm, const float* sfc, const float* consts,
+                             int lead_hours, float* latent_ws, float* atm_out, float* sfc_out, void* stream);
+
 /* 3D neighborhood attention on qkv [batch*D*H*W, 3C] (q | k | v, each head-major)
  * -> out [batch*D*H*W, C]. precision FP32: float32 in/out; BF16: bfloat16 in/out
  * (BF16 requires dh = C/heads in {16, 32, 48, 64}).

@@ -38,6 +38,13 @@ class wm_config(ctypes.Structure):
                 ("rope", _c_int)]
 
 
+class wm_codec_config(ctypes.Structure):
+    _fields_ = [("H0", _c_int), ("W0", _c_int), ("levels", _c_int), ("level_pad", _c_int), ("pd", _c_int),
+                ("p", _c_int), ("v_atm", _c_int), ("v_sfc_in", _c_int), ("v_sfc_out", _c_int), ("n_const", _c_int),
+                ("Ce", _c_int), ("heads", _c_int), ("kd", _c_int), ("kh", _c_int), ("kw", _c_int), ("blocks", _c_int),
+                ("C", _c_int), ("lon_periodic", _c_int), ("ln_eps", _c_float), ("precision", _c_int)]
+
+
 _SIGS = {
     "wm_create": (_c_int, [ctypes.POINTER(wm_config), ctypes.c_char_p, ctypes.POINTER(_vp)]),
     "wm_create_from_host": (_c_int, [ctypes.POINTER(wm_config), _vp, _sz, ctypes.POINTER(_vp)]),
@@ -71,6 +78,11 @@ _SIGS = {
     "wm_op_linear_e4m3": (_c_int, [_vp, _vp, _c_float, _vp, _vp, _c_float, _c_int, _c_int, _c_int, _c_int, _vp]),
     "wm_op_layernorm_e4m3": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_float, _c_float, _vp]),
     "wm_fp8_scales": (_c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_c_float)]),
+    "wm_codec_create": (_c_int, [ctypes.POINTER(wm_codec_config), _vp, _sz, ctypes.POINTER(_vp)]),
+    "wm_codec_destroy": (_c_int, [_vp]),
+    "wm_encode": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "wm_decode": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "wm_forecast_fields": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -326,3 +338,39 @@ def wm_fp8_scales(ctx, which, block) -> tuple:
     out = (_c_float * 4)()
     _check(lib().wm_fp8_scales(ctx, int(which), int(block), out))
     return tuple(out)
+
+
+# ------------------------------------------------------- encoder / decoder ---
+
+def make_codec_config(codec, C, precision=WM_PREC_BF16) -> wm_codec_config:
+    """wm_codec_config from an object with the fields of wm_codec_config (synth.Codec) and the latent width C."""
+    return wm_codec_config(codec.H0, codec.W0, codec.levels, codec.level_pad, codec.pd, codec.p, codec.v_atm,
+                           codec.v_sfc_in, codec.v_sfc_out, codec.n_const, codec.Ce, codec.heads, codec.kd,
+                           codec.kh, codec.kw, codec.blocks, int(C), int(bool(codec.lon_periodic)),
+                           float(codec.ln_eps), int(precision))
+
+
+def wm_codec_create(cfg: wm_codec_config, weights) -> int:
+    """weights: contiguous float32 host array (numpy)."""
+    import numpy as np
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    out = _vp()
+    _check(lib().wm_codec_create(ctypes.byref(cfg), w.ctypes.data, w.size, ctypes.byref(out)))
+    return out.value
+
+
+def wm_codec_destroy(codec) -> None:
+    _check(lib().wm_codec_destroy(codec))
+
+
+def wm_encode(codec, atm, sfc, consts, latent, stream=None) -> None:
+    _check(lib().wm_encode(codec, _ptr(atm), _ptr(sfc), _ptr(consts), _ptr(latent), _stream(stream)))
+
+
+def wm_decode(codec, latent, atm_out, sfc_out, stream=None) -> None:
+    _check(lib().wm_decode(codec, _ptr(latent), _ptr(atm_out), _ptr(sfc_out), _stream(stream)))
+
+
+def wm_forecast_fields(ctx, codec, atm, sfc, consts, lead_hours, latent_ws, atm_out, sfc_out, stream=None) -> None:
+    _check(lib().wm_forecast_fields(ctx, codec, _ptr(atm), _ptr(sfc), _ptr(consts), int(lead_hours), _ptr(latent_ws),
+                                    _ptr(atm_out), _ptr(sfc_out), _stream(stream)))
