@@ -248,6 +248,40 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
   constexpr int ls = LS, smask = (1 << LS) - 1;
   const int WC = p.WC;
   const int mi = lane >> 3;
+  // Shared-memory byte address of this lane's ldmatrix row for key group gg.
+  // For 8- and 16-wide rectangles a group is 2 or 1 whole rectangle rows, so
+  // the address is the lane's row-0 address plus a row index clamped into the
+  // rectangle (keys past it are masked). 32-wide rectangles use the general
+  // row / column split.
+  constexpr int RPG = LS == 3 ? 2 : 1;                   // rectangle rows per 16-key group (LS <= 4)
+  const int last_row = (q.nkeys >> LS) - 1;
+  const uint32_t rstride = (uint32_t)(WC * DHP * 2);
+  const uint32_t kbase = sK32 + (uint32_t)(((q.wr0 * WC + q.wc0 +
+                                             (LS == 3 ? (lane & 7) : (((mi >> 1) * 8 + (lane & 7)) & smask))) * DHP +
+                                            (mi & 1) * 8) * 2);
+  const uint32_t vbase = sV32 + (uint32_t)(((q.wr0 * WC + q.wc0 +
+                                             (LS == 3 ? (lane & 7) : (((mi & 1) * 8 + (lane & 7)) & smask))) * DHP +
+                                            (mi >> 1) * 8) * 2);
+  auto k_addr = [&](int gg) -> uint32_t {
+    if constexpr (LS <= 4) {
+      return kbase + (uint32_t)min(RPG * gg + (LS == 3 ? (mi >> 1) : 0), last_row) * rstride;
+    } else {
+      int jk = gg * 16 + (mi >> 1) * 8 + (lane & 7);
+      if (jk >= q.nkeys) jk = 0;
+      const int krow = (q.wr0 + (jk >> ls)) * WC + q.wc0 + (jk & smask);
+      return sK32 + (uint32_t)((krow * DHP + (mi & 1) * 8) * 2);
+    }
+  };
+  auto v_addr = [&](int gg) -> uint32_t {
+    if constexpr (LS <= 4) {
+      return vbase + (uint32_t)min(RPG * gg + (LS == 3 ? (mi & 1) : 0), last_row) * rstride;
+    } else {
+      int jv = gg * 16 + (mi & 1) * 8 + (lane & 7);
+      if (jv >= q.nkeys) jv = 0;
+      const int vrow = (q.wr0 + (jv >> ls)) * WC + q.wc0 + (jv & smask);
+      return sV32 + (uint32_t)((vrow * DHP + (mi >> 1) * 8) * 2);
+    }
+  };
   for (int g0 = 0; g0 < q.ngroups; g0 += GCH) {
     float s[GCH][2][4];
 #pragma unroll
@@ -255,13 +289,11 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
 #pragma unroll
       for (int nb = 0; nb < 2; ++nb) s[gi][nb][0] = s[gi][nb][1] = s[gi][nb][2] = s[gi][nb][3] = 0.f;
       if (g0 + gi < q.ngroups) {
-        int jk = (g0 + gi) * 16 + (mi >> 1) * 8 + (lane & 7);
-        if (jk >= q.nkeys) jk = 0;
-        const int krow = (q.wr0 + (jk >> ls)) * WC + q.wc0 + (jk & smask);
+        const uint32_t ka = k_addr(g0 + gi);
 #pragma unroll
         for (int kc = 0; kc < KC; ++kc) {
           uint32_t b0, b1, b2, b3;
-          ldsm_x4(sK32 + (uint32_t)((krow * DHP + kc * 16 + (mi & 1) * 8) * 2), b0, b1, b2, b3);
+          ldsm_x4(ka + kc * 32, b0, b1, b2, b3);
           mma_bf16(s[gi][0], q.qa[kc][0], q.qa[kc][1], q.qa[kc][2], q.qa[kc][3], b0, b1);
           mma_bf16(s[gi][1], q.qa[kc][0], q.qa[kc][1], q.qa[kc][2], q.qa[kc][3], b2, b3);
         }
@@ -343,13 +375,11 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
       const uint32_t pa1 = pack_bf16(pr[0][2], pr[0][3]);
       const uint32_t pa2 = pack_bf16(pr[1][0], pr[1][1]);
       const uint32_t pa3 = pack_bf16(pr[1][2], pr[1][3]);
-      int jv = (g0 + gi) * 16 + (mi & 1) * 8 + (lane & 7);
-      if (jv >= q.nkeys) jv = 0;
-      const int vrow = (q.wr0 + (jv >> ls)) * WC + q.wc0 + (jv & smask);
+      const uint32_t va = v_addr(g0 + gi);
 #pragma unroll
       for (int nd = 0; nd < ND; nd += 2) {
         uint32_t b0, b1, b2, b3;
-        ldsm_x4_t(sV32 + (uint32_t)((vrow * DHP + nd * 8 + (mi >> 1) * 8) * 2), b0, b1, b2, b3);
+        ldsm_x4_t(va + nd * 16, b0, b1, b2, b3);
         mma_bf16(q.o[nd], pa0, pa1, pa2, pa3, b0, b1);
         mma_bf16(q.o[nd + 1], pa0, pa1, pa2, pa3, b2, b3);
       }
@@ -414,7 +444,7 @@ struct WarpQT {
   float o[MD][4];         // O^T: (dh g / g+8 of tile md) x (query 2t4 / 2t4+1)
   float mrow[2], lrow[2]; // queries 2t4, 2t4+1
   int rlo[2];
-  float cbias[2][2][2];   // [group parity][query k][key row i = g / g + 8]
+  uint64_t cbias2[2][2];  // [group parity][key row i = g / g + 8]: packed (0 or -inf) for queries 2 t4, 2 t4 + 1
   int wr0, wc0, nkeys, ngroups;
   int qh, qw;             // query g (the one this thread stores)
   bool qvalid, live;
@@ -436,6 +466,7 @@ __device__ __forceinline__ void warp_begin_t(WarpQT<DH, LS>& q, const Params& p,
   q.nkeys = (wr1 - q.wr0) << LS;
   q.ngroups = (q.nkeys + 15) / 16;
   // the thread's two softmax queries (columns 2 t4, 2 t4 + 1)
+  float cb[2][2][2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int qi = 2 * t4 + k;
@@ -448,9 +479,13 @@ __device__ __forceinline__ void warp_begin_t(WarpQT<DH, LS>& q, const Params& p,
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         const int col = (hf * 16 + g + 8 * i) & smask;
-        q.cbias[hf][k][i] = ((colmask >> col) & 1u) ? 0.f : -INFINITY;
+        cb[hf][i][k] = ((colmask >> col) & 1u) ? 0.f : -INFINITY;
       }
   }
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) q.cbias2[hf][i] = pack_f2(cb[hf][i][0], cb[hf][i][1]);
   // the query this thread loads and stores: query g
   q.qh = wh0 + g / p.WW;
   q.qw = ww0 + g % p.WW;
@@ -478,15 +513,36 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
   const int WC = p.WC;
   const int mi = lane >> 3;
   const int g = lane >> 2;
-  // shared-memory byte offset of rectangle key j (keys past the rectangle
-  // read key 0: they are masked)
-  auto key_off = [&](int j) -> uint32_t {
-    if (j >= q.nkeys) j = 0;
-    return (uint32_t)(((q.wr0 + (j >> LS)) * WC + q.wc0 + (j & smask)) * (DHP * 2));
-  };
+  // Shared-memory byte address of this lane's ldmatrix row for key group gg
+  // (as in the Q.K^T family: row-0 address plus a clamped row index for 8-
+  // and 16-wide rectangles; keys past the rectangle are masked).
+  constexpr int RPG = LS == 3 ? 2 : 1;
+  const int last_row = (q.nkeys >> LS) - 1;
+  const uint32_t rstride = (uint32_t)(WC * DHP * 2);
   const int lk = (mi & 1) * 8 + (lane & 7);            // key row this lane addresses in a K ldmatrix
   const int lv = (mi >> 1) * 8 + (lane & 7);           // ... in a V ldmatrix.trans
-  const uint32_t kc0 = sK32 + (uint32_t)((mi >> 1) * 16), vc0 = sV32 + (uint32_t)((mi & 1) * 16);
+  const uint32_t kbase = sK32 + (uint32_t)(((q.wr0 * WC + q.wc0 + (LS == 3 ? (lane & 7) : (lk & smask))) * DHP +
+                                            (mi >> 1) * 8) * 2);
+  const uint32_t vbase = sV32 + (uint32_t)(((q.wr0 * WC + q.wc0 + (LS == 3 ? (lane & 7) : (lv & smask))) * DHP +
+                                            (mi & 1) * 8) * 2);
+  auto k_addr = [&](int gg) -> uint32_t {
+    if constexpr (LS <= 4) {
+      return kbase + (uint32_t)min(RPG * gg + (LS == 3 ? (mi & 1) : 0), last_row) * rstride;
+    } else {
+      int j = gg * 16 + lk;
+      if (j >= q.nkeys) j = 0;
+      return sK32 + (uint32_t)((((q.wr0 + (j >> LS)) * WC + q.wc0 + (j & smask)) * DHP + (mi >> 1) * 8) * 2);
+    }
+  };
+  auto v_addr = [&](int gg) -> uint32_t {
+    if constexpr (LS <= 4) {
+      return vbase + (uint32_t)min(RPG * gg + (LS == 3 ? (mi >> 1) : 0), last_row) * rstride;
+    } else {
+      int j = gg * 16 + lv;
+      if (j >= q.nkeys) j = 0;
+      return sV32 + (uint32_t)((((q.wr0 + (j >> LS)) * WC + q.wc0 + (j & smask)) * DHP + (mi & 1) * 8) * 2);
+    }
+  };
   for (int g0 = 0; g0 < q.ngroups; g0 += GCH) {
     // Groups past the rectangle (in the last chunk) skip all their work
     // behind uniform branches; they would only contribute -inf to the max.
@@ -495,7 +551,7 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
     for (int gi = 0; gi < GCH; ++gi) {
       if (g0 + gi < q.ngroups) {
         s[gi][0] = s[gi][1] = s[gi][2] = s[gi][3] = 0.f;
-        const uint32_t ka = kc0 + key_off((g0 + gi) * 16 + lk);
+        const uint32_t ka = k_addr(g0 + gi);
 #pragma unroll
         for (int kc = 0; kc < KC; ++kc) {
           uint32_t a0, a1, a2, a3;
@@ -504,7 +560,9 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
         }
       }
     }
-    // mask + scale, per-query chunk max
+    // mask + scale, per-query chunk max; entries (key i, queries 2 t4 and
+    // 2 t4 + 1) go through the paired instructions together
+    const uint64_t scale2 = pack_f2(p.scale_log2, p.scale_log2);
     float mx[2] = {-INFINITY, -INFINITY};
 #pragma unroll
     for (int gi = 0; gi < GCH; ++gi) {
@@ -514,17 +572,16 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           const int row = (gg * 16 + 8 * i + g) >> LS;
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const bool rok = (unsigned)(row - q.rlo[k]) < (unsigned)p.kh;
-            const float v = rok ? fmaf(s[gi][2 * i + k], p.scale_log2, q.cbias[half][k][i]) : -INFINITY;
-            s[gi][2 * i + k] = v;
-            mx[k] = fmaxf(mx[k], v);
-          }
+          float t0, t1;
+          fma_f2(t0, t1, s[gi][2 * i], s[gi][2 * i + 1], scale2, q.cbias2[half][i]);
+          s[gi][2 * i] = ((unsigned)(row - q.rlo[0]) < (unsigned)p.kh) ? t0 : -INFINITY;
+          s[gi][2 * i + 1] = ((unsigned)(row - q.rlo[1]) < (unsigned)p.kh) ? t1 : -INFINITY;
         }
+        mx[0] = max3(mx[0], s[gi][0], s[gi][2]);
+        mx[1] = max3(mx[1], s[gi][1], s[gi][3]);
       }
     }
-    float mref[2];
+    float mref[2], alpha[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], 4));
@@ -532,28 +589,35 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
       mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], 16));
       const float mnew = fmaxf(q.mrow[k], mx[k]);
       mref[k] = (mnew == -INFINITY) ? 0.f : mnew;
-      const float alpha = ex2(q.mrow[k] - mref[k]);
+      alpha[k] = ex2(q.mrow[k] - mref[k]);
       q.mrow[k] = mnew;
-      q.lrow[k] *= alpha;
+    }
+    const uint64_t mref2 = pack_f2(mref[0], mref[1]), alpha2 = pack_f2(alpha[0], alpha[1]);
+    mul_f2(q.lrow[0], q.lrow[1], alpha2);
 #pragma unroll
-      for (int md = 0; md < MD; ++md) {
-        q.o[md][k] *= alpha;
-        q.o[md][2 + k] *= alpha;
-      }
+    for (int md = 0; md < MD; ++md) {
+      mul_f2(q.o[md][0], q.o[md][1], alpha2);
+      mul_f2(q.o[md][2], q.o[md][3], alpha2);
     }
     float lsum[2] = {0.f, 0.f};
 #pragma unroll
     for (int gi = 0; gi < GCH; ++gi) {
       if (g0 + gi < q.ngroups) {
         float pr[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) pr[e] = ex2(s[gi][e] - mref[e & 1]);
-        lsum[0] += pr[0] + pr[2];
-        lsum[1] += pr[1] + pr[3];
+        float d0, d1;
+        sub_f2(d0, d1, s[gi][0], s[gi][1], mref2);
+        pr[0] = ex2(d0);
+        pr[1] = ex2(d1);
+        sub_f2(d0, d1, s[gi][2], s[gi][3], mref2);
+        pr[2] = ex2(d0);
+        pr[3] = ex2(d1);
+        float e0, e1;
+        add_f2(e0, e1, pr[0], pr[1], pr[2], pr[3]);
+        add_f2(lsum[0], lsum[1], lsum[0], lsum[1], e0, e1);
         // P^T blocks (keys 0-7 / 8-15 x queries) transposed into the B operand
         const uint32_t b0 = movmatrix_t(pack_bf16(pr[0], pr[1]));
         const uint32_t b1 = movmatrix_t(pack_bf16(pr[2], pr[3]));
-        const uint32_t va = vc0 + key_off((g0 + gi) * 16 + lv);
+        const uint32_t va = v_addr(g0 + gi);
 #pragma unroll
         for (int md = 0; md < MD; ++md) {
           uint32_t a0, a1, a2, a3;
@@ -562,8 +626,7 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
         }
       }
     }
-    q.lrow[0] += lsum[0];
-    q.lrow[1] += lsum[1];
+    add_f2(q.lrow[0], q.lrow[1], q.lrow[0], q.lrow[1], lsum[0], lsum[1]);
   }
 }
 
