@@ -103,21 +103,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic(kind):
-    """DRAM bytes per launch of this kernel from the committed ncu summary, or
-    None when the kernel source has changed since that capture."""
+def _capture(kind, field="dram_bytes_per_launch"):
+    """A per-launch counter of this kernel from the committed ncu summary
+    (DRAM bytes, warp instructions), or None when the kernel source has
+    changed since that capture."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f).get(kind)
-    if not d:
+    if not d or field not in d:
         return None
     with open(os.path.join(ROOT, d["source"]), "rb") as f:
         if hashlib.sha256(f.read()).hexdigest() != d["source_sha256"]:
             return None
-    return d["dram_bytes_per_launch"]
+    return d[field]
+
+
+def _traffic(kind):
+    return _capture(kind, "dram_bytes_per_launch")
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -144,6 +149,21 @@ def _dist():
     return ws, rank, local
 
 
+def _small_block_seconds(threads=None) -> float:
+    """Seconds per FP64 oracle block on the small latent (4x24x48x128), timed in
+    a fresh interpreter whose BLAS runs `threads` threads (None: its default)."""
+    code = ("import sys, time; sys.path.insert(0, %r); import synth; from oracle import wm_oracle as orc; "
+            "s = synth.SMALL; x = synth.latent(s, 1, 1); w = synth.block_weights(s.C, 0, 0, 0); orc.block(x, w, s); "
+            "t = time.perf_counter(); [orc.block(x, w, s) for _ in range(3)]; "
+            "print((time.perf_counter() - t) / 3)") % ROOT
+    env = dict(os.environ)
+    if threads:
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[var] = str(threads)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    return float(out.stdout.strip().splitlines()[-1])
+
+
 def cpu_oracle_baseline(seconds_budget: float = 12.0, sample=CPU_SAMPLE):
     """Time the FP64 oracle on a bounded band of the workload; scale to forecasts/s."""
     from oracle import wm_oracle as orc
@@ -163,7 +183,20 @@ def cpu_oracle_baseline(seconds_budget: float = 12.0, sample=CPU_SAMPLE):
             "sample": (f"one block on a {sample.D}x{sample.H}x{sample.W}x{sample.C} latitude band of the latent "
                        f"({sample.N} tokens, x{reps}), {dt:.2f} s per block, scaled by tokens to 8 blocks x "
                        f"{synth.FULL.N} tokens; numpy float64, BLAS multi-threaded, gathers single-threaded"),
-            "seconds_per_forecast": sec_per_forecast}
+            "seconds_per_forecast": sec_per_forecast,
+            "small_latent": _small_latent_cpu()}
+
+
+def _small_latent_cpu():
+    """The small latent's oracle block on one thread and on every core, and
+    the 14-day rollout (448 blocks) those times imply."""
+    try:
+        one, allc = _small_block_seconds(1), _small_block_seconds(None)
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"error": str(e)[:200]}
+    return {"workload": "one block, latent 4x24x48x128, window 3x5x5", "block_s_1_thread": one,
+            "block_s_all_cores": allc, "cores": os.cpu_count(),
+            "rollout_336h_s_1_thread": 448 * one, "rollout_336h_s_all_cores": 448 * allc}
 
 
 def run_reference(args):
@@ -266,6 +299,20 @@ def run_ours(args):
                     "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"], "traffic": traffic,
                     "peak_source": f"{peaks['source']} bf16 sustained (kernel timed inside a long step)"}
     roofline["avg_launch_ms"] = avg_ms
+    # Instruction-issue view: the attention kernel's limit is issuing its
+    # softmax instructions, not DRAM. Warp instructions per launch from the
+    # ncu capture over the live launch time, against 4 schedulers x SMs x
+    # the SM clock sampled during the timed region (one warp instruction per
+    # scheduler per cycle).
+    instr = _capture(dom, "warp_instructions_per_launch")
+    clk_mhz = (clk.summary() or {}).get("sm_mhz") or 2070.0
+    if instr:
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        issue_peak = 4 * n_sm * clk_mhz * 1e6
+        roofline["issue"] = {"warp_instructions_per_launch": instr,
+                             "achieved_per_s": instr / (avg_ms * 1e-3), "peak_per_s": issue_peak,
+                             "frac": instr / (avg_ms * 1e-3) / issue_peak,
+                             "peak_source": f"4 warp schedulers x {n_sm} SMs x median SM clock under load"}
     roofline["kernels_ms_per_step"] = {k: v[0] / args.steps for k, v in kt.items()}
     roofline["gemm_tflops"] = {k: flops[k] / (kt[k][0] / kt[k][1] * 1e-3) / 1e12 for k in ("qkv", "proj", "fc1", "fc2")
                                if kt[k][1]}
