@@ -326,7 +326,9 @@ typedef struct {
 
 /* Upload weights and allocate the workspace for one field set. Errors:
  * WM_ERR_INVALID_ARG for inconsistent sizes or a blob of the wrong length,
- * WM_ERR_OOM, WM_ERR_CUDA. */
+ * WM_ERR_OOM, WM_ERR_CUDA. Calls on one codec share its workspace: do not run
+ * two of them concurrently (different streams or threads); use one codec per
+ * concurrent caller. */
 wm_status wm_codec_create(const wm_codec_config* cfg, const float* host_weights, size_t n_floats, wm_codec** out);
 wm_status wm_codec_destroy(wm_codec* codec);
 /* Physical fields -> latent (all device pointers; asynchronous on stream). */
