@@ -400,7 +400,7 @@ def run_ours(args):
         out.update(hourly_ensemble_bench(wm, torch, dev))
 
     if not args.no_serve and rank == 0:
-        out["serve"] = serve_bench(wm, torch, n_requests=args.serve_requests)
+        out["serve"] = serve_bench(wm, torch, n_requests=args.serve_requests, bf16_only=args.serve_bf16_only)
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_oracle_baseline()
@@ -577,25 +577,56 @@ def hourly_ensemble_bench(wm, torch, dev, full_members=8, reps=2):
     return res
 
 
-def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0):
+def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0, bf16_only=False):
     """Poisson request stream on the small latent through the continuous-batching server.
 
     Requests: exponential inter-arrivals (mean 1/rate s), lead times uniform in
-    1..336 h, latent i seeded by its request index. Reported per precision:
-    p50/p99 latency (submit -> finished) at the offered rate, forecasts/s
-    closed-loop at saturation, and the BF16-vs-FP32 error of the served results.
+    1..336 h, latent i seeded by its request index (generated when the request
+    is first needed). Reported per precision: p50/p99 latency (submit ->
+    finished) at the offered rate, forecasts/s closed-loop at saturation; for
+    BF16 also the first (up to 240) requests of the stream under an HBM budget
+    of one resident request (later arrivals queue until the slot frees); the
+    BF16-vs-FP32 error of the served results.
     """
     s = synth.SMALL
     p6, p1 = synth.processor_weights(s, seed=0)
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, n_requests)
     leads = rng.integers(1, 337, n_requests)
-    xs = [synth.latent(s, 1, seed=1000 + i) for i in range(n_requests)]
+    cache = {}
+
+    def latent(i):
+        if i not in cache:
+            cache[i] = synth.latent(s, 1, seed=1000 + i)
+        return cache[i]
+
     max_batch = 16
     res = {"workload": (f"Poisson arrivals {rate}/s, {n_requests} requests, leads U{{1..336}} h, latent 4x24x48x128, "
                         f"P6 8 + P1 4 blocks, max batch {max_batch}")}
     outs = {}
-    for prec, name in ((wm.WM_PREC_BF16, "bf16"), (wm.WM_PREC_FP32, "fp32")):
+
+    def open_loop(srv, n=n_requests):
+        t0 = time.perf_counter()
+        arrive = np.cumsum(gaps)
+        ids, got = [], {}
+        i = 0
+        while len(got) < n:
+            now = time.perf_counter() - t0
+            while i < n and arrive[i] <= now:
+                ids.append(wm.wm_server_submit(srv, latent(i), int(leads[i])))
+                i += 1
+            for j, rid in enumerate(ids):
+                if j in got:
+                    continue
+                buf = np.empty_like(latent(0))
+                done, _ = wm.wm_server_poll(srv, rid, buf)
+                if done:
+                    got[j] = buf
+            time.sleep(0.0005)
+        return got, wm.wm_server_stats(srv)
+
+    precs = ((wm.WM_PREC_BF16, "bf16"),) if bf16_only else ((wm.WM_PREC_BF16, "bf16"), (wm.WM_PREC_FP32, "fp32"))
+    for prec, name in precs:
         ctx = wm.wm_create_from_host(wm.make_config(s, prec), synth.pack_weights(p6, p1))
         lat_floats, ws = wm.wm_ctx_sizes(ctx, max_batch)
         budget = ws + (max_batch + 64) * lat_floats * 4   # 64 resident request slots
@@ -603,24 +634,7 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0):
             # ---- open loop at the offered rate
             srv = wm.wm_server_start(ctx, budget, max_batch)
             try:
-                t0 = time.perf_counter()
-                arrive = np.cumsum(gaps)
-                ids, got = [], {}
-                i = 0
-                while len(got) < n_requests:
-                    now = time.perf_counter() - t0
-                    while i < n_requests and arrive[i] <= now:
-                        ids.append(wm.wm_server_submit(srv, xs[i], int(leads[i])))
-                        i += 1
-                    for j, rid in enumerate(ids):
-                        if j in got:
-                            continue
-                        buf = np.empty_like(xs[0])
-                        done, _ = wm.wm_server_poll(srv, rid, buf)
-                        if done:
-                            got[j] = buf
-                    time.sleep(0.0005)
-                st = wm.wm_server_stats(srv)
+                got, st = open_loop(srv)
             finally:
                 wm.wm_server_stop(srv)
             outs[name] = got
@@ -628,12 +642,26 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0):
             res[f"{name}_p99_ms"] = st["p99_ms"]
             res[f"{name}_open_loop_forecasts_per_s"] = st["forecasts_per_s"]
             res[f"{name}_max_resident"] = st["max_active"]
+            if name == "bf16":
+                # ---- the stream's start with room for one resident request: arrivals queue
+                small = ws + (max_batch + 1) * lat_floats * 4
+                n_small = min(240, n_requests)
+                srv = wm.wm_server_start(ctx, small, max_batch)
+                try:
+                    _, st = open_loop(srv, n_small)
+                finally:
+                    wm.wm_server_stop(srv)
+                res["bf16_budget1_requests"] = n_small
+                res["bf16_budget1_p50_ms"] = st["p50_ms"]
+                res["bf16_budget1_p99_ms"] = st["p99_ms"]
+                res["bf16_budget1_max_resident"] = st["max_active"]
+                res["hbm_budget_bytes"] = {"default": int(budget), "small": int(small)}
             # ---- closed loop: all requests at once, throughput at saturation
-            n_sat = min(64, n_requests)
+            n_sat = min(64, n_requests) if not bf16_only else n_requests
             srv = wm.wm_server_start(ctx, budget, max_batch)
             try:
                 t0 = time.perf_counter()
-                ids = [wm.wm_server_submit(srv, xs[j], int(leads[j])) for j in range(n_sat)]
+                ids = [wm.wm_server_submit(srv, latent(j), int(leads[j])) for j in range(n_sat)]
                 left = set(ids)
                 while left:
                     for rid in list(left):
@@ -645,8 +673,11 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0):
             finally:
                 wm.wm_server_stop(srv)
             res[f"{name}_saturated_forecasts_per_s"] = n_sat / dt
+            res[f"{name}_saturated_requests"] = n_sat
         finally:
             wm.wm_destroy(ctx)
+    if bf16_only:
+        return res
     errs = [float(np.linalg.norm(outs["bf16"][j].astype(np.float64) - outs["fp32"][j]) /
                   np.linalg.norm(outs["fp32"][j].astype(np.float64))) for j in range(n_requests)]
     res["bf16_vs_fp32_rel_l2_median"] = float(np.median(errs))
@@ -668,6 +699,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fields", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-bf16-only", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
