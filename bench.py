@@ -363,12 +363,20 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         f8_ms = e0.elapsed_time(e1)
+        # per-kernel times of one more FP8-MLP step (eager, CUDA events per launch)
+        wm.wm_timing_begin(ctx, 8 * shape.blocks_p6 + 16)
+        wm.wm_processor_step(ctx, xa, wm.WM_P6)
+        torch.cuda.synchronize()
+        f8_kt = wm.wm_timing_end(ctx)
         wm.wm_set_precision(ctx, wm.WM_PREC_FP32)
         wm.wm_processor_step(ctx, xb, wm.WM_P6)
         wm.wm_set_precision(ctx, wm.WM_PREC_BF16)
         torch.cuda.synchronize()
         out["fp8mlp"] = {"value": 1e3 / f8_ms, "unit": UNIT, "ms_per_step": f8_ms,
-                         "fp8mlp_vs_fp32_rel_l2": wm.wm_rel_l2(xa, xb)}
+                         "fp8mlp_vs_fp32_rel_l2": wm.wm_rel_l2(xa, xb),
+                         "kernels_ms_per_step": {k: v[0] for k, v in f8_kt.items() if v[1]},
+                         "e4m3_tflops": {k: flops[k] / (f8_kt[k][0] / f8_kt[k][1] * 1e-3) / 1e12
+                                         for k in ("fc1", "fc2") if f8_kt[k][1]}}
         del xa, xb
 
     # ---------------- end to end through the host-buffer C-ABI call

@@ -45,6 +45,10 @@ struct Params {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// The online softmax moves its reference max only when a row's maximum grows
+// by more than this many powers of two.
+constexpr float kLazyLog2 = 8.f;
+
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
@@ -329,24 +333,39 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
         gmx[gi][rr] = max3(max3(s[gi][0][2 * rr], s[gi][0][2 * rr + 1], s[gi][1][2 * rr]), s[gi][1][2 * rr + 1],
                            -INFINITY);
     }
+    float mx[2];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {   // tree over the groups, then the quad
+      float m = gmx[0][rr];
+#pragma unroll
+      for (int gi = 1; gi < GCH; gi += 2) m = gi + 1 < GCH ? max3(m, gmx[gi][rr], gmx[gi + 1][rr]) : fmaxf(m, gmx[gi][rr]);
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      mx[rr] = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    }
+    // Lazy rescale: the reference max of the online softmax moves (and O and
+    // the row sums are rescaled) only when some row of the warp sees its
+    // maximum grow by more than kLazyLog2 (exponent units); otherwise the old
+    // reference stays and the chunk's probabilities are at most 2^kLazyLog2,
+    // well inside the FP32 accumulators and the bf16 P operand.
+    const bool grow = (mx[0] > q.mrow[0] + kLazyLog2) || (mx[1] > q.mrow[1] + kLazyLog2);
+    if (__any_sync(0xffffffffu, grow)) {
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const float mnew = fmaxf(q.mrow[rr], mx[rr]);
+        const float alpha = ex2(q.mrow[rr] - ((mnew == -INFINITY) ? 0.f : mnew));
+        const uint64_t alpha2 = pack_f2(alpha, alpha);
+        q.mrow[rr] = mnew;
+        q.lrow[rr] *= alpha;
+#pragma unroll
+        for (int nd = 0; nd < ND; ++nd) mul_f2(q.o[nd][2 * rr], q.o[nd][2 * rr + 1], alpha2);
+      }
+    }
     float mref[2];
     uint64_t mref2[2];
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {   // tree over the groups, then the quad
-      float mx = max3(max3(gmx[0][rr], gmx[1][rr], gmx[2][rr]), gmx[3][rr], -INFINITY);
-      if constexpr (GCH == 8)
-        mx = max3(max3(mx, gmx[4][rr], gmx[5][rr]), gmx[6][rr], gmx[7][rr]);
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-      const float mnew = fmaxf(q.mrow[rr], mx);
-      mref[rr] = (mnew == -INFINITY) ? 0.f : mnew;
+    for (int rr = 0; rr < 2; ++rr) {
+      mref[rr] = (q.mrow[rr] == -INFINITY) ? 0.f : q.mrow[rr];
       mref2[rr] = pack_f2(mref[rr], mref[rr]);
-      const float alpha = ex2(q.mrow[rr] - mref[rr]);
-      const uint64_t alpha2 = pack_f2(alpha, alpha);
-      q.mrow[rr] = mnew;
-      q.lrow[rr] *= alpha;
-#pragma unroll
-      for (int nd = 0; nd < ND; ++nd) mul_f2(q.o[nd][2 * rr], q.o[nd][2 * rr + 1], alpha2);
     }
     // P = exp2(S - m), row sums (per thread; quad-reduced at the end), O += P V
     float lsum[GCH][2];
@@ -384,20 +403,13 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
         mma_bf16(q.o[nd + 1], pa0, pa1, pa2, pa3, b2, b3);
       }
     }
-    {
-      float t0, t1, u0, u1;
-      add_f2(t0, t1, lsum[0][0], lsum[0][1], lsum[1][0], lsum[1][1]);
-      add_f2(u0, u1, lsum[2][0], lsum[2][1], lsum[3][0], lsum[3][1]);
-      add_f2(t0, t1, t0, t1, u0, u1);
-      if constexpr (GCH == 8) {
-        float v0, v1, w0, w1;
-        add_f2(v0, v1, lsum[4][0], lsum[4][1], lsum[5][0], lsum[5][1]);
-        add_f2(w0, w1, lsum[6][0], lsum[6][1], lsum[7][0], lsum[7][1]);
-        add_f2(v0, v1, v0, v1, w0, w1);
-        add_f2(t0, t1, t0, t1, v0, v1);
-      }
-      add_f2(q.lrow[0], q.lrow[1], q.lrow[0], q.lrow[1], t0, t1);
-    }
+    // pairwise tree over the chunk's groups: ((0+1)+(2+3)) + ((4+5)+(6+7)) ...
+#pragma unroll
+    for (int w = 1; w < GCH; w *= 2)
+#pragma unroll
+      for (int i = 0; i + w < GCH; i += 2 * w)
+        add_f2(lsum[i][0], lsum[i][1], lsum[i][0], lsum[i][1], lsum[i + w][0], lsum[i + w][1]);
+    add_f2(q.lrow[0], q.lrow[1], q.lrow[0], q.lrow[1], lsum[0][0], lsum[0][1]);
   }
 }
 
@@ -581,24 +593,31 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
         mx[1] = max3(mx[1], s[gi][1], s[gi][3]);
       }
     }
-    float mref[2], alpha[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], 4));
       mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], 8));
       mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], 16));
-      const float mnew = fmaxf(q.mrow[k], mx[k]);
-      mref[k] = (mnew == -INFINITY) ? 0.f : mnew;
-      alpha[k] = ex2(q.mrow[k] - mref[k]);
-      q.mrow[k] = mnew;
     }
-    const uint64_t mref2 = pack_f2(mref[0], mref[1]), alpha2 = pack_f2(alpha[0], alpha[1]);
-    mul_f2(q.lrow[0], q.lrow[1], alpha2);
+    // lazy rescale, as in the Q.K^T family
+    const bool grow = (mx[0] > q.mrow[0] + kLazyLog2) || (mx[1] > q.mrow[1] + kLazyLog2);
+    if (__any_sync(0xffffffffu, grow)) {
+      float alpha[2];
 #pragma unroll
-    for (int md = 0; md < MD; ++md) {
-      mul_f2(q.o[md][0], q.o[md][1], alpha2);
-      mul_f2(q.o[md][2], q.o[md][3], alpha2);
+      for (int k = 0; k < 2; ++k) {
+        const float mnew = fmaxf(q.mrow[k], mx[k]);
+        alpha[k] = ex2(q.mrow[k] - ((mnew == -INFINITY) ? 0.f : mnew));
+        q.mrow[k] = mnew;
+      }
+      const uint64_t alpha2 = pack_f2(alpha[0], alpha[1]);
+      mul_f2(q.lrow[0], q.lrow[1], alpha2);
+#pragma unroll
+      for (int md = 0; md < MD; ++md) {
+        mul_f2(q.o[md][0], q.o[md][1], alpha2);
+        mul_f2(q.o[md][2], q.o[md][3], alpha2);
+      }
     }
+    const uint64_t mref2 = pack_f2(q.mrow[0] == -INFINITY ? 0.f : q.mrow[0], q.mrow[1] == -INFINITY ? 0.f : q.mrow[1]);
     float lsum[2] = {0.f, 0.f};
 #pragma unroll
     for (int gi = 0; gi < GCH; ++gi) {
