@@ -225,6 +225,8 @@ __device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, uint32
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// all but the most recent bulk group have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Write this thread's row of a 32 x 32 output chunk into the warp's staging
@@ -404,6 +406,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t ebuf32 = smem_u32(ebuf);
     uint8_t* ebuf2 = ebuf + 4096;                 // EPI_RESID_LN: the bf16 copy's staging tile
     const uint32_t ebuf2_32 = ebuf32 + 4096;
+    // Narrow outputs (bf16: 2 KB per 32 x 32 chunk, e4m3: 1 KB) alternate
+    // between two halves of the warp's 4 KB staging tile, so a chunk waits
+    // only for the store of the chunk two before it.
+    constexpr bool kPing = !kResLN && EPI != EPI_RESID_F32 && EPI != EPI_STORE_F32;
+    constexpr int kChunkBytes = EPI == EPI_GELU_F8 ? 1024 : 2048;
+    uint32_t staged = 0;                          // chunks this warp has staged (all tiles)
     int it = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
       const int buf = it & 1;
@@ -483,6 +491,22 @@ __global__ void __launch_bounds__(THREADS, 1)
             fma_f2(v[j], v[j + 1], t0, t1, rstd2, pack_f2(lbb[j], lbb[j + 1]));
             if constexpr (EPI == EPI_LNF_GELU) gelu_erf2(v[j], v[j + 1]);
           }
+        } else if ((EPI == EPI_GELU || EPI == EPI_GELU_F8) && bias && n + 32 <= N) {
+          // whole chunk with a bias: the same steps two columns per instruction
+          const uint64_t alpha2 = pack_f2(alpha, alpha), oscale2 = pack_f2(out_scale, out_scale);
+          const float4* b4 = reinterpret_cast<const float4*>(bias + n);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 b = __ldg(b4 + q);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int j = 4 * q + 2 * h;
+              if constexpr (F8) mul_f2(v[j], v[j + 1], alpha2);
+              add_f2(v[j], v[j + 1], v[j], v[j + 1], h ? b.z : b.x, h ? b.w : b.y);
+              gelu_erf2(v[j], v[j + 1]);
+              if constexpr (EPI == EPI_GELU_F8) mul_f2(v[j], v[j + 1], oscale2);
+            }
+          }
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -536,18 +560,24 @@ __global__ void __launch_bounds__(THREADS, 1)
           wm2 += cq + d * d * (wn * 32.f / nt);
           wn = nt;
         }
-        if (lane == 0) bulk_wait_read_all();   // the previous chunk's store has left the staging tile
+        // the store that last used this staging buffer has read it
+        if (lane == 0) {
+          if constexpr (kPing) bulk_wait_read_1();
+          else bulk_wait_read_all();
+        }
         __syncwarp();
+        const uint32_t soff = kPing ? (staged & 1u) * (uint32_t)kChunkBytes : 0u;
+        ++staged;
         if constexpr (kResLN) stage_row<EPI_STORE_F32>(ebuf, v, lane);
-        else if constexpr (kLNF) stage_row<EPI_STORE>(ebuf, v, lane);
-        else stage_row<EPI>(ebuf, v, lane);
+        else if constexpr (kLNF) stage_row<EPI_STORE>(ebuf + soff, v, lane);
+        else stage_row<EPI>(ebuf + soff, v, lane);
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
           if constexpr (EPI == EPI_RESID_F32)
             tma_reduce_add_2d(&tmC, ebuf32, n, row0);
           else
-            tma_store_2d(&tmC, ebuf32, n, row0);
+            tma_store_2d(&tmC, ebuf32 + soff, n, row0);
           bulk_commit();
         }
         if constexpr (kResLN) {
