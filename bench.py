@@ -399,6 +399,7 @@ def run_ours(args):
     if not args.no_fields and rank == 0:
         out["fields_14d_full"] = fields_bench(wm, torch, dev, ctx, shape)
     out["autotune"] = wm.wm_autotune_report().strip().splitlines()
+    out["roofline"]["attn_halo"] = attn_halo(out["autotune"], shape)
     wm.wm_destroy(ctx)
 
     # ---------------- 14-day rollout on the small latent (whole rollout as one CUDA graph)
@@ -418,6 +419,30 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def attn_halo(report, shape):
+    """Scored keys per query and key level against the window's keys, for the
+    attention plan the tuner kept at this shape (its line in the report:
+    "... window=KDxKHxKW ... -> <family> ... patch=PHxPW ..."). A warp scores
+    the rectangle (PH + kh - 1) x pow2(PW + kw - 1) for its PH x PW queries
+    (16 queries, or 8 in the transposed family)."""
+    import re
+    win = f"window={shape.kd}x{shape.kh}x{shape.kw}"
+    for line in report:
+        if line.startswith("attention") and f"C={shape.C} " in line and win in line:
+            m = re.search(r"patch=(\d+)x(\d+)", line)
+            if not m:
+                return None
+            ph, pw = int(m.group(1)), int(m.group(2))
+            span = 8
+            while span < pw + shape.kw - 1:
+                span *= 2
+            issued = (ph + shape.kh - 1) * span
+            useful = shape.kh * shape.kw
+            return {"plan": line.split("->")[1].strip(), "scored_keys_per_query_level": issued,
+                    "window_keys_per_level": useful, "scored_over_useful": issued / useful}
+    return None
 
 
 def fields_bench(wm, torch, dev, ctx, shape, lead=336, reps=2):
@@ -593,7 +618,8 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0, bf16_only=False):
     Requests: exponential inter-arrivals (mean 1/rate s), lead times uniform in
     1..336 h, latent i seeded by its request index (generated when the request
     is first needed). Reported per precision: p50/p99 latency (submit ->
-    finished) at the offered rate, forecasts/s closed-loop at saturation; for
+    finished) at the offered rate, forecasts/s closed-loop at saturation
+    (BF16, FP8-MLP and the FP32 plain path); for
     BF16 also the first (up to 240) requests of the stream under an HBM budget
     of one resident request (later arrivals queue until the slot frees); the
     BF16-vs-FP32 error of the served results.
@@ -635,7 +661,9 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0, bf16_only=False):
             time.sleep(0.0005)
         return got, wm.wm_server_stats(srv)
 
-    precs = ((wm.WM_PREC_BF16, "bf16"),) if bf16_only else ((wm.WM_PREC_BF16, "bf16"), (wm.WM_PREC_FP32, "fp32"))
+    precs = ((wm.WM_PREC_BF16, "bf16"),) if bf16_only else ((wm.WM_PREC_BF16, "bf16"),
+                                                            (wm.WM_PREC_BF16_FP8MLP, "fp8mlp"),
+                                                            (wm.WM_PREC_FP32, "fp32"))
     for prec, name in precs:
         ctx = wm.wm_create_from_host(wm.make_config(s, prec), synth.pack_weights(p6, p1))
         lat_floats, ws = wm.wm_ctx_sizes(ctx, max_batch)
@@ -688,10 +716,11 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0, bf16_only=False):
             wm.wm_destroy(ctx)
     if bf16_only:
         return res
-    errs = [float(np.linalg.norm(outs["bf16"][j].astype(np.float64) - outs["fp32"][j]) /
-                  np.linalg.norm(outs["fp32"][j].astype(np.float64))) for j in range(n_requests)]
-    res["bf16_vs_fp32_rel_l2_median"] = float(np.median(errs))
-    res["bf16_vs_fp32_rel_l2_max"] = float(np.max(errs))
+    for name in ("bf16", "fp8mlp"):
+        errs = [float(np.linalg.norm(outs[name][j].astype(np.float64) - outs["fp32"][j]) /
+                      np.linalg.norm(outs["fp32"][j].astype(np.float64))) for j in range(n_requests)]
+        res[f"{name}_vs_fp32_rel_l2_median"] = float(np.median(errs))
+        res[f"{name}_vs_fp32_rel_l2_max"] = float(np.max(errs))
     return res
 
 

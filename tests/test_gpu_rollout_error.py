@@ -32,7 +32,8 @@ def test_rollout_error_curve_against_oracle():
     ctx = wm.wm_create_from_host(wm.make_config(s, wm.WM_PREC_BF16), synth.pack_weights(p6, p1))
     curves = {}
     try:
-        for prec, name in ((wm.WM_PREC_FP32, "fp32"), (wm.WM_PREC_BF16, "bf16")):
+        for prec, name in ((wm.WM_PREC_FP32, "fp32"), (wm.WM_PREC_BF16, "bf16"),
+                           (wm.WM_PREC_BF16_FP8MLP, "fp8mlp")):
             wm.wm_set_precision(ctx, prec)
             xt = torch.from_numpy(x).cuda()
             errs = []
@@ -56,5 +57,5 @@ def test_rollout_error_curve_against_oracle():
     # first step: 8 blocks, each within the per-block tolerance
     assert curves["fp32"][0] <= 8e-5
     assert curves["bf16"][0] <= 8 * 2e-2
-    assert all(np.isfinite(curves["bf16"])) and all(np.isfinite(curves["fp32"]))
-    assert curves["fp32"][-1] < curves["bf16"][-1]
+    assert all(all(np.isfinite(v)) for v in curves.values())
+    assert curves["fp32"][-1] < curves["bf16"][-1] < curves["fp8mlp"][-1]
