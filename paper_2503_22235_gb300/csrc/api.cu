@@ -29,8 +29,8 @@ namespace {
 
 struct BlockW {
   const float *ln1_g, *ln1_b, *wqkv, *bqkv, *wo, *bo, *ln2_g, *ln2_b, *w1, *b1, *w2, *b2;
-  bf16 *hqkv, *ho, *h1, *h2;
-  CUtensorMap tm_qkv[2], tm_o[2], tm_1[2], tm_2[2];  // [0]: box 128 rows, [1]: box 256 rows
+  bf16 *ho, *h2;       // bf16 Wo and W2 (Wqkv and W1 are used LayerNorm-folded, below)
+  CUtensorMap tm_o[2], tm_2[2];  // [0]: box 128 rows, [1]: box 256 rows
   // LayerNorm folded into QKV and FC1: bf16 W diag(gamma), its column sums,
   // and the folded bias b + W beta
   bf16 *fqkv, *f1;
@@ -482,7 +482,7 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
   WM_CUDA(cudaMalloc(&ctx->d_w32, n * 4));
   WM_CUDA(cudaMemcpy(ctx->d_w32, host, n * 4, cudaMemcpyHostToDevice));
   const size_t C = c.C;
-  const size_t mats = 12 * C * C;  // wqkv + wo + w1 + w2 per block
+  const size_t mats = 5 * C * C;   // bf16 wo + w2 per block
   WM_CUDA(cudaMalloc(&ctx->d_wh, mats * nb * 2));
   WM_CUDA(cudaMalloc(&ctx->d_wq, 8 * C * C * nb));
   WM_CUDA(cudaMalloc(&ctx->d_wf, 7 * C * C * nb * 2));
@@ -506,13 +506,9 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
     w.w2 = p; p += 4 * C * C;
     w.b2 = p; p += C;
     bf16* h = ctx->d_wh + mats * i;
-    w.hqkv = h; h += 3 * C * C;
     w.ho = h; h += C * C;
-    w.h1 = h; h += 4 * C * C;
     w.h2 = h;
-    WM_TRY(wm::launch_f32_to_bf16(w.wqkv, w.hqkv, 3 * C * C, 0));
     WM_TRY(wm::launch_f32_to_bf16(w.wo, w.ho, C * C, 0));
-    WM_TRY(wm::launch_f32_to_bf16(w.w1, w.h1, 4 * C * C, 0));
     WM_TRY(wm::launch_f32_to_bf16(w.w2, w.h2, 4 * C * C, 0));
     // ---- FP8 MLP: static per-tensor scales from bounds that hold for every input
     {
@@ -595,9 +591,7 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
       bool ok = true;
       for (int k = 0; k < 2; ++k) {
         const uint32_t box = k ? 256 : 128;
-        ok = ok && wm::make_tmap_bf16(&w.tm_qkv[k], w.hqkv, 3 * C, C, box);
         ok = ok && wm::make_tmap_bf16(&w.tm_o[k], w.ho, C, C, box);
-        ok = ok && wm::make_tmap_bf16(&w.tm_1[k], w.h1, 4 * C, C, box);
         ok = ok && wm::make_tmap_bf16(&w.tm_2[k], w.h2, C, 4 * C, box);
       }
       if (!ok) return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the weights");
