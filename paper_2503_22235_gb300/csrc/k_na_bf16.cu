@@ -287,20 +287,23 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
     }
   };
   for (int g0 = 0; g0 < q.ngroups; g0 += GCH) {
+    // Every group of the chunk is scored, without a branch, so the groups'
+    // MMA chains interleave; a group past the rectangle reads clamped (valid)
+    // keys and is masked below, contributing exactly zero.
     float s[GCH][2][4];
 #pragma unroll
     for (int gi = 0; gi < GCH; ++gi) {
 #pragma unroll
       for (int nb = 0; nb < 2; ++nb) s[gi][nb][0] = s[gi][nb][1] = s[gi][nb][2] = s[gi][nb][3] = 0.f;
-      if (g0 + gi < q.ngroups) {
-        const uint32_t ka = k_addr(g0 + gi);
+    }
 #pragma unroll
-        for (int kc = 0; kc < KC; ++kc) {
-          uint32_t b0, b1, b2, b3;
-          ldsm_x4(ka + kc * 32, b0, b1, b2, b3);
-          mma_bf16(s[gi][0], q.qa[kc][0], q.qa[kc][1], q.qa[kc][2], q.qa[kc][3], b0, b1);
-          mma_bf16(s[gi][1], q.qa[kc][0], q.qa[kc][1], q.qa[kc][2], q.qa[kc][3], b2, b3);
-        }
+    for (int kc = 0; kc < KC; ++kc) {
+#pragma unroll
+      for (int gi = 0; gi < GCH; ++gi) {
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4(k_addr(g0 + gi) + kc * 32, b0, b1, b2, b3);
+        mma_bf16(s[gi][0], q.qa[kc][0], q.qa[kc][1], q.qa[kc][2], q.qa[kc][3], b0, b1);
+        mma_bf16(s[gi][1], q.qa[kc][0], q.qa[kc][1], q.qa[kc][2], q.qa[kc][3], b2, b3);
       }
     }
     // mask + scale + chunk row max. Key j sits at rectangle row j >> LS and
@@ -371,10 +374,7 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
     float lsum[GCH][2];
 #pragma unroll
     for (int gi = 0; gi < GCH; ++gi) {
-      if (g0 + gi >= q.ngroups) {
-        lsum[gi][0] = lsum[gi][1] = 0.f;
-        continue;
-      }
+      // (a group past the rectangle has S = -inf: P = 0 adds exactly nothing)
       float pr[2][4];
 #pragma unroll
       for (int nb = 0; nb < 2; ++nb)
