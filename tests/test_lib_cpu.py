@@ -84,3 +84,33 @@ def test_binding_signatures_match_header_arity():
     for name, (_, args) in _binding._SIGS.items():
         assert name in arity, name
         assert len(args) == arity[name], (name, len(args), arity[name])
+
+
+def _header_struct_fields(name):
+    """[(field, c type)] of `typedef struct { ... } name;` in include/wm.h, in order."""
+    import re
+    with open(wm.HEADER) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    m = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = decl.split(None, 1)
+        fields += [(n.strip(), ctype) for n in names.split(",")]
+    return fields
+
+
+@pytest.mark.parametrize("name", ["wm_config", "wm_codec_config"])
+def test_binding_structs_mirror_the_header(name):
+    """The ctypes structures have the header's fields, in order, with matching types."""
+    import ctypes
+    cls = getattr(wm, name)
+    want = _header_struct_fields(name)
+    got = [(f, t) for f, t in cls._fields_]
+    assert [f for f, _ in got] == [f for f, _ in want]
+    kinds = {"int": ctypes.c_int, "float": ctypes.c_float}
+    for (f, t), (_, c) in zip(got, want):
+        assert t is kinds[c], (f, t, c)
