@@ -133,3 +133,27 @@ def test_codec_weight_blob_length_is_checked(weights):
     blob = synth.pack_codec_weights(weights)
     with pytest.raises(wm.WmError):
         wm.wm_codec_create(wm.make_codec_config(CD, C, wm.WM_PREC_BF16), blob[:-1])
+
+
+@pytest.mark.parametrize("prec", [wm.WM_PREC_FP32, wm.WM_PREC_BF16])
+def test_clamped_longitude_codec_matches_oracle(fields, prec):
+    """The same encoder and decoder with clamped (non-periodic) longitude windows."""
+    cd = dataclasses.replace(CD, lon_periodic=False)
+    w = synth.codec_weights(cd, C, seed=2, stress=True)
+    codec = wm.wm_codec_create(wm.make_codec_config(cd, C, prec), synth.pack_codec_weights(w))
+    try:
+        atm, sfc, cst = fields
+        lat = torch.empty(cd.D, cd.H, cd.W, C, device="cuda")
+        wm.wm_encode(codec, _dev(atm), _dev(sfc), _dev(cst), lat)
+        a_out = torch.empty(cd.levels, cd.H0, cd.W0, cd.v_atm, device="cuda")
+        s_out = torch.empty(cd.H0, cd.W0, cd.v_sfc_out, device="cuda")
+        wm.wm_decode(codec, lat, a_out, s_out)
+        torch.cuda.synchronize()
+        ref_lat = orc.encode(atm, sfc, cst, w, cd)
+        ra, rs = orc.decode(lat.cpu().numpy(), w, cd)
+        errs = (orc.rel_l2(lat.cpu().numpy(), ref_lat), orc.rel_l2(a_out.cpu().numpy(), ra),
+                orc.rel_l2(s_out.cpu().numpy(), rs))
+        print("clamped-longitude codec rel-L2", [f"{e:.2e}" for e in errs])
+        assert max(errs) <= TOL[prec], errs
+    finally:
+        wm.wm_codec_destroy(codec)

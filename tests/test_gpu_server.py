@@ -2,8 +2,9 @@
 
 Requests with uneven lead times arrive while others run, share batched
 processor steps, and each result must equal the same forecast computed alone
-(wm_latent_rollout on one latent) bit for bit: the kernels are row
-independent and the schedule per request does not depend on the mix.
+(wm_latent_rollout on one latent) bit for bit, in every precision (BF16,
+FP8-MLP, FP32): the kernels are row independent, the FP8 scales static, and
+the schedule per request does not depend on the mix.
 """
 import dataclasses
 import time
@@ -20,12 +21,13 @@ pytestmark = pytest.mark.gpu
 SHAPE = dataclasses.replace(synth.SMALL, blocks_p6=2, blocks_p1=1)
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=[wm.WM_PREC_BF16, wm.WM_PREC_BF16_FP8MLP, wm.WM_PREC_FP32],
+                ids=["bf16", "fp8mlp", "fp32"])
+def ctx(request):
     from paper_2503_22235_gb300 import build as wm_build
     wm_build.build()
     p6, p1 = synth.processor_weights(SHAPE, seed=0, stress=True)
-    c = wm.wm_create_from_host(wm.make_config(SHAPE, wm.WM_PREC_BF16), synth.pack_weights(p6, p1))
+    c = wm.wm_create_from_host(wm.make_config(SHAPE, request.param), synth.pack_weights(p6, p1))
     yield c
     wm.wm_destroy(c)
 
