@@ -135,6 +135,19 @@ wm_status wm_latent_rollout(wm_ctx* ctx, float* latent, int batch, int lead_hour
 wm_status wm_forecast_host(wm_ctx* ctx, const float* host_in, float* host_out, int batch,
                            int lead_hours, void* stream);
 
+/* A stream of n end-to-end forecasts from HOST memory: forecast i copies
+ * host_in[i] to the device, rolls it out to lead_hours and copies the result
+ * to host_out[i] (float32 [batch,D,H,W,C] each). Two library-owned device
+ * latents alternate, so the upload of forecast i + 1 and the download of
+ * forecast i - 1 run on library-owned copy streams while forecast i computes
+ * on `stream`. Each result equals wm_forecast_host's bit for bit. Returns
+ * once every result is in host memory. host_in[i] may repeat; host_out[i]
+ * must not alias another forecast's input or output that is still in flight
+ * (the same pointer for every output is fine: downloads are serialised).
+ * Pinned host buffers make the copies asynchronous DMA. */
+wm_status wm_forecast_host_many(wm_ctx* ctx, const float* const* host_in, float* const* host_out, int n, int batch,
+                                int lead_hours, void* stream);
+
 /* Batched uneven rollouts: latents[i] (device, one float32 latent each) is
  * advanced in place to lead_hours[i]. All requests advance together one
  * processor step per tick; the requests due for the same processor in a tick

@@ -54,6 +54,7 @@ _SIGS = {
     "wm_processor_step": (_c_int, [_vp, _vp, _c_int, _c_int, _vp]),
     "wm_latent_rollout": (_c_int, [_vp, _vp, _c_int, _c_int, _vp]),
     "wm_forecast_host": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
+    "wm_forecast_host_many": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _c_int, _c_int, _c_int, _vp]),
     "wm_rollout_batch": (_c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_c_int), _c_int, _vp]),
     "wm_schedule": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "wm_rollout_hourly": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _vp]),
@@ -187,6 +188,16 @@ def wm_latent_rollout(ctx, latent, lead_hours, stream=None):
 def wm_forecast_host(ctx, host_in, host_out, lead_hours, stream=None):
     _check(lib().wm_forecast_host(ctx, _ptr(host_in), _ptr(host_out), host_in.shape[0], int(lead_hours),
                                   _stream(stream)))
+
+
+def wm_forecast_host_many(ctx, host_ins, host_outs, lead_hours, stream=None):
+    n = len(host_ins)
+    if len(host_outs) != n:
+        raise ValueError("one output per input")
+    batch = host_ins[0].shape[0] if n else 1
+    ins = (_vp * max(n, 1))(*[_ptr(t) for t in host_ins])
+    outs = (_vp * max(n, 1))(*[_ptr(t) for t in host_outs])
+    _check(lib().wm_forecast_host_many(ctx, ins, outs, n, batch, int(lead_hours), _stream(stream)))
 
 
 def wm_rollout_batch(ctx, latents, lead_hours, stream=None):

@@ -310,6 +310,28 @@ def test_forecast_from_host_buffers_equals_device_rollout():
         wm.wm_destroy(ctx)
 
 
+def test_forecast_stream_from_host_buffers_equals_single_calls():
+    s = synth.Shape(D=4, H=24, W=48, C=128, heads=4, kd=3, kh=5, kw=5, blocks_p6=2, blocks_p1=1)
+    ctx, _, _ = make_ctx(s, wm.WM_PREC_BF16)
+    try:
+        xs = [torch.from_numpy(synth.latent(s, 2, seed=40 + i)).pin_memory() for i in range(5)]
+        outs = [torch.full_like(x, float("nan")).pin_memory() for x in xs]
+        wm.wm_forecast_host_many(ctx, xs, outs, 7)
+        for x, o in zip(xs, outs):
+            ref = torch.empty_like(x).pin_memory()
+            wm.wm_forecast_host(ctx, x, ref, 7)
+            assert torch.equal(o, ref)
+        # one input repeated into one shared output: the last result stays
+        shared = torch.empty_like(xs[0]).pin_memory()
+        wm.wm_forecast_host_many(ctx, [xs[1], xs[2], xs[3]], [shared] * 3, 7)
+        assert torch.equal(shared, outs[3])
+        wm.wm_forecast_host_many(ctx, [], [], 7)          # nothing to do
+        with pytest.raises(wm.WmError):
+            wm.wm_forecast_host_many(ctx, xs[:1], outs[:1], -1)
+    finally:
+        wm.wm_destroy(ctx)
+
+
 def test_batched_uneven_rollouts_equal_single_rollouts():
     s = synth.Shape(D=4, H=24, W=48, C=128, heads=4, kd=3, kh=5, kw=5, blocks_p6=2, blocks_p1=1)
     ctx, _, _ = make_ctx(s, wm.WM_PREC_BF16, max_batch=4)
