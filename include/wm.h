@@ -137,10 +137,10 @@ wm_status wm_forecast_host(wm_ctx* ctx, const float* host_in, float* host_out, i
 
 /* A stream of n end-to-end forecasts from HOST memory: forecast i copies
  * host_in[i] to the device, rolls it out to lead_hours and copies the result
- * to host_out[i] (float32 [batch,D,H,W,C] each). Two library-owned device
- * latents alternate, so the upload of forecast i + 1 and the download of
- * forecast i - 1 run on library-owned copy streams while forecast i computes
- * on `stream`. Each result equals wm_forecast_host's bit for bit. Returns
+ * to host_out[i] (float32 [batch,D,H,W,C] each). A ring of three
+ * library-owned device latents lets the upload of forecast i + 1 and the
+ * download of forecast i - 1 run on library-owned copy streams while forecast
+ * i computes on `stream`. Each result equals wm_forecast_host's bit for bit. Returns
  * once every result is in host memory. host_in[i] may repeat; host_out[i]
  * must not alias another forecast's input or output that is still in flight
  * (the same pointer for every output is fine: downloads are serialised).

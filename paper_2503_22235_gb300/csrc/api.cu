@@ -74,10 +74,10 @@ struct wm_ctx {
   size_t stage_cap = 0;  // floats
   float* d_io = nullptr;
   size_t io_cap = 0;     // floats
-  float* d_io2 = nullptr;                   // second latent of wm_forecast_host_many
-  size_t io2_cap = 0;
+  float* d_ring[3] = {};                    // wm_forecast_host_many's ring of device latents
+  size_t ring_cap[3] = {};
   cudaStream_t up_stream = nullptr, down_stream = nullptr;   // its copy streams
-  cudaEvent_t io_ev[6] = {};                // uploaded[2], computed[2], downloaded[2]
+  cudaEvent_t io_ev[9] = {};                // uploaded[3], computed[3], downloaded[3]
   // graphs
   std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
   // optional per-launch timing (CUDA events around each hot-path kernel)
@@ -687,7 +687,7 @@ wm_status wm_destroy(wm_ctx* ctx) {
   cudaFree(ctx->d_rope);
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_io);
-  cudaFree(ctx->d_io2);
+  for (float* p : ctx->d_ring) cudaFree(p);
   if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
   if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);
   for (cudaEvent_t e : ctx->io_ev)
@@ -765,37 +765,39 @@ wm_status wm_forecast_host_many(wm_ctx* ctx, const float* const* host_in, float*
     if (!host_in[i] || !host_out[i]) return fail(WM_ERR_INVALID_ARG, "a host pointer is NULL");
   if (n == 0) return WM_OK;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  constexpr int R = 3;
   const size_t floats = (size_t)batch * ctx->N * ctx->cfg.C;
-  WM_TRY(ensure_buffer(&ctx->d_io, &ctx->io_cap, floats));
-  WM_TRY(ensure_buffer(&ctx->d_io2, &ctx->io2_cap, floats));
+  for (int r = 0; r < R; ++r) WM_TRY(ensure_buffer(&ctx->d_ring[r], &ctx->ring_cap[r], floats));
   if (!ctx->up_stream) WM_CUDA(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking));
   if (!ctx->down_stream) WM_CUDA(cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking));
   for (cudaEvent_t& e : ctx->io_ev)
     if (!e) WM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   cudaStream_t s = (cudaStream_t)stream;
-  float* buf[2] = {ctx->d_io, ctx->d_io2};
   cudaEvent_t* up = ctx->io_ev;          // forecast's input is on the device
-  cudaEvent_t* comp = ctx->io_ev + 2;    // forecast's rollout is done
-  cudaEvent_t* down = ctx->io_ev + 4;    // forecast's result has left the buffer
-  // nothing queued earlier on `stream` may still be using the buffers
+  cudaEvent_t* comp = ctx->io_ev + R;    // forecast's rollout is done
+  cudaEvent_t* down = ctx->io_ev + 2 * R;  // forecast's result has left its latent
+  // nothing queued earlier on `stream` may still be using the ring
   WM_CUDA(cudaEventRecord(comp[0], s));
   WM_CUDA(cudaStreamWaitEvent(ctx->up_stream, comp[0], 0));
+  // Forecast i uses latent i mod 3: its upload overlaps forecast i - 1's
+  // rollout and needs only forecast i - 3's download to be done, so an upload
+  // and a download may each take up to a whole rollout.
   auto upload = [&](int i) -> wm_status {
-    const int b = i & 1;
-    if (i >= 2) WM_CUDA(cudaStreamWaitEvent(ctx->up_stream, down[b], 0));   // forecast i - 2 downloaded
-    WM_CUDA(cudaMemcpyAsync(buf[b], host_in[i], floats * 4, cudaMemcpyHostToDevice, ctx->up_stream));
+    const int b = i % R;
+    if (i >= R) WM_CUDA(cudaStreamWaitEvent(ctx->up_stream, down[b], 0));
+    WM_CUDA(cudaMemcpyAsync(ctx->d_ring[b], host_in[i], floats * 4, cudaMemcpyHostToDevice, ctx->up_stream));
     WM_CUDA(cudaEventRecord(up[b], ctx->up_stream));
     return WM_OK;
   };
   WM_TRY(upload(0));
   for (int i = 0; i < n; ++i) {
-    const int b = i & 1;
+    const int b = i % R;
     if (i + 1 < n) WM_TRY(upload(i + 1));
     WM_CUDA(cudaStreamWaitEvent(s, up[b], 0));
-    WM_TRY(wm_latent_rollout(ctx, buf[b], batch, lead_hours, stream));
+    WM_TRY(wm_latent_rollout(ctx, ctx->d_ring[b], batch, lead_hours, stream));
     WM_CUDA(cudaEventRecord(comp[b], s));
     WM_CUDA(cudaStreamWaitEvent(ctx->down_stream, comp[b], 0));
-    WM_CUDA(cudaMemcpyAsync(host_out[i], buf[b], floats * 4, cudaMemcpyDeviceToHost, ctx->down_stream));
+    WM_CUDA(cudaMemcpyAsync(host_out[i], ctx->d_ring[b], floats * 4, cudaMemcpyDeviceToHost, ctx->down_stream));
     WM_CUDA(cudaEventRecord(down[b], ctx->down_stream));
   }
   WM_CUDA(cudaStreamSynchronize(ctx->down_stream));
