@@ -244,6 +244,16 @@ __device__ __forceinline__ void warp_begin(WarpQ<DH, LS>& q, const Params& p, co
   q.lrow[0] = q.lrow[1] = 0.f;
 }
 
+// Calls f(std::integral_constant<int, r>) for the runtime r in 1 .. R (no
+// call for r = 0); r is warp-uniform.
+template <int R, class F>
+__device__ __forceinline__ void tail_chunk(int r, F& f) {
+  if constexpr (R >= 1) {
+    if (r == R) f(std::integral_constant<int, R>{});
+    else tail_chunk<R - 1>(r, f);
+  }
+}
+
 // One key level: S = Q K^T over the warp's rectangle (up to GCH groups of 16
 // keys before one online-softmax update), mask, softmax update, O += P V.
 template <int DH, int LS, int GCH>
@@ -286,20 +296,25 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
       return sV32 + (uint32_t)((vrow * DHP + (mi >> 1) * 8) * 2);
     }
   };
-  for (int g0 = 0; g0 < q.ngroups; g0 += GCH) {
+  // One chunk of G groups starting at g0: S for all of them, one online
+  // softmax update, O += P V. Full chunks have GCH groups; the level's last
+  // chunk has exactly the groups left (a compile-time size 1 .. GCH - 1), so
+  // no group is scored past the rectangle.
+  int g0 = 0;
+  auto chunk = [&](auto gsize) {
+    constexpr int G = decltype(gsize)::value;
     // Every group of the chunk is scored, without a branch, so the groups'
-    // MMA chains interleave; a group past the rectangle reads clamped (valid)
-    // keys and is masked below, contributing exactly zero.
-    float s[GCH][2][4];
+    // MMA chains interleave.
+    float s[G][2][4];
 #pragma unroll
-    for (int gi = 0; gi < GCH; ++gi) {
+    for (int gi = 0; gi < G; ++gi) {
 #pragma unroll
       for (int nb = 0; nb < 2; ++nb) s[gi][nb][0] = s[gi][nb][1] = s[gi][nb][2] = s[gi][nb][3] = 0.f;
     }
 #pragma unroll
     for (int kc = 0; kc < KC; ++kc) {
 #pragma unroll
-      for (int gi = 0; gi < GCH; ++gi) {
+      for (int gi = 0; gi < G; ++gi) {
         uint32_t b0, b1, b2, b3;
         ldsm_x4(k_addr(g0 + gi) + kc * 32, b0, b1, b2, b3);
         mma_bf16(s[gi][0], q.qa[kc][0], q.qa[kc][1], q.qa[kc][2], q.qa[kc][3], b0, b1);
@@ -313,17 +328,16 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
     // unsigned compare per n8 block. Entries 2 t4 and 2 t4 + 1 of a row go
     // through the paired instructions together.
     const uint64_t scale2 = pack_f2(p.scale_log2, p.scale_log2);
-    float gmx[GCH][2];
+    float gmx[G][2];
 #pragma unroll
-    for (int gi = 0; gi < GCH; ++gi) {
+    for (int gi = 0; gi < G; ++gi) {
       const int gg = g0 + gi;
-      const bool live = gg < q.ngroups;
 #pragma unroll
       for (int nb = 0; nb < 2; ++nb) {
         const int row = (gg * 16 + nb * 8) >> LS;
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr) {
-          const bool rok = live && ((unsigned)(row - q.rlo[rr]) < (unsigned)p.kh);
+          const bool rok = (unsigned)(row - q.rlo[rr]) < (unsigned)p.kh;
           const int half = (LS == 5) ? (gg & 1) : 0;
           float t0, t1;
           fma_f2(t0, t1, s[gi][nb][2 * rr], s[gi][nb][2 * rr + 1], scale2, q.cbias[half][nb][rr]);
@@ -341,7 +355,7 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
     for (int rr = 0; rr < 2; ++rr) {   // tree over the groups, then the quad
       float m = gmx[0][rr];
 #pragma unroll
-      for (int gi = 1; gi < GCH; gi += 2) m = gi + 1 < GCH ? max3(m, gmx[gi][rr], gmx[gi + 1][rr]) : fmaxf(m, gmx[gi][rr]);
+      for (int gi = 1; gi < G; gi += 2) m = gi + 1 < G ? max3(m, gmx[gi][rr], gmx[gi + 1][rr]) : fmaxf(m, gmx[gi][rr]);
       m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
       mx[rr] = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
     }
@@ -371,10 +385,9 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
       mref2[rr] = pack_f2(mref[rr], mref[rr]);
     }
     // P = exp2(S - m), row sums (per thread; quad-reduced at the end), O += P V
-    float lsum[GCH][2];
+    float lsum[G][2];
 #pragma unroll
-    for (int gi = 0; gi < GCH; ++gi) {
-      // (a group past the rectangle has S = -inf: P = 0 adds exactly nothing)
+    for (int gi = 0; gi < G; ++gi) {
       float pr[2][4];
 #pragma unroll
       for (int nb = 0; nb < 2; ++nb)
@@ -405,12 +418,14 @@ __device__ __forceinline__ void warp_level(WarpQ<DH, LS>& q, const Params& p, ui
     }
     // pairwise tree over the chunk's groups: ((0+1)+(2+3)) + ((4+5)+(6+7)) ...
 #pragma unroll
-    for (int w = 1; w < GCH; w *= 2)
+    for (int w = 1; w < G; w *= 2)
 #pragma unroll
-      for (int i = 0; i + w < GCH; i += 2 * w)
+      for (int i = 0; i + w < G; i += 2 * w)
         add_f2(lsum[i][0], lsum[i][1], lsum[i][0], lsum[i][1], lsum[i + w][0], lsum[i + w][1]);
     add_f2(q.lrow[0], q.lrow[1], q.lrow[0], q.lrow[1], lsum[0][0], lsum[0][1]);
-  }
+  };
+  for (; g0 + GCH <= q.ngroups; g0 += GCH) chunk(std::integral_constant<int, GCH>{});
+  tail_chunk<GCH - 1>(q.ngroups - g0, chunk);
 }
 
 template <int DH, int LS>
