@@ -570,21 +570,21 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
       return sV32 + (uint32_t)((((q.wr0 + (j >> LS)) * WC + q.wc0 + (j & smask)) * DHP + (mi & 1) * 8) * 2);
     }
   };
-  for (int g0 = 0; g0 < q.ngroups; g0 += GCH) {
-    // Groups past the rectangle (in the last chunk) skip all their work
-    // behind uniform branches; they would only contribute -inf to the max.
-    float s[GCH][4];
+  // Chunks of GCH groups, then one chunk of exactly the groups left, as in
+  // the Q.K^T family.
+  int g0 = 0;
+  auto chunk = [&](auto gsize) {
+    constexpr int G = decltype(gsize)::value;
+    float s[G][4];
 #pragma unroll
-    for (int gi = 0; gi < GCH; ++gi) {
-      if (g0 + gi < q.ngroups) {
-        s[gi][0] = s[gi][1] = s[gi][2] = s[gi][3] = 0.f;
-        const uint32_t ka = k_addr(g0 + gi);
+    for (int gi = 0; gi < G; ++gi) {
+      s[gi][0] = s[gi][1] = s[gi][2] = s[gi][3] = 0.f;
+      const uint32_t ka = k_addr(g0 + gi);
 #pragma unroll
-        for (int kc = 0; kc < KC; ++kc) {
-          uint32_t a0, a1, a2, a3;
-          ldsm_x4(ka + kc * 32, a0, a1, a2, a3);
-          mma_bf16(s[gi], a0, a1, a2, a3, q.qb[kc][0], q.qb[kc][1]);
-        }
+      for (int kc = 0; kc < KC; ++kc) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(ka + kc * 32, a0, a1, a2, a3);
+        mma_bf16(s[gi], a0, a1, a2, a3, q.qb[kc][0], q.qb[kc][1]);
       }
     }
     // mask + scale, per-query chunk max; entries (key i, queries 2 t4 and
@@ -592,21 +592,19 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
     const uint64_t scale2 = pack_f2(p.scale_log2, p.scale_log2);
     float mx[2] = {-INFINITY, -INFINITY};
 #pragma unroll
-    for (int gi = 0; gi < GCH; ++gi) {
+    for (int gi = 0; gi < G; ++gi) {
       const int gg = g0 + gi;
-      if (gg < q.ngroups) {
-        const int half = (LS == 5) ? (gg & 1) : 0;
+      const int half = (LS == 5) ? (gg & 1) : 0;
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int row = (gg * 16 + 8 * i + g) >> LS;
-          float t0, t1;
-          fma_f2(t0, t1, s[gi][2 * i], s[gi][2 * i + 1], scale2, q.cbias2[half][i]);
-          s[gi][2 * i] = ((unsigned)(row - q.rlo[0]) < (unsigned)p.kh) ? t0 : -INFINITY;
-          s[gi][2 * i + 1] = ((unsigned)(row - q.rlo[1]) < (unsigned)p.kh) ? t1 : -INFINITY;
-        }
-        mx[0] = max3(mx[0], s[gi][0], s[gi][2]);
-        mx[1] = max3(mx[1], s[gi][1], s[gi][3]);
+      for (int i = 0; i < 2; ++i) {
+        const int row = (gg * 16 + 8 * i + g) >> LS;
+        float t0, t1;
+        fma_f2(t0, t1, s[gi][2 * i], s[gi][2 * i + 1], scale2, q.cbias2[half][i]);
+        s[gi][2 * i] = ((unsigned)(row - q.rlo[0]) < (unsigned)p.kh) ? t0 : -INFINITY;
+        s[gi][2 * i + 1] = ((unsigned)(row - q.rlo[1]) < (unsigned)p.kh) ? t1 : -INFINITY;
       }
+      mx[0] = max3(mx[0], s[gi][0], s[gi][2]);
+      mx[1] = max3(mx[1], s[gi][1], s[gi][3]);
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -635,33 +633,33 @@ __device__ __forceinline__ void warp_level_t(WarpQT<DH, LS>& q, const Params& p,
     const uint64_t mref2 = pack_f2(q.mrow[0] == -INFINITY ? 0.f : q.mrow[0], q.mrow[1] == -INFINITY ? 0.f : q.mrow[1]);
     float lsum[2] = {0.f, 0.f};
 #pragma unroll
-    for (int gi = 0; gi < GCH; ++gi) {
-      if (g0 + gi < q.ngroups) {
-        float pr[4];
-        float d0, d1;
-        sub_f2(d0, d1, s[gi][0], s[gi][1], mref2);
-        pr[0] = ex2(d0);
-        pr[1] = ex2(d1);
-        sub_f2(d0, d1, s[gi][2], s[gi][3], mref2);
-        pr[2] = ex2(d0);
-        pr[3] = ex2(d1);
-        float e0, e1;
-        add_f2(e0, e1, pr[0], pr[1], pr[2], pr[3]);
-        add_f2(lsum[0], lsum[1], lsum[0], lsum[1], e0, e1);
-        // P^T blocks (keys 0-7 / 8-15 x queries) transposed into the B operand
-        const uint32_t b0 = movmatrix_t(pack_bf16(pr[0], pr[1]));
-        const uint32_t b1 = movmatrix_t(pack_bf16(pr[2], pr[3]));
-        const uint32_t va = v_addr(g0 + gi);
+    for (int gi = 0; gi < G; ++gi) {
+      float pr[4];
+      float d0, d1;
+      sub_f2(d0, d1, s[gi][0], s[gi][1], mref2);
+      pr[0] = ex2(d0);
+      pr[1] = ex2(d1);
+      sub_f2(d0, d1, s[gi][2], s[gi][3], mref2);
+      pr[2] = ex2(d0);
+      pr[3] = ex2(d1);
+      float e0, e1;
+      add_f2(e0, e1, pr[0], pr[1], pr[2], pr[3]);
+      add_f2(lsum[0], lsum[1], lsum[0], lsum[1], e0, e1);
+      // P^T blocks (keys 0-7 / 8-15 x queries) transposed into the B operand
+      const uint32_t b0 = movmatrix_t(pack_bf16(pr[0], pr[1]));
+      const uint32_t b1 = movmatrix_t(pack_bf16(pr[2], pr[3]));
+      const uint32_t va = v_addr(g0 + gi);
 #pragma unroll
-        for (int md = 0; md < MD; ++md) {
-          uint32_t a0, a1, a2, a3;
-          ldsm_x4_t(va + md * 32, a0, a1, a2, a3);
-          mma_bf16(q.o[md], a0, a1, a2, a3, b0, b1);
-        }
+      for (int md = 0; md < MD; ++md) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4_t(va + md * 32, a0, a1, a2, a3);
+        mma_bf16(q.o[md], a0, a1, a2, a3, b0, b1);
       }
     }
     add_f2(q.lrow[0], q.lrow[1], q.lrow[0], q.lrow[1], lsum[0], lsum[1]);
-  }
+  };
+  for (; g0 + GCH <= q.ngroups; g0 += GCH) chunk(std::integral_constant<int, GCH>{});
+  tail_chunk<GCH - 1>(q.ngroups - g0, chunk);
 }
 
 template <int DH, int LS>
