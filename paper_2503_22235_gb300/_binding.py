@@ -185,9 +185,28 @@ def wm_latent_rollout(ctx, latent, lead_hours, stream=None):
     _check(lib().wm_latent_rollout(ctx, _ptr(latent), latent.shape[0], int(lead_hours), _stream(stream)))
 
 
+def _host_latents(ctx, tensors, batch):
+    """Check that each host buffer holds `batch` whole float32 latents of this
+    context, contiguous in host memory: the library trusts the sizes it is given."""
+    per = wm_ctx_sizes(ctx, 1)[0]
+    for t in tensors:
+        if getattr(t, "is_cuda", False):
+            raise ValueError("host buffer expected, got a CUDA tensor")
+        dt = str(getattr(t, "dtype", ""))
+        if dt not in ("torch.float32", "float32"):
+            raise ValueError(f"float32 host buffer expected, got {dt or type(t).__name__}")
+        contiguous = t.is_contiguous() if hasattr(t, "is_contiguous") else t.flags["C_CONTIGUOUS"]
+        if not contiguous:
+            raise ValueError("host buffer must be contiguous")
+        n = t.numel() if hasattr(t, "numel") and callable(t.numel) else t.size
+        if n != batch * per:
+            raise ValueError(f"host buffer holds {n} floats, expected {batch} x {per}")
+
+
 def wm_forecast_host(ctx, host_in, host_out, lead_hours, stream=None):
-    _check(lib().wm_forecast_host(ctx, _ptr(host_in), _ptr(host_out), host_in.shape[0], int(lead_hours),
-                                  _stream(stream)))
+    batch = host_in.shape[0]
+    _host_latents(ctx, [host_in, host_out], batch)
+    _check(lib().wm_forecast_host(ctx, _ptr(host_in), _ptr(host_out), batch, int(lead_hours), _stream(stream)))
 
 
 def wm_forecast_host_many(ctx, host_ins, host_outs, lead_hours, stream=None):
@@ -195,6 +214,7 @@ def wm_forecast_host_many(ctx, host_ins, host_outs, lead_hours, stream=None):
     if len(host_outs) != n:
         raise ValueError("one output per input")
     batch = host_ins[0].shape[0] if n else 1
+    _host_latents(ctx, list(host_ins) + list(host_outs), batch)
     ins = (_vp * max(n, 1))(*[_ptr(t) for t in host_ins])
     outs = (_vp * max(n, 1))(*[_ptr(t) for t in host_outs])
     _check(lib().wm_forecast_host_many(ctx, ins, outs, n, batch, int(lead_hours), _stream(stream)))
@@ -258,15 +278,21 @@ def wm_ctx_reserve(ctx, batch):
 
 # ------------------------------------------------------------------ serving ---
 
+_server_ctx = {}   # server handle -> its context, for the host-buffer size checks
+
+
 def wm_server_start(ctx, hbm_budget_bytes, max_batch) -> int:
     out = _vp()
     _check(lib().wm_server_start(ctx, int(hbm_budget_bytes), int(max_batch), ctypes.byref(out)))
+    _server_ctx[out.value] = ctx
     return out.value
 
 
 def wm_server_submit(srv, host_latent, lead_hours) -> int:
     """host_latent: contiguous float32 host array/tensor of one latent. Raises WmError (WM_ERR_BUSY) when full."""
     rid = ctypes.c_uint64()
+    if srv in _server_ctx:
+        _host_latents(_server_ctx[srv], [host_latent], 1)
     _check(lib().wm_server_submit(srv, _ptr(host_latent), int(lead_hours), ctypes.byref(rid)))
     return rid.value
 
@@ -274,6 +300,8 @@ def wm_server_submit(srv, host_latent, lead_hours) -> int:
 def wm_server_poll(srv, req_id, host_out=None):
     """(done, latency_ms): copies the result into host_out when done."""
     done, lat = _c_int(), ctypes.c_double()
+    if host_out is not None and srv in _server_ctx:
+        _host_latents(_server_ctx[srv], [host_out], 1)
     _check(lib().wm_server_poll(srv, ctypes.c_uint64(req_id), _ptr(host_out), ctypes.byref(done), ctypes.byref(lat)))
     return bool(done.value), lat.value
 
@@ -289,6 +317,7 @@ def wm_server_stats(srv) -> dict:
 
 
 def wm_server_stop(srv):
+    _server_ctx.pop(srv, None)
     _check(lib().wm_server_stop(srv))
 
 

@@ -328,6 +328,15 @@ def test_forecast_stream_from_host_buffers_equals_single_calls():
         wm.wm_forecast_host_many(ctx, [], [], 7)          # nothing to do
         with pytest.raises(wm.WmError):
             wm.wm_forecast_host_many(ctx, xs[:1], outs[:1], -1)
+        # the binding refuses host buffers the library would overrun
+        with pytest.raises(ValueError):
+            wm.wm_forecast_host(ctx, xs[0].double(), outs[0], 7)
+        with pytest.raises(ValueError):
+            wm.wm_forecast_host(ctx, xs[0], outs[0][:1], 7)
+        with pytest.raises(ValueError):
+            wm.wm_forecast_host_many(ctx, [xs[0]], [outs[0].transpose(1, 2)], 7)
+        with pytest.raises(ValueError):
+            wm.wm_forecast_host_many(ctx, [xs[0].cuda()], [outs[0]], 7)
     finally:
         wm.wm_destroy(ctx)
 
