@@ -388,10 +388,11 @@ def run_ours(args):
         hin = torch.from_numpy(x0).pin_memory()
         houts = [torch.empty_like(hin).pin_memory() for _ in range(2)]
         wm.wm_forecast_host_many(ctx, [hin] * max(3, args.warmup), [houts[i % 2] for i in range(max(3, args.warmup))], 6)
-        barrier()
-        t0 = time.perf_counter()
-        wm.wm_forecast_host_many(ctx, [hin] * args.steps, [houts[i % 2] for i in range(args.steps)], 6)
-        dt = max_over_ranks(time.perf_counter() - t0, dev)
+        with ClockSampler(local) as eclk:
+            barrier()
+            t0 = time.perf_counter()
+            wm.wm_forecast_host_many(ctx, [hin] * args.steps, [houts[i % 2] for i in range(args.steps)], 6)
+            dt = max_over_ranks(time.perf_counter() - t0, dev)
         for _ in range(max(1, args.warmup)):
             wm.wm_forecast_host(ctx, hin, houts[0], 6)
         barrier()
@@ -402,6 +403,7 @@ def run_ours(args):
         nbytes = hin.numel() * 4
         out["e2e"] = {"value": ws * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                       "d2h_bytes_per_step": nbytes, "call": "wm_forecast_host_many(lead 6 h, K forecasts)",
+                      "clocks": eclk.summary(),
                       "single_call": {"value": ws * args.steps / dt1, "call": "wm_forecast_host(lead 6 h) x K"}}
     # ---------------- 0.25-degree fields -> 14-day forecast -> fields (encoder, rollout, decoder)
     if not args.no_fields and rank == 0:
