@@ -749,10 +749,16 @@ wm_status wm_forecast_host(wm_ctx* ctx, const float* host_in, float* host_out, i
   const size_t floats = (size_t)batch * ctx->N * ctx->cfg.C;
   WM_TRY(ensure_buffer(&ctx->d_io, &ctx->io_cap, floats));
   cudaStream_t s = (cudaStream_t)stream;
-  WM_CUDA(cudaMemcpyAsync(ctx->d_io, host_in, floats * 4, cudaMemcpyHostToDevice, s));
-  WM_TRY(wm_latent_rollout(ctx, ctx->d_io, batch, lead_hours, stream));
-  WM_CUDA(cudaMemcpyAsync(host_out, ctx->d_io, floats * 4, cudaMemcpyDeviceToHost, s));
-  WM_CUDA(cudaStreamSynchronize(s));
+  auto enqueue = [&]() -> wm_status {
+    WM_CUDA(cudaMemcpyAsync(ctx->d_io, host_in, floats * 4, cudaMemcpyHostToDevice, s));
+    WM_TRY(wm_latent_rollout(ctx, ctx->d_io, batch, lead_hours, stream));
+    WM_CUDA(cudaMemcpyAsync(host_out, ctx->d_io, floats * 4, cudaMemcpyDeviceToHost, s));
+    return WM_OK;
+  };
+  const wm_status st = enqueue();
+  const cudaError_t e = cudaStreamSynchronize(s);   // the copies are done with the host buffers
+  if (st != WM_OK) return st;
+  if (e != cudaSuccess) return fail(WM_ERR_CUDA, cudaGetErrorString(e));
   return WM_OK;
 }
 
@@ -789,20 +795,29 @@ wm_status wm_forecast_host_many(wm_ctx* ctx, const float* const* host_in, float*
     WM_CUDA(cudaEventRecord(up[b], ctx->up_stream));
     return WM_OK;
   };
-  WM_TRY(upload(0));
-  for (int i = 0; i < n; ++i) {
-    const int b = i % R;
-    if (i + 1 < n) WM_TRY(upload(i + 1));
-    WM_CUDA(cudaStreamWaitEvent(s, up[b], 0));
-    WM_TRY(wm_latent_rollout(ctx, ctx->d_ring[b], batch, lead_hours, stream));
-    WM_CUDA(cudaEventRecord(comp[b], s));
-    WM_CUDA(cudaStreamWaitEvent(ctx->down_stream, comp[b], 0));
-    WM_CUDA(cudaMemcpyAsync(host_out[i], ctx->d_ring[b], floats * 4, cudaMemcpyDeviceToHost, ctx->down_stream));
-    WM_CUDA(cudaEventRecord(down[b], ctx->down_stream));
-  }
-  WM_CUDA(cudaStreamSynchronize(ctx->down_stream));
-  WM_CUDA(cudaStreamSynchronize(ctx->up_stream));
-  WM_CUDA(cudaStreamSynchronize(s));
+  auto enqueue = [&]() -> wm_status {
+    WM_TRY(upload(0));
+    for (int i = 0; i < n; ++i) {
+      const int b = i % R;
+      if (i + 1 < n) WM_TRY(upload(i + 1));
+      WM_CUDA(cudaStreamWaitEvent(s, up[b], 0));
+      WM_TRY(wm_latent_rollout(ctx, ctx->d_ring[b], batch, lead_hours, stream));
+      WM_CUDA(cudaEventRecord(comp[b], s));
+      WM_CUDA(cudaStreamWaitEvent(ctx->down_stream, comp[b], 0));
+      WM_CUDA(cudaMemcpyAsync(host_out[i], ctx->d_ring[b], floats * 4, cudaMemcpyDeviceToHost, ctx->down_stream));
+      WM_CUDA(cudaEventRecord(down[b], ctx->down_stream));
+    }
+    return WM_OK;
+  };
+  const wm_status st = enqueue();
+  // every copy has finished with the caller's host buffers before returning,
+  // on the error path too
+  const cudaError_t e1 = cudaStreamSynchronize(ctx->down_stream);
+  const cudaError_t e2 = cudaStreamSynchronize(ctx->up_stream);
+  const cudaError_t e3 = cudaStreamSynchronize(s);
+  if (st != WM_OK) return st;
+  for (cudaError_t e : {e1, e2, e3})
+    if (e != cudaSuccess) return fail(WM_ERR_CUDA, cudaGetErrorString(e));
   return WM_OK;
 }
 
