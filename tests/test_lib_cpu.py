@@ -114,3 +114,20 @@ def test_binding_structs_mirror_the_header(name):
     kinds = {"int": ctypes.c_int, "float": ctypes.c_float}
     for (f, t), (_, c) in zip(got, want):
         assert t is kinds[c], (f, t, c)
+
+
+def test_binding_refuses_host_buffers_the_library_would_overrun(monkeypatch):
+    # The host-copy calls trust the sizes they are given; the binding checks
+    # dtype, device, contiguity and element count first (no GPU needed here).
+    import numpy as np
+    import torch
+    from paper_2503_22235_gb300 import _binding as b
+    per = 2 * 3 * 4 * 8
+    monkeypatch.setattr(b, "wm_ctx_sizes", lambda ctx, batch=1: (per * batch, 0))
+    good = torch.zeros(2, 2, 3, 4, 8)
+    b._host_latents(None, [good, good.clone()], 2)
+    b._host_latents(None, [np.zeros((1, 2, 3, 4, 8), np.float32)], 1)
+    for bad, batch in [(good.double(), 2), (good[:1], 2), (good.transpose(2, 3), 2),
+                       (np.zeros((2, 2, 3, 4, 8)), 2), (good, 3)]:
+        with pytest.raises(ValueError):
+            b._host_latents(None, [bad], batch)
