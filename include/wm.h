@@ -128,14 +128,18 @@ wm_status wm_processor_step(wm_ctx* ctx, float* latent, int batch, int which, vo
  * T = 0 is a no-op; T < 0 gives WM_ERR_INVALID_ARG. */
 wm_status wm_latent_rollout(wm_ctx* ctx, float* latent, int batch, int lead_hours, void* stream);
 
-/* End-to-end forecast from HOST memory: copies host_in (float32 [batch,D,H,W,C])
- * to a library-owned device latent, runs wm_latent_rollout, copies the result
- * to host_out (may equal host_in) and synchronises the stream before returning.
- * Pinned host buffers make the copies asynchronous DMA. */
+/* End-to-end forecast from HOST memory (the problem statement of Section 2.1:
+ * one state in, the state lead_hours later out): copies host_in (float32
+ * [batch,D,H,W,C]) to a library-owned device latent, runs wm_latent_rollout,
+ * copies the result to host_out (may equal host_in) and synchronises the
+ * stream before returning, on the error path too. Pinned host buffers make
+ * the copies asynchronous DMA. The caller guarantees the buffer sizes.
+ * Errors: WM_ERR_INVALID_ARG (NULL, batch < 1, T < 0), WM_ERR_OOM, WM_ERR_CUDA. */
 wm_status wm_forecast_host(wm_ctx* ctx, const float* host_in, float* host_out, int batch,
                            int lead_hours, void* stream);
 
-/* A stream of n end-to-end forecasts from HOST memory: forecast i copies
+/* A stream of n end-to-end forecasts from HOST memory (Section 2.1, as
+ * wm_forecast_host): forecast i copies
  * host_in[i] to the device, rolls it out to lead_hours and copies the result
  * to host_out[i] (float32 [batch,D,H,W,C] each). A ring of three
  * library-owned device latents lets the upload of forecast i + 1 and the
@@ -144,7 +148,8 @@ wm_status wm_forecast_host(wm_ctx* ctx, const float* host_in, float* host_out, i
  * once every result is in host memory. host_in[i] may repeat; host_out[i]
  * must not alias another forecast's input or output that is still in flight
  * (the same pointer for every output is fine: downloads are serialised).
- * Pinned host buffers make the copies asynchronous DMA. */
+ * Pinned host buffers make the copies asynchronous DMA. n = 0 is a no-op.
+ * Errors as wm_forecast_host; every copy has finished before it returns. */
 wm_status wm_forecast_host_many(wm_ctx* ctx, const float* const* host_in, float* const* host_out, int n, int batch,
                                 int lead_hours, void* stream);
 
