@@ -79,8 +79,10 @@ typedef struct wm_server wm_server;
 
 /* ----------------------------------------------------------- context ---- */
 
-/* Create a context on the current CUDA device and upload the weights.
- * weights_path: weight file = 8-byte magic "WM3WGT1\0", int32 C, blocks_p6,
+/* Create a context on the current CUDA device and upload the weights of the
+ * six-hour and one-hour processors (Section 2.1, Appendix A.2; the paper has 10
+ * blocks per processor, here blocks_p6 and blocks_p1). The library copies the
+ * weights; the caller keeps the file. weights_path: weight file = 8-byte magic "WM3WGT1\0", int32 C, blocks_p6,
  * blocks_p1, 0 (little endian), then float32 tensors: for the six-hour blocks
  * then the one-hour blocks, per block in this order
  *   ln1_g[C] ln1_b[C] wqkv[3C][C] bqkv[3C] wo[C][C] bo[C] ln2_g[C] ln2_b[C]
@@ -93,29 +95,38 @@ wm_status wm_create(const wm_config* cfg, const char* weights_path, wm_ctx** out
  * must equal (blocks_p6 + blocks_p1) * (12*C*C + 13*C). The buffer is copied. */
 wm_status wm_create_from_host(const wm_config* cfg, const float* weights, size_t n_floats, wm_ctx** out);
 
-/* Synchronises the device, frees everything the context owns. NULL is a no-op. */
+/* Synchronises the device, frees everything the context owns. NULL is a no-op.
+ * (Library service; no counterpart in the paper.) */
 wm_status wm_destroy(wm_ctx* ctx);
 
-/* Switch the precision used by later compute calls (weights for all precisions are resident). */
+/* Switch the precision used by later compute calls (weights for all precisions
+ * are resident). The paper trains in half precision (Appendix A.3); the
+ * precisions here are this library's. WM_ERR_INVALID_ARG for an unknown value. */
 wm_status wm_set_precision(wm_ctx* ctx, int precision);
 
 /* Sizes for `batch` latents at the context's current precision: floats per
- * latent (D*H*W*C) and bytes of the workspace the compute calls need. */
+ * latent (D*H*W*C) and bytes of the workspace the compute calls need (HOST
+ * outputs, both required; WM_ERR_INVALID_ARG otherwise). (Library service.) */
 wm_status wm_ctx_sizes(wm_ctx* ctx, int batch, size_t* latent_floats, size_t* workspace_bytes);
 
 /* Allocate the workspace for `batch` latents now (at the current precision),
- * so that later calls, and graph captures, allocate nothing. */
+ * so that later calls, and graph captures, allocate nothing. WM_ERR_OOM if
+ * it does not fit. (Library service.) */
 wm_status wm_ctx_reserve(wm_ctx* ctx, int batch);
 
 /* The tile plans the autotuner chose so far in this process (text, one line
- * per shape, NUL-terminated, truncated to len - 1 bytes). The attention
- * kernel's plans are timed when a context's BF16 workspace is allocated. */
+ * per shape, NUL-terminated, truncated to len - 1 bytes; buf is HOST). The
+ * attention kernel's plans are timed when a context's BF16 workspace is
+ * allocated. (Library service.) */
 wm_status wm_autotune_report(char* buf, size_t len);
 
 /* ----------------------------------------------------------- compute ---- */
 
-/* One block (index `block` of processor `which`) applied in place to
- * latent (device, float32 [batch, D, H, W, C]). */
+/* One neighborhood-attention transformer block (Section 2.1, Appendix A.2;
+ * the formula at the top of this file), index `block` of processor `which`,
+ * applied in place to latent (device, float32 [batch, D, H, W, C]).
+ * WM_ERR_INVALID_ARG for which/block out of range, a NULL or misaligned latent
+ * or batch < 1; WM_ERR_OOM, WM_ERR_CUDA, WM_ERR_TIMEOUT. */
 wm_status wm_block_forward(wm_ctx* ctx, float* latent, int batch, int which, int block, void* stream);
 
 /* One processor call (all of its blocks, in order) in place: a six-hour step
@@ -153,7 +164,8 @@ wm_status wm_forecast_host(wm_ctx* ctx, const float* host_in, float* host_out, i
 wm_status wm_forecast_host_many(wm_ctx* ctx, const float* const* host_in, float* const* host_out, int n, int batch,
                                 int lead_hours, void* stream);
 
-/* Batched uneven rollouts: latents[i] (device, one float32 latent each) is
+/* Batched uneven rollouts (the latent rollout of Section 2.1 for each request;
+ * the batching is this library's): latents[i] (device, one float32 latent each) is
  * advanced in place to lead_hours[i]. All requests advance together one
  * processor step per tick; the requests due for the same processor in a tick
  * run as one batched step (row-independent kernels, so each result equals its
@@ -173,7 +185,8 @@ wm_status wm_rollout_hourly(wm_ctx* ctx, const float* x, int max_lead, float* ou
 /* Greedy schedule of Section 2.1 (pure host): n6 = T div 6, n1 = T mod 6. */
 wm_status wm_schedule(int lead_hours, int* n6, int* n1);
 
-/* FP64 error reduction on the GPU: out[0] = sum (a-b)^2, out[1] = sum b^2 over n
+/* FP64 error reduction on the GPU (the relative-L2 metric of the parity
+ * tolerances; library service): out[0] = sum (a-b)^2, out[1] = sum b^2 over n
  * float32 elements (device pointers); out is HOST memory of 2 doubles, filled
  * after an internal synchronisation of `stream`. rel-L2 = sqrt(out[0]/out[1]). */
 wm_status wm_rel_l2(const float* a, const float* b, size_t n, double* out, void* stream);
@@ -199,7 +212,7 @@ wm_status wm_rel_l2(const float* a, const float* b, size_t n, double* out, void*
 wm_status wm_rel_l2_noalloc(const float* a, const float* b, size_t n, double* out, void* stream);
 
 /* Reads (and clears) the device status word that bounded device-side waits
- * write; synchronises the device. WM_OK or WM_ERR_TIMEOUT. */
+ * write; synchronises the device. WM_OK or WM_ERR_TIMEOUT. (Library service.) */
 wm_status wm_device_status(void);
 
 /* Self-test of the bounded-wait path: launches one kernel that waits on a
@@ -207,7 +220,7 @@ wm_status wm_device_status(void);
  * returns. Expect WM_ERR_TIMEOUT, after which the context must stay usable. */
 wm_status wm_selftest_wait_timeout(int timeout_us);
 
-/* Per-launch kernel timing. Between wm_timing_begin and wm_timing_end every
+/* Per-launch kernel timing (library service). Between wm_timing_begin and wm_timing_end every
  * hot-path kernel launched by compute calls on this context is bracketed by a
  * CUDA event pair on its stream (rollouts then run eagerly instead of from a
  * graph). wm_timing_end synchronises the device and returns, per kernel kind
@@ -219,11 +232,15 @@ wm_status wm_timing_begin(wm_ctx* ctx, int max_launches);
 wm_status wm_timing_end(wm_ctx* ctx, double* ms_by_kind /* [WM_KERNEL_KINDS] */,
                         int* launches_by_kind /* [WM_KERNEL_KINDS] */);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none); the string is
+ * owned by the library and valid until the thread's next failing call. */
 const char* wm_last_error(void);
 
 /* ----------------------------------------------------------- serving ---- */
 /* Forecast server with continuous batching (one worker thread per server).
+ * It serves the operational use of Section 3.1: forecasts of one model to many
+ * lead times. The paper describes no server; the policy below is this
+ * library's.
  * Requests are a HOST latent (float32 [1, D, H, W, C], copied at submit) and a
  * lead time. They are admitted into device-resident latent slots in arrival
  * order while slots are free; the number of slots is set by the HBM budget:
@@ -257,7 +274,12 @@ wm_status wm_server_stop(wm_server* srv);
 
 /* ---------------------------------------------------------- op level ---- */
 /* The individual hot-path kernels on caller device buffers, for parity tests
- * of each step against the oracle. All synchronous-free; `stream` as above. */
+ * of each step against the oracle. Each is one step of the block at the top of
+ * this file (Section 2.1, Appendix A.2): LayerNorm (LN1, LN2), the linear
+ * layers (QKV, output projection, FC1, FC2) with their GELU and residual
+ * epilogues, and the neighborhood attention. All are asynchronous on
+ * `stream`; WM_ERR_INVALID_ARG for bad sizes, NULL or misaligned pointers,
+ * WM_ERR_CUDA for a failed launch. */
 
 /* LayerNorm over C of M float32 rows of x; out is float32 (out_bf16 = 0) or
  * bfloat16 (out_bf16 = 1) [M, C]. */
@@ -348,6 +370,7 @@ typedef struct {
  * two of them concurrently (different streams or threads); use one codec per
  * concurrent caller. */
 wm_status wm_codec_create(const wm_codec_config* cfg, const float* host_weights, size_t n_floats, wm_codec** out);
+/* Synchronises the device and frees the codec (NULL is a no-op). */
 wm_status wm_codec_destroy(wm_codec* codec);
 /* Physical fields -> latent (all device pointers; asynchronous on stream). */
 wm_status wm_encode(wm_codec* codec, const float* atm, const float* sfc, const float* consts, float* latent,
@@ -360,7 +383,8 @@ wm_status wm_decode(wm_codec* codec, const float* latent, float* atm_out, float*
 wm_status wm_forecast_fields(wm_ctx* ctx, wm_codec* codec, const float* atm, const float* sfc, const float* consts,
                              int lead_hours, float* latent_ws, float* atm_out, float* sfc_out, void* stream);
 
-/* 3D neighborhood attention on qkv [batch*D*H*W, 3C] (q | k | v, each head-major)
+/* 3D neighborhood attention (Section 2.1; window, bump edges and circular
+ * longitude padding of Appendix A.2) on qkv [batch*D*H*W, 3C] (q | k | v, each head-major)
  * -> out [batch*D*H*W, C]. precision FP32: float32 in/out; BF16: bfloat16 in/out
  * (BF16 requires dh = C/heads in {16, 32, 48, 64}).
  * variant (BF16 only; FP32 takes 0): WM_NA_AUTO uses the plan tuned for this
