@@ -26,6 +26,10 @@
  *   - Latents at the boundary are always float32 [batch, D, H, W, C],
  *     contiguous, whatever the internal precision.
  *   - The library owns weights, workspace, CUDA graphs and server slots.
+ *   - Concurrency: a context's compute calls share its workspace. Host calls
+ *     from several threads are serialised by the context, but their GPU work
+ *     must not overlap: issue one context's calls on one stream (or order
+ *     the streams), or use one context per concurrent stream.
  */
 #ifndef WM_H
 #define WM_H
@@ -252,6 +256,9 @@ const char* wm_last_error(void);
  * arrive meanwhile join at the next tick. A finished request keeps its result
  * in its slot until wm_server_poll collects it (which frees the slot).
  * Latency = submit call -> the host sees the tick that finished the request. */
+/* While the server runs, ctx belongs to it (its worker issues the context's
+ * compute calls on the server's own stream): use another context for other
+ * work until wm_server_stop. */
 wm_status wm_server_start(wm_ctx* ctx, size_t hbm_budget_bytes, int max_batch, wm_server** out);
 
 /* Queue a request; WM_ERR_BUSY when the pending queue is full, WM_ERR_INVALID_ARG for T < 0. */
