@@ -131,3 +131,32 @@ def test_binding_refuses_host_buffers_the_library_would_overrun(monkeypatch):
                        (np.zeros((2, 2, 3, 4, 8)), 2), (good, 3)]:
         with pytest.raises(ValueError):
             b._host_latents(None, [bad], batch)
+
+
+def test_header_is_plain_c_and_a_c_program_links_against_the_library():
+    # The boundary is a C ABI: wm.h must compile as strict C99 and a C program
+    # must link against libwm.so and call it (wm_schedule is host-only).
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.join(root, "paper_2503_22235_gb300")
+    if not os.path.exists(os.path.join(libdir, "libwm.so")):
+        pytest.skip("libwm.so not built")
+    work = os.path.join(root, "_build", "c_abi_check")
+    os.makedirs(work, exist_ok=True)
+    src = os.path.join(work, "main.c")
+    with open(src, "w") as f:
+        f.write('#include <stdio.h>\n#include "wm.h"\n'
+                "int main(void) {\n"
+                "  int n6 = -1, n1 = -1;\n"
+                "  if (wm_schedule(337, &n6, &n1) != WM_OK || n6 != 56 || n1 != 1) return 1;\n"
+                "  if (wm_schedule(-1, &n6, &n1) != WM_ERR_INVALID_ARG || wm_last_error()[0] == 0) return 2;\n"
+                "  return 0;\n}\n")
+    exe = os.path.join(work, "main")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(root, "include"),
+                    src, "-L", libdir, "-lwm", "-Wl,-rpath," + libdir, "-o", exe], check=True)
+    assert subprocess.run([exe]).returncode == 0
