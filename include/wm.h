@@ -177,7 +177,7 @@ wm_status wm_forecast_host_many(wm_ctx* ctx, const float* const* host_in, float*
 wm_status wm_rollout_batch(wm_ctx* ctx, float* const* latents, const int* lead_hours, int n, void* stream);
 
 /* Every hourly lead time 0..max_lead from one initial state (the hourly
- * forecasts of Section 3.1): out[t] (device, max_lead + 1 contiguous float32
+ * forecasts of Section 4.1, Forecast Accessibility): out[t] (device, max_lead + 1 contiguous float32
  * latents) = the rollout of x (device, one latent) to t hours. By the greedy
  * schedule (Section 2.1) lead 6k + r is r one-hour steps after the k-th
  * six-hour anchor, so the anchors form one chain of six-hour steps and the
@@ -205,15 +205,23 @@ wm_status wm_rel_l2(const float* a, const float* b, size_t n, double* out, void*
  * device and stalls every other stream).
  *   - n <= 268,435,456 elements (4096 partial sums of 65,536 elements each);
  *     larger n gives WM_ERR_INVALID_ARG and launches nothing.
- *   - The first call on a device looks up the scratch array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture.
+ *   - Every call looks up the scratch array's device address on the current
+ *     device (cudaGetSymbolAddress, which allocates nothing); the first call
+ *     on a device also loads the library's device code there, so make it
+ *     before any stream capture. n = 0 writes out = {0, 0} and launches
+ *     nothing.
  *   - All calls share the one scratch array; calls whose kernels overlap on
  *     the GPU (e.g. from two streams at once) race and may return wrong sums.
  *     Every partial is rewritten on each call, so nothing needs clearing.
  *   - The sums are deterministic (fixed summation order), so they can differ
  *     from wm_rel_l2's atomically accumulated sums in the last bits. */
 wm_status wm_rel_l2_noalloc(const float* a, const float* b, size_t n, double* out, void* stream);
+
+/* NaN / infinity scan of the error check (library service; the paper has no
+ * counterpart): *count (HOST) = the number of non-finite elements of x
+ * (device, n float32), after an internal synchronisation of `stream`.
+ * Allocates an 8-byte device counter per call. */
+wm_status wm_count_nonfinite(const float* x, size_t n, unsigned long long* count, void* stream);
 
 /* Reads (and clears) the device status word that bounded device-side waits
  * write; synchronises the device. WM_OK or WM_ERR_TIMEOUT. (Library service.) */
@@ -242,7 +250,7 @@ const char* wm_last_error(void);
 
 /* ----------------------------------------------------------- serving ---- */
 /* Forecast server with continuous batching (one worker thread per server).
- * It serves the operational use of Section 3.1: forecasts of one model to many
+ * It serves the operational use of Section 4.1 (Forecast Accessibility): forecasts of one model to many
  * lead times. The paper describes no server; the policy below is this
  * library's.
  * Requests are a HOST latent (float32 [1, D, H, W, C], copied at submit) and a
@@ -267,12 +275,17 @@ wm_status wm_server_submit(wm_server* srv, const float* host_latent, int lead_ho
 /* *done = 1 once the request has finished: its result is copied to host_out
  * (HOST, may be NULL to discard), latency_ms (may be NULL) is set, and the
  * request and its slot are released. *done = 0 while it is queued or running.
- * WM_ERR_NOT_FOUND for an unknown or already collected id. */
+ * WM_ERR_NOT_FOUND for an unknown or already collected id; a poll that races
+ * another poll of the same finished id gets WM_ERR_NOT_FOUND while the other
+ * one copies the result out (each result is collected exactly once). If the
+ * copy fails (WM_ERR_CUDA) the result stays collectable. */
 wm_status wm_server_poll(wm_server* srv, uint64_t req_id, float* host_out, int* done, double* latency_ms);
 
-/* out[9] (HOST): completed requests, p50 latency ms, p99 latency ms, mean
+/* out[11] (HOST): completed requests, p50 latency ms, p99 latency ms, mean
  * latency ms, forecasts/s (completed / (last completion - first arrival)),
- * most requests resident at once, ticks, batched steps launched, slots. */
+ * most requests resident at once, ticks, batched steps launched, slots, most
+ * requests advanced by one batched step, batched steps that advanced two or
+ * more requests together. */
 wm_status wm_server_stats(wm_server* srv, double* out);
 
 /* Stops the worker after its current tick and frees the slots; pending and

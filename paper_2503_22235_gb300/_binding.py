@@ -60,6 +60,7 @@ _SIGS = {
     "wm_rollout_hourly": (_c_int, [_vp, _vp, _c_int, _vp, _c_int, _vp]),
     "wm_rel_l2": (_c_int, [_vp, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp]),
     "wm_rel_l2_noalloc": (_c_int, [_vp, _vp, _sz, ctypes.POINTER(ctypes.c_double), _vp]),
+    "wm_count_nonfinite": (_c_int, [_vp, _sz, ctypes.POINTER(ctypes.c_ulonglong), _vp]),
     "wm_device_status": (_c_int, []),
     "wm_selftest_wait_timeout": (_c_int, [_c_int]),
     "wm_last_error": (ctypes.c_char_p, []),
@@ -251,6 +252,13 @@ def wm_rel_l2_noalloc(a, b, stream=None) -> float:
     return (out[0] / out[1]) ** 0.5 if out[1] > 0 else float(out[0] > 0)
 
 
+def wm_count_nonfinite(x, stream=None) -> int:
+    """Number of NaN or infinite elements of the float32 device tensor x."""
+    out = ctypes.c_ulonglong()
+    _check(lib().wm_count_nonfinite(_ptr(x), x.numel(), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
 def wm_device_status() -> None:
     _check(lib().wm_device_status())
 
@@ -307,7 +315,7 @@ def wm_server_poll(srv, req_id, host_out=None):
 
 
 SERVER_STATS = ("completed", "p50_ms", "p99_ms", "mean_ms", "forecasts_per_s", "max_active", "ticks",
-                "batched_steps", "slots")
+                "batched_steps", "slots", "max_step_batch", "multi_request_steps")
 
 
 def wm_server_stats(srv) -> dict:

@@ -8,7 +8,9 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -39,17 +41,37 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "wm.h"), __file__]
 
 
+STAMP = LIB + ".sha256"
+
+
+def _source_hash() -> str:
+    """sha256 over every input of the build (sources, headers, this script,
+    the compiler flags) and the host architecture, so a library built from
+    other sources, or on another machine, is never taken as current."""
+    h = hashlib.sha256()
+    h.update(platform.machine().encode())
+    h.update(" ".join(NVCC_FLAGS).encode())
+    for p in sorted(_deps()):
+        h.update(os.path.relpath(p, ROOT).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    """True when libwm.so exists and was linked from exactly the current sources."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(p) <= t for p in _deps())
+    with open(STAMP) as f:
+        return f.read().strip() == _source_hash()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libwm.so; returns its path. Rebuilds only when a source is newer."""
+    """Compile and link libwm.so; returns its path. Rebuilds unless the stamp
+    beside the library records the hash of the current sources."""
     if not force and up_to_date():
         return LIB
+    digest = _source_hash()
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     srcs = _sources()
@@ -72,11 +94,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         msg = "\n".join(f"--- {os.path.basename(s)}\n{out}" for s, out in errors)
         raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)
+    with open(STAMP + ".tmp", "w") as f:
+        f.write(digest + "\n")
+    os.replace(STAMP + ".tmp", STAMP)
     return LIB
 
 

@@ -240,11 +240,15 @@ int pick_bn(long M, int N) {
 }
 
 // ---- optional per-launch timing: an event pair around each hot-path kernel
+const char* const kKernelNames[WM_KERNEL_KINDS] = {"ln1", "qkv", "attention", "proj", "ln2", "fc1", "fc2"};
+
+// Also an NVTX range named for the kernel kind.
 struct TimedLaunch {
   wm_ctx* ctx;
   cudaStream_t s;
   int idx = -1;
-  TimedLaunch(wm_ctx* c, int kind, cudaStream_t st) : ctx(c), s(st) {
+  wm::NvtxRange range;
+  TimedLaunch(wm_ctx* c, int kind, cudaStream_t st) : ctx(c), s(st), range(kKernelNames[kind]) {
     if (!ctx->timing) return;
     const size_t i = ctx->ev_marks.size() * 2;
     if (i + 2 > ctx->ev_pool.size()) return;
@@ -258,6 +262,9 @@ struct TimedLaunch {
 };
 
 wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool first, cudaStream_t s) {
+  char range_name[32];
+  std::snprintf(range_name, sizeof range_name, "%s block %d", which == WM_P6 ? "P6" : "P1", b);
+  wm::NvtxRange range(range_name);
   const wm_config& c = ctx->cfg;
   const BlockW& w = ctx->blk[which][b];
   const long M = (long)batch * ctx->N;
@@ -364,6 +371,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
 }
 
 wm_status processor_step(wm_ctx* ctx, float* x, int batch, int which, cudaStream_t s) {
+  wm::NvtxRange range(which == WM_P6 ? "six-hour step" : "one-hour step");
   const int L = which == WM_P6 ? ctx->cfg.blocks_p6 : ctx->cfg.blocks_p1;
   for (int b = 0; b < L; ++b) WM_TRY(block_forward(ctx, x, batch, which, b, b == 0, s));
   return WM_OK;
@@ -971,12 +979,34 @@ wm_status wm_rel_l2(const float* a, const float* b, size_t n, double* out, void*
   cudaStream_t s = (cudaStream_t)stream;
   double* acc = nullptr;
   WM_CUDA(cudaMalloc(&acc, 2 * sizeof(double)));
-  cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
-  wm_status st = wm::launch_sqdiff(a, b, n, acc, s);
+  wm_status st = WM_OK;
+  const cudaError_t ez = cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
+  if (ez != cudaSuccess) st = wm::cuda_fail(ez, "wm_rel_l2 accumulator clear");
+  if (st == WM_OK) st = wm::launch_sqdiff(a, b, n, acc, s);
   if (st == WM_OK) {
     cudaError_t e = cudaMemcpyAsync(out, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = wm::cuda_fail(e, "wm_rel_l2 readback");
+  }
+  cudaFree(acc);
+  return st;
+}
+
+wm_status wm_count_nonfinite(const float* x, size_t n, unsigned long long* count, void* stream) {
+  if (!x || !count) return fail(WM_ERR_INVALID_ARG, "NULL argument");
+  *count = 0;
+  if (n == 0) return WM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* acc = nullptr;
+  WM_CUDA(cudaMalloc(&acc, sizeof(unsigned long long)));
+  wm_status st = WM_OK;
+  const cudaError_t ez = cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s);
+  if (ez != cudaSuccess) st = wm::cuda_fail(ez, "wm_count_nonfinite counter clear");
+  if (st == WM_OK) st = wm::launch_count_nonfinite(x, n, acc, s);
+  if (st == WM_OK) {
+    cudaError_t e = cudaMemcpyAsync(count, acc, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = wm::cuda_fail(e, "wm_count_nonfinite readback");
   }
   cudaFree(acc);
   return st;

@@ -147,6 +147,24 @@ wm_status launch_sqdiff(const float* a, const float* b, size_t n, double* acc2, 
   return WM_OK;
 }
 
+// NaN / infinity scan: *count += the non-finite elements of x.
+__global__ void count_nonfinite_kernel(const float* __restrict__ x, size_t n, unsigned long long* __restrict__ count) {
+  unsigned int c = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    c += isfinite(x[i]) ? 0u : 1u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
+wm_status launch_count_nonfinite(const float* x, size_t n, unsigned long long* count, cudaStream_t s) {
+  if (!n) return WM_OK;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 4);
+  count_nonfinite_kernel<<<blocks, 256, 0, s>>>(x, n, count);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
 // ------------------------------------------------- bounded-wait self test ----
 // Waits for *flag to become non-zero -- nothing ever sets it -- for at most
 // limit_ns, then records WM_ERR_TIMEOUT in the status word and returns.

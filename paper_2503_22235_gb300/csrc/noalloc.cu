@@ -12,8 +12,6 @@
 // The reduction is also deterministic: block i sums elements
 // [i * kChunk, (i + 1) * kChunk) in a fixed order into partial i, and one
 // block then adds the partials in a fixed order.
-#include <mutex>
-
 #include "wm_internal.cuh"
 
 namespace {
@@ -82,23 +80,15 @@ __global__ void __launch_bounds__(kThreads) noalloc_finish_kernel(double* __rest
   }
 }
 
-std::mutex g_addr_mu;
-double* g_addr[64] = {};
-
 // Device address of the scratch array on the current device. Host code only
-// sees a stand-in for the array, so the address is looked up once per device.
+// sees a stand-in for the array, so the address is looked up on every call:
+// the lookup allocates nothing and costs no launch, and a cached address would
+// go stale if the module were reloaded (for example after cudaDeviceReset).
 wm_status scratch_address(double** out) {
-  int dev = 0;
-  WM_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return wm::fail(WM_ERR_INVALID_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lk(g_addr_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return wm::cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return wm::cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+  *out = static_cast<double*>(p);
   return WM_OK;
 }
 

@@ -27,7 +27,9 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 
-enum ReqState { PENDING = 0, ACTIVE = 1, DONE = 2 };
+// COLLECTING: a poller has taken the finished result and is copying it out;
+// every other poll of that id already sees it as collected.
+enum ReqState { PENDING = 0, ACTIVE = 1, DONE = 2, COLLECTING = 3 };
 
 struct Req {
   std::vector<float> input;  // host copy of the initial latent until admission
@@ -64,7 +66,9 @@ struct wm_server {
   clk::time_point t_first_arrival, t_last_done;
   bool any_arrival = false;
   long ticks = 0, batched_steps = 0;
+  long multi_request_steps = 0;   // batched steps that advanced two or more requests together
   int max_active = 0;
+  int max_step_batch = 0;         // most requests advanced by one batched step
 };
 
 namespace {
@@ -78,6 +82,11 @@ wm_status run_tick(wm_server* s, const std::vector<uint64_t>& ids, const std::ve
       if (which[i] == w) due.push_back(slots[i]);
     for (size_t b0 = 0; b0 < due.size(); b0 += s->max_batch) {
       const int g = (int)std::min<size_t>(s->max_batch, due.size() - b0);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->max_step_batch = std::max(s->max_step_batch, g);
+        if (g >= 2) ++s->multi_request_steps;
+      }
       if (g == 1) {
         wm_status st = wm_processor_step(s->ctx, s->slab + (size_t)due[b0] * lat, 1, w, s->stream);
         if (st != WM_OK) return st;
@@ -255,23 +264,33 @@ wm_status wm_server_poll(wm_server* s, uint64_t req_id, float* host_out, int* do
   if (!s || !done) return wm::fail(WM_ERR_INVALID_ARG, "bad poll arguments");
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->reqs.find(req_id);
-  if (it == s->reqs.end()) return wm::fail(WM_ERR_NOT_FOUND, "unknown request id");
+  if (it == s->reqs.end() || it->second.state == COLLECTING)
+    return wm::fail(WM_ERR_NOT_FOUND, "unknown or already collected request id");
   *done = 0;
   if (it->second.state != DONE) {
     if (s->worker_error != WM_OK) return wm::fail(s->worker_error, "server stopped: " + s->worker_msg);
     return WM_OK;
   }
-  Req r = it->second;
-  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r.t_done - r.t_arrive).count();
+  // Claim the result under the lock: a concurrent poll of the same id now
+  // gets WM_ERR_NOT_FOUND, so the slot is copied out and released once.
+  it->second.state = COLLECTING;
+  const int slot = it->second.slot;
+  const double lat_ms = std::chrono::duration<double, std::milli>(it->second.t_done - it->second.t_arrive).count();
   if (host_out) {
     lk.unlock();
-    cudaError_t e = cudaMemcpyAsync(host_out, s->slab + (size_t)r.slot * s->latent_floats, s->latent_floats * 4,
+    cudaError_t e = cudaMemcpyAsync(host_out, s->slab + (size_t)slot * s->latent_floats, s->latent_floats * 4,
                                     cudaMemcpyDeviceToHost, s->io_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->io_stream);
-    if (e != cudaSuccess) return wm::cuda_fail(e, "server result copy");
     lk.lock();
+    if (e != cudaSuccess) {
+      // the result is still in its slot: leave it collectable
+      auto again = s->reqs.find(req_id);
+      if (again != s->reqs.end()) again->second.state = DONE;
+      return wm::cuda_fail(e, "server result copy");
+    }
   }
-  s->free_slots.push_back(r.slot);
+  if (latency_ms) *latency_ms = lat_ms;
+  s->free_slots.push_back(slot);
   s->reqs.erase(req_id);
   *done = 1;
   s->cv.notify_all();
@@ -304,6 +323,8 @@ wm_status wm_server_stats(wm_server* s, double* out) {
   out[6] = (double)s->ticks;
   out[7] = (double)s->batched_steps;
   out[8] = (double)s->nslots;
+  out[9] = (double)s->max_step_batch;
+  out[10] = (double)s->multi_request_steps;
   return WM_OK;
 }
 

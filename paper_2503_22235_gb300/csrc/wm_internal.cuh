@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -27,6 +28,16 @@ wm_status cuda_fail(cudaError_t e, const char* what);
     cudaError_t e_ = (call);                               \
     if (e_ != cudaSuccess) return wm::cuda_fail(e_, #call); \
   } while (0)
+
+// NVTX range for the lifetime of a scope (host side): profilers show one range
+// per processor step, block and kernel launch. Without a profiler attached the
+// push and pop are no-ops.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device status word written by bounded device-side waits (one per device).
 int* device_status_word();
@@ -219,6 +230,8 @@ wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, 
 wm_status launch_f32_to_bf16(const float* in, __nv_bfloat16* out, size_t n, cudaStream_t s);
 wm_status launch_f32_to_e4m3(const float* in, uint8_t* out, size_t n, float inv_scale, cudaStream_t s);
 wm_status launch_sqdiff(const float* a, const float* b, size_t n, double* acc2, cudaStream_t s);
+// *count += number of NaN or infinite elements of x[0, n).
+wm_status launch_count_nonfinite(const float* x, size_t n, unsigned long long* count, cudaStream_t s);
 wm_status launch_wait_selftest(int timeout_us, cudaStream_t s);
 
 }  // namespace wm

@@ -45,7 +45,9 @@ def _alone(ctx, x, lead):
 
 
 def test_server_results_equal_alone_and_in_the_mix(ctx):
-    leads = [13, 1, 0, 7, 6, 24, 2, 19, 12, 5]
+    # the first two are long six-hour chains submitted back to back, so they
+    # share batched six-hour steps whatever the worker's timing
+    leads = [48, 42, 0, 7, 6, 24, 2, 19, 12, 5]
     xs = [synth.latent(SHAPE, 1, seed=100 + i) for i in range(len(leads))]
     srv = wm.wm_server_start(ctx, _budget(ctx, slots=4, max_batch=3), max_batch=3)
     try:
@@ -69,7 +71,11 @@ def test_server_results_equal_alone_and_in_the_mix(ctx):
         assert len(outs) == len(ids)
         st = wm.wm_server_stats(srv)
         assert st["completed"] == len(ids)
-        assert st["slots"] == 4 and st["max_active"] <= 4
+        assert st["slots"] == 4 and 2 <= st["max_active"] <= 4
+        # the requests really were mixed: some batched steps advanced two or
+        # more requests at once
+        assert st["max_step_batch"] >= 2 and st["multi_request_steps"] >= 1, st
+        assert st["max_step_batch"] <= 3
         assert st["p50_ms"] <= st["p99_ms"]
     finally:
         wm.wm_server_stop(srv)
@@ -105,5 +111,47 @@ def test_server_budget_and_arguments(ctx):
             time.sleep(0.001)
         assert len(got) == 3
         assert wm.wm_server_stats(srv)["max_active"] == 1
+    finally:
+        wm.wm_server_stop(srv)
+
+
+def test_concurrent_polls_collect_each_result_once(ctx):
+    """Two threads poll every finished request at the same time: exactly one
+    of them receives the result, the other sees the id as collected, and no
+    slot is handed out twice (later requests in a full server still match
+    their single-request rollouts)."""
+    import threading
+    srv = wm.wm_server_start(ctx, _budget(ctx, slots=3, max_batch=2), max_batch=2)
+    try:
+        xs = [synth.latent(SHAPE, 1, seed=200 + i) for i in range(12)]
+        for round_ in range(4):
+            batch = xs[3 * round_:3 * round_ + 3]
+            ids = [wm.wm_server_submit(srv, x, 7) for x in batch]
+            got = {rid: [] for rid in ids}
+            lock = threading.Lock()
+
+            def poller(rid):
+                deadline = time.time() + 60
+                while time.time() < deadline:
+                    buf = np.empty_like(xs[0])
+                    try:
+                        done, _ = wm.wm_server_poll(srv, rid, buf)
+                    except wm.WmError as e:
+                        assert e.status == wm.WM_ERR_NOT_FOUND
+                        return
+                    if done:
+                        with lock:
+                            got[rid].append(buf)
+                        return
+                    time.sleep(0.0002)
+
+            threads = [threading.Thread(target=poller, args=(rid,)) for rid in ids for _ in range(2)]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+            for rid, x in zip(ids, batch):
+                assert len(got[rid]) == 1, (round_, rid, len(got[rid]))
+                assert np.array_equal(got[rid][0], _alone(ctx, x, 7))
     finally:
         wm.wm_server_stop(srv)

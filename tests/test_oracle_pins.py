@@ -340,6 +340,38 @@ def test_rollout_schedule_and_prefix_composition():
     assert orc.rel_l2(y7, other) > 1e-3
 
 
+def _dense_chain(x, blocks, shape):
+    for w in blocks:
+        x = _torch_block_dense(x, w, shape)
+    return x
+
+
+def test_processor_is_its_blocks_in_order():
+    """Appendix A.2: a processor is a stack of NA blocks, each with its own
+    weights, applied in order. Pinned against the independent dense block
+    chained by hand; the reversed order and a stack that reuses block 0's
+    weights both give a different result, so an order or indexing slip in the
+    oracle cannot pass."""
+    shape = dataclasses.replace(TINY, blocks_p6=3)
+    x = synth.latent(shape, 2, seed=6)
+    p6, _ = synth.processor_weights(shape, seed=0, stress=True)
+    y = orc.processor(x, p6, shape)
+    assert np.max(np.abs(y - _dense_chain(x, p6, shape))) < 1e-11
+    assert orc.rel_l2(y, _dense_chain(x, p6[::-1], shape)) > 1e-3
+    assert orc.rel_l2(y, _dense_chain(x, [p6[0]] * 3, shape)) > 1e-3
+
+
+def test_rollout_is_the_greedy_chain_of_dense_blocks():
+    """Section 2.1: 13 h = two six-hour calls then one one-hour call, each
+    call its processor's blocks in order (dense block chained by hand)."""
+    x = synth.latent(TINY, 1, seed=7)
+    p6, p1 = synth.processor_weights(TINY, seed=0, stress=True)
+    ref = _dense_chain(x, list(p6) + list(p6) + list(p1), TINY)
+    assert np.max(np.abs(orc.rollout(x, 13, p6, p1, TINY) - ref)) < 1e-11
+    wrong_order = _dense_chain(x, list(p1) + list(p6) + list(p6), TINY)
+    assert orc.rel_l2(ref, wrong_order) > 1e-3
+
+
 def test_rel_l2():
     a = np.array([3.0, 4.0])
     assert orc.rel_l2(a, a) == 0.0

@@ -39,6 +39,11 @@ def test_noalloc_rel_l2_matches_allocating_entry_point_on_consecutive_calls():
         for r, g in zip(ref, got):
             assert abs(g - r) <= 1e-12 * abs(r), (n, r, g)
         assert abs(wm.wm_rel_l2_noalloc(a, b) - wm.wm_rel_l2(a, b)) < 1e-12
+        # and against the same sums taken on the host in float64
+        ah, bh = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+        host = (float(np.sum((ah - bh) ** 2)), float(np.sum(bh * bh)))
+        for h, g in zip(host, got):
+            assert abs(g - h) <= 1e-12 * abs(h), (n, h, g)
 
 
 def test_noalloc_rel_l2_rejects_sizes_beyond_its_scratch():
@@ -48,3 +53,12 @@ def test_noalloc_rel_l2_rejects_sizes_beyond_its_scratch():
     st = L.wm_rel_l2_noalloc(16, 16, 268_435_457, out, None)
     assert st == wm.WM_ERR_INVALID_ARG
     assert b"268435456" in L.wm_last_error()
+
+
+def test_noalloc_rel_l2_of_zero_elements_is_zero_and_launches_nothing():
+    L = wm.lib()
+    out = (ctypes.c_double * 2)(7.0, 7.0)
+    a = torch.zeros(4, device="cuda")
+    st = L.wm_rel_l2_noalloc(a.data_ptr(), a.data_ptr(), 0, out, torch.cuda.current_stream().cuda_stream)
+    assert st == wm.WM_OK, L.wm_last_error()
+    assert out[0] == 0.0 and out[1] == 0.0
