@@ -220,7 +220,8 @@ wm_status wm_rel_l2_noalloc(const float* a, const float* b, size_t n, double* ou
 /* NaN / infinity scan of the error check (library service; the paper has no
  * counterpart): *count (HOST) = the number of non-finite elements of x
  * (device, n float32), after an internal synchronisation of `stream`.
- * Allocates an 8-byte device counter per call. */
+ * Allocates an 8-byte device counter per call. n = 0 gives 0 and reads
+ * nothing (x may then be NULL); otherwise WM_ERR_INVALID_ARG for a NULL x. */
 wm_status wm_count_nonfinite(const float* x, size_t n, unsigned long long* count, void* stream);
 
 /* Reads (and clears) the device status word that bounded device-side waits

@@ -993,9 +993,10 @@ wm_status wm_rel_l2(const float* a, const float* b, size_t n, double* out, void*
 }
 
 wm_status wm_count_nonfinite(const float* x, size_t n, unsigned long long* count, void* stream) {
-  if (!x || !count) return fail(WM_ERR_INVALID_ARG, "NULL argument");
+  if (!count) return fail(WM_ERR_INVALID_ARG, "NULL count");
   *count = 0;
-  if (n == 0) return WM_OK;
+  if (n == 0) return WM_OK;   // nothing to read: x may be NULL
+  if (!x) return fail(WM_ERR_INVALID_ARG, "NULL x");
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* acc = nullptr;
   WM_CUDA(cudaMalloc(&acc, sizeof(unsigned long long)));
