@@ -412,7 +412,11 @@ wm_status wm_forecast_fields(wm_ctx* ctx, wm_codec* codec, const float* atm, con
  * shape, else the arithmetic family fixed for it, else the default. Otherwise
  * one of WM_NA_QK_CHUNK8, WM_NA_QK_CHUNK4, WM_NA_KQ picks the arithmetic
  * family, optionally OR-ed with WM_NA_PER_TILE or WM_NA_PERSISTENT to pick
- * the kernel kind (else the kind is chosen by a heuristic). Families round
+ * the kernel kind (else the kind is chosen by a heuristic); or WM_NA_TCGEN05
+ * alone, the tcgen05 kernel (tensor-memory accumulators, 16 x 8 query tiles;
+ * head dim 32 or 48 with window 5x5 or 7x7 in latitude x longitude, or head
+ * dim 64 with 5x5; at least kh + 3 latitudes; clamped longitude needs
+ * W >= kw + 7), WM_ERR_INVALID_ARG for other shapes. Families round
  * differently (order of the softmax sums); the kernel kind and CTA shape do
  * not change any result. */
 enum {
@@ -421,7 +425,9 @@ enum {
   WM_NA_QK_CHUNK4 = 2,   /* as above, update every 4 key groups */
   WM_NA_KQ = 3,          /* S^T = K Q^T, 8 queries per warp, update every 8 key groups */
   WM_NA_PER_TILE = 4,    /* one CTA per query tile */
-  WM_NA_PERSISTENT = 8   /* persistent CTAs with a producer warp */
+  WM_NA_PERSISTENT = 8,  /* persistent CTAs with a producer warp */
+  WM_NA_TCGEN05 = 16     /* S = Q K^T and O += P V on tcgen05, 128 queries per CTA tile, update per 8-longitude
+                            half of a key level (its own family; alone, not combined with the bits above) */
 };
 wm_status wm_op_neighborhood_attention(const void* qkv, void* out, int batch, int D, int H, int W, int C,
                                        int heads, int kd, int kh, int kw, int lon_periodic, int precision,

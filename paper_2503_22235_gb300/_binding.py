@@ -21,6 +21,7 @@ WM_PREC_FP32, WM_PREC_BF16, WM_PREC_BF16_FP8MLP = 0, 1, 2
 EPI_STORE, EPI_GELU, EPI_RESID_F32, EPI_STORE_F32, EPI_GELU_F8 = 0, 1, 2, 3, 4
 WM_NA_AUTO, WM_NA_QK_CHUNK8, WM_NA_QK_CHUNK4, WM_NA_KQ = 0, 1, 2, 3
 WM_NA_PER_TILE, WM_NA_PERSISTENT = 4, 8
+WM_NA_TCGEN05 = 16
 
 _c_int, _c_float, _vp, _sz = ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
 

@@ -1119,7 +1119,8 @@ wm_status wm_op_neighborhood_attention(const void* qkv, void* out, int batch, in
   }
   if (precision != WM_PREC_BF16) return fail(WM_ERR_INVALID_ARG, "attention precision must be FP32 or BF16");
   if (C % 8 != 0) return fail(WM_ERR_INVALID_ARG, "BF16 attention needs C % 8 == 0");
-  if (variant < 0 || variant > 15 || (variant & 12) == 12 || (variant != 0 && (variant & 3) == 0))
+  if (variant != WM_NA_TCGEN05 &&
+      (variant < 0 || variant > 15 || (variant & 12) == 12 || (variant != 0 && (variant & 3) == 0)))
     return fail(WM_ERR_INVALID_ARG, "bad attention variant");
   return wm::launch_na_bf16((const bf16*)qkv, (bf16*)out, batch, D, H, W, C, heads, kd, kh, kw, lon_periodic != 0, s,
                             variant);

@@ -67,6 +67,7 @@ wm_status prepare_kernels() {
   if (dev >= 0 && dev < 64 && done[dev]) return WM_OK;
   wm_status st = prepare_gemm_tc();
   if (st == WM_OK) st = prepare_na_bf16();
+  if (st == WM_OK) st = prepare_na_tc();
   if (st == WM_OK) st = prepare_na_f32();
   if (st == WM_OK && !device_status_word()) st = fail(WM_ERR_OOM, "device status word allocation failed");
   if (st == WM_OK && dev >= 0 && dev < 64) done[dev] = true;

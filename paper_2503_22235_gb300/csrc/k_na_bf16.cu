@@ -932,9 +932,11 @@ struct NaPlan {
   int gch;       // 16-key groups scored per softmax update
   int tr;        // 1: transposed formulation
   int WH, WW, span;   // warp patch and key-rectangle width (fixed by tr and the window)
+  int tc;        // 1: the tcgen05 kernel (k_na_tc.cu; the fields above are unused)
 };
 
-int family(const NaPlan& pl) { return pl.gch | (pl.tr << 8); }
+constexpr int kFamilyTc = 1024;
+int family(const NaPlan& pl) { return pl.tc ? kFamilyTc : (pl.gch | (pl.tr << 8)); }
 
 using NaKey = std::array<int, 11>;
 std::mutex g_na_mu;
@@ -985,8 +987,15 @@ size_t plan_smem(const NaPlan& pl, int kh, int H, int dh) {
 }
 
 // Candidate plans of one arithmetic family (fam = 0: every family).
-std::vector<NaPlan> na_candidates(int kh, int kw, int H, int dh, int fam) {
+std::vector<NaPlan> na_candidates(int kh, int kw, int H, int W, int C, int heads, bool periodic, int fam) {
+  const int dh = C / heads;
   std::vector<NaPlan> out;
+  if ((fam == 0 || fam == kFamilyTc) && na_tc_supported(H, W, C, heads, kh, kw, periodic)) {
+    NaPlan tc{};
+    tc.NWH = tc.NWW = 1;
+    tc.tc = 1;
+    out.push_back(tc);
+  }
   int WH, WW, span;
   auto add = [&](int nwh, int nww, int kind, int nbuf, int gch, int tr) {
     NaPlan pl{nwh, nww, kind, nbuf, gch, tr, WH, WW, span};
@@ -1021,10 +1030,11 @@ std::vector<NaPlan> na_candidates(int kh, int kw, int H, int dh, int fam) {
 // kernel kind `kind`, unless it is -1): fewest staged keys per query times
 // tile waste; persistent plans are preferred when the tile count gives every
 // SM several tiles.
-NaPlan na_heuristic(int B, int D, int H, int W, int heads, int kh, int kw, int dh, int fam, int kind) {
+NaPlan na_heuristic(int B, int D, int H, int W, int heads, int kh, int kw, int dh, bool periodic, int fam, int kind) {
   NaPlan best{};
   double best_score = 1e30;
-  for (const NaPlan& pl : na_candidates(kh, kw, H, dh, fam)) {
+  for (const NaPlan& pl : na_candidates(kh, kw, H, W, heads * dh, heads, periodic, fam)) {
+    if (pl.tc) return pl;   // the tcgen05 family has one plan
     if (kind >= 0 && pl.kind != kind) continue;
     const int TH = pl.NWH * pl.WH, TW = pl.NWW * pl.WW;
     const int th = (H + TH - 1) / TH, tw = (W + TW - 1) / TW;
@@ -1107,6 +1117,8 @@ wm_status launch_plan(const NaPlan& pl, na::Params p, cudaStream_t s, bool pdl) 
 }
 
 wm_status launch_with(const NaPlan& pl, const na::Params& p, int dh, cudaStream_t s, bool pdl = false) {
+  if (pl.tc)
+    return launch_na_tc(p.qkv, p.out, p.B, p.D, p.H, p.W, p.C, p.heads, p.kd, p.kh, p.kw, p.periodic != 0, s, pdl);
   switch (dh) {
     case 16: return launch_plan<16>(pl, p, s, pdl);
     case 32: return launch_plan<32>(pl, p, s, pdl);
@@ -1139,7 +1151,11 @@ wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, in
     return fail(WM_ERR_INVALID_ARG, "longitude window too wide for the BF16 attention kernel");
   NaPlan pl{};
   int fam = 8, kind = -1;
-  if (variant != 0) {
+  if (variant == WM_NA_TCGEN05) {
+    if (!na_tc_supported(H, W, C, heads, kh, kw, periodic))
+      return fail(WM_ERR_INVALID_ARG, "shape not supported by the tcgen05 attention kernel");
+    fam = kFamilyTc;
+  } else if (variant != 0) {
     static const int fams[4] = {0, 8, 4, 8 | 256};
     fam = fams[variant & 3];
     kind = (variant & 4) ? 0 : (variant & 8) ? 1 : -1;
@@ -1150,7 +1166,7 @@ wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, in
     auto ig = g_na_family.find(na_key(0, D, H, W, C, heads, kd, kh, kw, periodic));
     if (ig != g_na_family.end()) fam = ig->second;
   }
-  if (!pl.NWH) pl = na_heuristic(B, D, H, W, heads, kh, kw, dh, fam, kind);
+  if (!pl.NWH) pl = na_heuristic(B, D, H, W, heads, kh, kw, dh, periodic, fam, kind);
   if (!pl.NWH) return fail(WM_ERR_INVALID_ARG, "attention window too large for the BF16 attention kernel");
   return launch_with(pl, make_params(qkv, out, B, D, H, W, C, heads, kd, kh, kw, periodic), dh, s, pdl);
 }
@@ -1177,7 +1193,7 @@ wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, 
     auto ig = g_na_family.find(na_key(0, D, H, W, C, heads, kd, kh, kw, periodic));
     if (ig != g_na_family.end()) fam_fixed = ig->second;
   }
-  for (const NaPlan& pl : na_candidates(kh, kw, H, dh, fam_fixed)) {
+  for (const NaPlan& pl : na_candidates(kh, kw, H, W, C, heads, periodic, fam_fixed)) {
     st = launch_with(pl, p, dh, s);
     if (st != WM_OK) break;
     cudaEventRecord(e0, s);
@@ -1192,9 +1208,12 @@ wm_status autotune_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, 
     cudaEventElapsedTime(&ms, e0, e1);
     {
       char line[200];
-      std::snprintf(line, sizeof line, "  candidate B=%d %s %s warps=%dx%d patch=%dx%d buffers=%d chunk=%d: %.3f ms\n",
-                    B, pl.tr ? "K.Q^T" : "Q.K^T", pl.kind ? "persistent" : "per-tile", pl.NWH, pl.NWW, pl.WH, pl.WW,
-                    pl.nbuf, pl.gch, ms / 3.0);
+      if (pl.tc)
+        std::snprintf(line, sizeof line, "  candidate B=%d tcgen05 persistent tile=16x8: %.3f ms\n", B, ms / 3.0);
+      else
+        std::snprintf(line, sizeof line, "  candidate B=%d %s %s warps=%dx%d patch=%dx%d buffers=%d chunk=%d: %.3f ms\n",
+                      B, pl.tr ? "K.Q^T" : "Q.K^T", pl.kind ? "persistent" : "per-tile", pl.NWH, pl.NWW, pl.WH, pl.WW,
+                      pl.nbuf, pl.gch, ms / 3.0);
       std::lock_guard<std::mutex> lk(g_na_mu);
       g_na_log += line;
     }
@@ -1223,11 +1242,17 @@ std::string describe_na_plans() {
     const NaKey& k = kv.first;
     const NaPlan& pl = kv.second;
     char line[256];
-    std::snprintf(line, sizeof line,
-                  "attention B=%d D=%d H=%d W=%d C=%d heads=%d window=%dx%dx%d periodic=%d -> %s %s warps=%dx%d "
-                  "patch=%dx%d buffers=%d chunk=%d %.3f ms\n",
-                  k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8], k[9], pl.tr ? "K.Q^T" : "Q.K^T",
-                  pl.kind ? "persistent" : "per-tile", pl.NWH, pl.NWW, pl.WH, pl.WW, pl.nbuf, pl.gch, g_na_ms[k]);
+    if (pl.tc)
+      std::snprintf(line, sizeof line,
+                    "attention B=%d D=%d H=%d W=%d C=%d heads=%d window=%dx%dx%d periodic=%d -> tcgen05 persistent "
+                    "tile=16x8 %.3f ms\n",
+                    k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8], k[9], g_na_ms[k]);
+    else
+      std::snprintf(line, sizeof line,
+                    "attention B=%d D=%d H=%d W=%d C=%d heads=%d window=%dx%dx%d periodic=%d -> %s %s warps=%dx%d "
+                    "patch=%dx%d buffers=%d chunk=%d %.3f ms\n",
+                    k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8], k[9], pl.tr ? "K.Q^T" : "Q.K^T",
+                    pl.kind ? "persistent" : "per-tile", pl.NWH, pl.NWW, pl.WH, pl.WW, pl.nbuf, pl.gch, g_na_ms[k]);
     out += line;
   }
   return out + g_na_log;

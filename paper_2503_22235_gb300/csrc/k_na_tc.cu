@@ -1,0 +1,678 @@
+// Fused 3D neighborhood attention on the 5th-generation tensor cores
+// (tcgen05): S = Q K^T and O += P V as tcgen05.mma with the accumulators in
+// tensor memory, BF16 operands, FP32 accumulation and FP32 softmax
+// statistics. The paper's attention is NATTEN's fused kernel (Section 2.1,
+// "NATTEN"; Appendix A.2: window (5, 7, 7), bump windows at the poles,
+// circular padding in longitude); this kernel computes the same function.
+//
+// Work unit ("tile"): batch element b, head, query level d and a block of
+// 16 latitudes x 8 longitudes = 128 queries, one per tensor-memory lane
+// (lane r = query (h0 + r / 8, w0 + r % 8)). All queries of a tile share
+// their kd key levels. For every key level the CTA stages a K and a V slab
+// of HR latitude rows x 16 longitude columns (the union of the tile's
+// windows, HR = 16 + kh - 1, plus spare columns), split into two halves of 8
+// longitude columns. Per (level, half) -- a "step" -- the tensor core
+// computes S = Q K^T for all 128 queries against the half's HR x 8 keys
+// (N = HR * 8, padded to 16), the softmax warps turn S into P in place, and
+// the tensor core accumulates O += P V.
+//
+// Warp roles (persistent CTAs, one per SM, 8 warps: two per SM sub-partition,
+// so each thread may use up to 255 registers):
+//   warps 0-3  softmax: warp q owns tensor-memory lanes 32q..32q+31, i.e.
+//              query rows 4q..4q+3 of the tile. Their windows cover kh + 3
+//              key rows, so each thread reads only those rows of S (8
+//              columns per key row, one 8-column tcgen05.ld each), masks
+//              keys outside its own window (bump rows, periodic or clamped
+//              columns), keeps a running max m and sum l in FP32 (the max
+//              moves only when a row's maximum grows by more than 2^8, and
+//              then O is rescaled in tensor memory), writes P = 2^(S - m) as
+//              bf16 pairs over the first half of its S columns, and zeros
+//              in the key rows its window does not reach. They also copy
+//              the next tile's queries into tensor memory (the A operand of
+//              Q K^T) and write each finished tile's O / l to global memory.
+//   warp 4     MMA issuer (one thread): QK(step + 2) is issued right after
+//              PV(step), so the other S buffer's softmax overlaps both.
+//   warps 5-7  loaders: cp.async 16-byte copies of the K/V slabs into a ring
+//              of NS stages, in a layout the MMA reads without swizzle:
+//              [K or V][half][channel chunk of 8][key][8 channels] with the
+//              chunk stride NKS = NPAD + 1 keys (conflict-free shared-memory
+//              stores; keys past HR * 8 are zero).
+// Tensor memory (512 columns): S0, S1 (NPAD each), O0, O1 (dh each), Q0, Q1
+// (dh / 2 each, bf16 pairs). Every mbarrier wait is bounded in time; on a
+// timeout the CTA records WM_ERR_TIMEOUT, drains its own copies and MMAs,
+// frees tensor memory and returns.
+#include <algorithm>
+#include <cmath>
+
+#include "tc_ptx.cuh"
+
+namespace wm {
+namespace natc {
+
+using namespace ptx;
+
+constexpr int kSoftWarps = 4, kMmaWarp = 4, kLoadWarps = 3;
+constexpr int kThreads = 32 * (kSoftWarps + 1 + kLoadWarps);
+constexpr int kMaxStages = 4;
+constexpr float kLazyLog2 = 8.f;   // the running max moves when a row max grows by more than this
+
+struct Params {
+  const __nv_bfloat16* qkv;
+  __nv_bfloat16* out;
+  int* status;
+  int B, D, H, W, C, heads, kd, periodic;
+  int HR;      // key rows of a slab
+  int NPAD;    // keys of a half as the MMA reads them (HR * 8 rounded up to 16)
+  int NKS;     // keys per channel chunk in shared memory (NPAD + 1)
+  int NS;      // slab stages
+  int tiles_h, tiles_w, ntiles;
+  int colO, colQ;   // tensor-memory columns of O0 (O1 = +oStride) and Q0 (Q1 = +qStride)
+  int oStride, qStride;
+  float scale_log2;   // log2(e) / sqrt(dh)
+};
+
+struct TileGeo {
+  int b, head, d, h0, w0;
+  int ld0;      // first key level
+  int s_lat;    // first slab latitude row
+  int s_lon;    // longitude of slab column 0 (periodic: may be negative or wrap)
+};
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+template <int KH, int KW>
+__device__ __forceinline__ TileGeo tile_geo(const Params& p, int t) {
+  TileGeo g;
+  const int tw = t % p.tiles_w;
+  t /= p.tiles_w;
+  const int th = t % p.tiles_h;
+  t /= p.tiles_h;
+  g.d = t % p.D;
+  t /= p.D;
+  g.head = t % p.heads;
+  g.b = t / p.heads;
+  g.h0 = th * 16;
+  g.w0 = tw * 8;
+  g.ld0 = clampi(g.d - p.kd / 2, 0, p.D - p.kd);
+  g.s_lat = clampi(g.h0 - KH / 2, 0, p.H - p.HR);
+  g.s_lon = p.periodic ? g.w0 - KW / 2 : clampi(g.w0 - KW / 2, 0, p.W - (KW + 7));
+  return g;
+}
+
+// Shared-memory matrix descriptor without swizzle: core matrices of 8 rows x
+// 16 bytes stored contiguously; lbo = byte distance between core matrices
+// adjacent along K, sbo = along M/N (both for K-major and, in this layout
+// type, for MN-major operands).
+__device__ __forceinline__ uint64_t desc_noswz(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, A K-major, B K-major
+// (b_mn = 0) or MN-major (b_mn = 1).
+__host__ __device__ constexpr uint32_t idesc_bf16_ab(int M, int N, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// D (tmem) (+)= A (tmem) * B (shared-memory descriptor)
+__device__ __forceinline__ void umma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 16-byte global -> shared copy through L1 (.ca: the lanes that share a
+// 32-byte sector are served by one L2 request)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Byte offset of (stage, K/V, half, chunk, key) in the slab ring.
+__device__ __forceinline__ uint32_t slab_off(const Params& p, int DHC, int stage, int kv, int h, int chunk, int key) {
+  return ((uint32_t)(((stage * 4 + kv * 2 + h) * DHC + chunk) * p.NKS + key)) * 16u;
+}
+
+// Softmax warps: copy this lane's query of tile ti into tensor-memory Q
+// buffer ti & 1 (bf16 pairs, the A operand of Q K^T). Out of line: it runs
+// once per tile and keeps the step loop's registers free.
+template <int DH, int KH, int KW>
+__device__ __noinline__ bool softmax_write_q(const Params& p, int ti, int q, int lane, uint32_t lane_base,
+                                             uint64_t* q_empty, uint64_t* q_full, volatile int* abort_flag) {
+  // the wait's outcome is made warp-uniform: the tcgen05 stores below are warp-collective
+  if (!__all_sync(0xffffffffu, mbar_wait(&q_empty[ti & 1], ((uint32_t)(ti >> 1) & 1u) ^ 1u, abort_flag)))
+    return false;
+  tc_fence_after();
+  const TileGeo G = tile_geo<KH, KW>(p, blockIdx.x + ti * gridDim.x);
+  const int a = min(G.h0 + 4 * q + (lane >> 3), p.H - 1), w = min(G.w0 + (lane & 7), p.W - 1);
+  const long tok = ((long)(G.b * p.D + G.d) * p.H + a) * p.W + w;
+  const uint4* src = reinterpret_cast<const uint4*>(p.qkv + tok * (3L * p.C) + (long)G.head * DH);
+  const uint32_t qcol = lane_base + (uint32_t)(p.colQ + (ti & 1) * p.qStride);
+#pragma unroll
+  for (int c = 0; c < DH / 16; ++c) {   // 16 channels = 8 columns per store
+    const uint4 x0 = __ldg(src + 2 * c), x1 = __ldg(src + 2 * c + 1);
+    const uint32_t r[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    tmem_st8(qcol + 8u * c, r);
+  }
+  tmem_wait_st();
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&q_full[ti & 1]);
+  return true;
+}
+
+// Softmax warps: O / l of tile ti (tensor-memory buffer ti & 1) to global
+// memory as bf16; frees the O buffer for the tile after next.
+template <int DH>
+__device__ __noinline__ bool softmax_epilogue(const Params& p, int ti, int lane, uint32_t lane_base, float l,
+                                              long orow, bool valid, uint64_t* o_full, uint64_t* o_empty,
+                                              volatile int* abort_flag) {
+  if (!__all_sync(0xffffffffu, mbar_wait(&o_full[ti & 1], (uint32_t)(ti >> 1) & 1u, abort_flag))) return false;
+  tc_fence_after();
+  uint32_t o[DH];
+#pragma unroll
+  for (int c = 0; c < DH / 8; ++c) {
+    uint32_t r[8];
+    tmem_ld8_nowait(lane_base + (uint32_t)(p.colO + (ti & 1) * p.oStride) + 8u * c, r);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) o[8 * c + i] = r[i];
+  }
+  tmem_wait_ld();
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&o_empty[ti & 1]);
+  if (valid) {
+    const float inv = 1.f / l;
+    uint4* dst = reinterpret_cast<uint4*>(p.out + orow);
+#pragma unroll
+    for (int c = 0; c < DH / 8; ++c) {
+      uint4 v;
+      v.x = pack_bf16(__uint_as_float(o[8 * c + 0]) * inv, __uint_as_float(o[8 * c + 1]) * inv);
+      v.y = pack_bf16(__uint_as_float(o[8 * c + 2]) * inv, __uint_as_float(o[8 * c + 3]) * inv);
+      v.z = pack_bf16(__uint_as_float(o[8 * c + 4]) * inv, __uint_as_float(o[8 * c + 5]) * inv);
+      v.w = pack_bf16(__uint_as_float(o[8 * c + 6]) * inv, __uint_as_float(o[8 * c + 7]) * inv);
+      dst[c] = v;
+    }
+  }
+  return true;
+}
+
+template <int DH, int KH, int KW>
+__global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
+  constexpr int DHC = DH / 8;       // 16-byte channel chunks per head
+  constexpr int WR = KH + 3;        // key rows a softmax warp reads
+  constexpr int RH = KH / 2, RW = KW / 2;
+  static_assert(DH % 16 == 0 && DH <= 64, "head dim");
+  static_assert(KW + 7 <= 16, "a slab row holds 16 longitude columns");
+
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t kv_full[kMaxStages], kv_empty[kMaxStages];
+  __shared__ __align__(8) uint64_t s_full[2], p_ready[2], pv_done[2], q_full[2], q_empty[2], o_full[2], o_empty[2];
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int my_tiles = blockIdx.x < p.ntiles ? (p.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int steps_per_tile = 2 * p.kd;
+  const int nsteps = my_tiles * steps_per_tile;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.NS; ++s) {
+      mbar_init(&kv_full[s], 32 * kLoadWarps);
+      mbar_init(&kv_empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&s_full[i], 1);
+      mbar_init(&p_ready[i], kSoftWarps);
+      mbar_init(&pv_done[i], 1);
+      mbar_init(&q_full[i], kSoftWarps);
+      mbar_init(&q_empty[i], 1);
+      mbar_init(&o_full[i], 1);
+      mbar_init(&o_empty[i], kSoftWarps);
+    }
+    mbar_init(&drain_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // The MMA also reads keys the loaders never write (past HR * 8 in every
+  // chunk, and the spare slab columns kw + 7 .. 15): masked scores, zero P,
+  // so they must hold finite values. Zero the whole ring once.
+  {
+    const int items = p.NS * 4 * DHC * p.NKS;
+    for (int i = threadIdx.x; i < items; i += blockDim.x)
+      *reinterpret_cast<uint4*>(smem + (uint32_t)i * 16u) = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  pdl_wait();      // qkv of the previous kernel is complete from here on
+  pdl_trigger();
+
+  // tensor-memory column of S buffer i (0 or 1)
+  auto colS = [&](int i) -> uint32_t { return (uint32_t)(i * p.NPAD); };
+
+  if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc_pv = idesc_bf16_ab(128, DH, 1);
+      const uint32_t idesc_qk = idesc_bf16_ab(128, p.NPAD, 0);
+      const uint32_t chunk_bytes = (uint32_t)p.NKS * 16u;
+      auto issue_qk = [&](int v) -> bool {
+        const int ti = v / steps_per_tile, r = v - ti * steps_per_tile, l = r >> 1, h = r & 1;
+        const int g = ti * p.kd + l, stage = g % p.NS;
+        if (r == 0 && !mbar_wait(&q_full[ti & 1], (uint32_t)(ti >> 1) & 1u, &abort_flag)) return false;
+        if (h == 0 && !mbar_wait(&kv_full[stage], (uint32_t)(g / p.NS) & 1u, &abort_flag)) return false;
+        tc_fence_after();
+        const uint32_t d = tmem + colS(v & 1);
+        const uint32_t a = tmem + (uint32_t)(p.colQ + (ti & 1) * p.qStride);
+        const uint32_t kb = sbase + slab_off(p, DHC, stage, 0, h, 0, 0);
+#pragma unroll
+        for (int k = 0; k < DH / 16; ++k)   // 16 channels = 2 chunks per MMA
+          umma_ts(d, a + 8u * k, desc_noswz(kb + 2u * k * chunk_bytes, chunk_bytes, 128u), idesc_qk, k > 0);
+        umma_commit(&s_full[v & 1]);
+        if (r == steps_per_tile - 1) umma_commit(&q_empty[ti & 1]);
+        return true;
+      };
+      auto issue_pv = [&](int u) -> bool {
+        const int ti = u / steps_per_tile, r = u - ti * steps_per_tile, l = r >> 1, h = r & 1;
+        const int g = ti * p.kd + l, stage = g % p.NS;
+        if (!mbar_wait(&p_ready[u & 1], (uint32_t)(u >> 1) & 1u, &abort_flag)) return false;
+        if (r == 0 && !mbar_wait(&o_empty[ti & 1], ((uint32_t)(ti >> 1) & 1u) ^ 1u, &abort_flag)) return false;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(p.colO + (ti & 1) * p.oStride);
+        const uint32_t a = tmem + colS(u & 1);
+        const uint32_t vb = sbase + slab_off(p, DHC, stage, 1, h, 0, 0);
+        const int nk = p.NPAD / 16;
+        for (int k = 0; k < nk; ++k)       // 16 keys = 2 core matrices per MMA
+          umma_ts(d, a + 8u * k, desc_noswz(vb + 256u * k, 128u, chunk_bytes), idesc_pv, (r > 0 || k > 0) ? 1u : 0u);
+        umma_commit(&pv_done[u & 1]);
+        if (h == 1) umma_commit(&kv_empty[stage]);
+        if (r == steps_per_tile - 1) umma_commit(&o_full[ti & 1]);
+        return true;
+      };
+      bool ok = true;
+      if (nsteps > 0) ok = issue_qk(0);
+      if (ok && nsteps > 1) ok = issue_qk(1);
+      for (int u = 0; u < nsteps && ok; ++u) {
+        ok = issue_pv(u);
+        if (ok && u + 2 < nsteps) ok = issue_qk(u + 2);
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(p.status, (int)WM_ERR_TIMEOUT);
+        umma_commit(&drain_bar);   // completes once every MMA issued above has finished
+        volatile int never = 0;
+        mbar_wait(&drain_bar, 0, &never);
+      }
+    }
+  } else if (warp > kMmaWarp) {
+    // --------------------------------------------------------------- loaders
+    // lane = (column parity, K or V, channel chunk): one instruction copies 2
+    // longitude columns x K and V x the head's chunks of one slab row.
+    const int lw = warp - kMmaWarp - 1;
+    const int colpar = lane >> 4, kv = (lane >> 3) & 1, c8 = lane & 7;
+    const bool active = c8 < DHC;
+    const long C3 = 3L * p.C;
+    bool ok = true;
+    int g = 0, prev_stage = -1;
+    for (int ti = 0; ti < my_tiles && ok; ++ti) {
+      const TileGeo G = tile_geo<KH, KW>(p, blockIdx.x + ti * gridDim.x);
+      int lonoff[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        int lon = G.s_lon + 2 * j + colpar;
+        if (p.periodic) {
+          lon %= p.W;
+          if (lon < 0) lon += p.W;
+        } else {
+          lon = min(lon, p.W - 1);   // spare columns past the grid: any finite data (masked)
+        }
+        lonoff[j] = lon * (int)C3;
+      }
+      const __nv_bfloat16* head_base = p.qkv + (long)(1 + kv) * p.C + (long)G.head * DH + c8 * 8;   // K or V
+      for (int l = 0; l < p.kd; ++l, ++g) {
+        const int stage = g % p.NS;
+        if (!mbar_wait(&kv_empty[stage], ((uint32_t)(g / p.NS) & 1u) ^ 1u, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        const long lev = (long)G.b * p.D + G.ld0 + l;
+        const __nv_bfloat16* row0 = head_base + ((lev * p.H + G.s_lat) * p.W) * C3;
+        const uint32_t d0 = sbase + slab_off(p, DHC, stage, kv, 0, c8, colpar);
+        const uint32_t d1 = sbase + slab_off(p, DHC, stage, kv, 1, c8, colpar);
+        if (active) {
+          for (int r = lw; r < p.HR; r += kLoadWarps) {
+            const __nv_bfloat16* src = row0 + (long)r * p.W * C3;
+            const uint32_t o = (uint32_t)r * 128u;   // 8 keys of 16 bytes per slab row
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cp_async16(d0 + o + 32u * j, src + lonoff[j]);
+            // half 1: columns 8 .. kw + 6 (the spare columns stay zero)
+#pragma unroll
+            for (int j = 0; j < (KW + 7) / 2 - 4; ++j) cp_async16(d1 + o + 32u * j, src + lonoff[4 + j]);
+          }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // the previous level's copies have landed: publish it to the MMA
+        if (prev_stage >= 0) {
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+          fence_async_smem();
+          mbar_arrive(&kv_full[prev_stage]);
+        }
+        prev_stage = stage;
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (ok && prev_stage >= 0) {
+      fence_async_smem();
+      mbar_arrive(&kv_full[prev_stage]);
+    }
+    if (!ok) {
+      abort_flag = 1;
+      atomicExch(p.status, (int)WM_ERR_TIMEOUT);
+    }
+  } else {
+    // --------------------------------------------------------------- softmax
+    const int q = warp;   // tensor-memory lane quarter = query rows 4q..4q+3
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    const uint64_t scale2 = pack_f2(p.scale_log2, p.scale_log2);
+    const uint64_t neg2 = pack_f2(-INFINITY, -INFINITY);
+    const long C3 = 3L * p.C;
+    bool ok = true;
+
+    if (my_tiles > 0) ok = softmax_write_q<DH, KH, KW>(p, 0, q, lane, lane_base, q_empty, q_full, &abort_flag);
+    float prev_l = 1.f;
+    long prev_orow = 0;
+    bool prev_valid = false;
+    for (int ti = 0; ti < my_tiles && ok; ++ti) {
+      const TileGeo G = tile_geo<KH, KW>(p, blockIdx.x + ti * gridDim.x);
+      // this lane's query and its window inside the slab
+      const int a = G.h0 + 4 * q + (lane >> 3), w = G.w0 + (lane & 7);
+      const bool valid = a < p.H && w < p.W;
+      const int ac = min(a, p.H - 1), wc = min(w, p.W - 1);
+      const int ra = clampi(ac - RH, 0, p.H - KH) - G.s_lat;                  // first window row in the slab
+      const int cb = p.periodic ? wc - G.w0 : clampi(wc - RW, 0, p.W - KW) - G.s_lon;   // first window column
+      const int a0 = min(G.h0 + 4 * q, p.H - 1);
+      const int R0 = min(clampi(a0 - RH, 0, p.H - KH) - G.s_lat, p.HR - WR);  // the warp's first key row
+      const int rlo = ra - R0;                                                // 0 .. 3
+      uint64_t cbias[2][4];   // per half: (0 | -inf) pairs for the 8 columns of a key row
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c0 = 8 * h + 2 * j;
+          const float b0 = (c0 >= cb && c0 < cb + KW) ? 0.f : -INFINITY;
+          const float b1 = (c0 + 1 >= cb && c0 + 1 < cb + KW) ? 0.f : -INFINITY;
+          cbias[h][j] = pack_f2(b0, b1);
+        }
+      const long orow = (((long)(G.b * p.D + G.d) * p.H + ac) * p.W + wc) * p.C + (long)G.head * DH;
+      float m = -INFINITY, lsum = 0.f;
+      const uint32_t ocol = lane_base + (uint32_t)(p.colO + (ti & 1) * p.oStride);
+
+      for (int r = 0; r < steps_per_tile && ok; ++r) {
+        const int u = ti * steps_per_tile + r, h = r & 1;
+        if (!__all_sync(0xffffffffu, mbar_wait(&s_full[u & 1], (uint32_t)(u >> 1) & 1u, &abort_flag))) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t scol = lane_base + colS(u & 1);
+        uint64_t cbh[4];   // this half's column bias pairs
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cbh[j] = h ? cbias[1][j] : cbias[0][j];
+        // One pass over this step's key rows (read from tensor memory in
+        // groups of RG rows): scale and mask, track the row max, and -- when
+        // with_p -- P = 2^(t - mref) as bf16 pairs into pk with its row sum.
+        constexpr int RG = (WR + 1) / 2;
+        uint32_t pk[WR][4];
+        auto pass = [&](bool with_p, float mref, float& mx, float& ls) {
+          const uint64_t mref2 = pack_f2(mref, mref);
+          float ls0 = 0.f, ls1 = 0.f;
+#pragma unroll
+          for (int g0 = 0; g0 < WR; g0 += RG) {
+            uint32_t sr[RG][8];
+#pragma unroll
+            for (int i = 0; i < RG; ++i)
+              if (g0 + i < WR) tmem_ld8_nowait(scol + 8u * (uint32_t)(R0 + g0 + i), sr[i]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < RG; ++i) {
+              const int rr = g0 + i;
+              if (rr < WR) {
+                const bool rok = (unsigned)(rr - rlo) < (unsigned)KH;
+                float t[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  fma_f2(t[2 * j], t[2 * j + 1], __uint_as_float(sr[i][2 * j]), __uint_as_float(sr[i][2 * j + 1]),
+                         scale2, rok ? cbh[j] : neg2);
+                mx = max3(mx, max3(t[0], t[1], t[2]), max3(t[3], t[4], t[5]));
+                mx = max3(mx, t[6], t[7]);
+                if (with_p) {
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) {
+                    float d0, d1;
+                    sub_f2(d0, d1, t[2 * j], t[2 * j + 1], mref2);
+                    const float e0 = ex2(d0), e1 = ex2(d1);
+                    add_f2(ls0, ls1, ls0, ls1, e0, e1);
+                    pk[rr][j] = pack_bf16(e0, e1);
+                  }
+                }
+              }
+            }
+          }
+          ls = ls0 + ls1;
+        };
+        // Single pass against the current running max; the step is redone
+        // only when some row's max grows by more than 2^kLazyLog2 (always on
+        // a tile's first step, where the max is not set yet). The decision is
+        // warp-uniform: the tensor-memory loads are warp-collective, and a
+        // row whose max did not move recomputes the same values.
+        const bool first = (r == 0);
+        float mx = -INFINITY, ls = 0.f;
+        pass(!first, m == -INFINITY ? 0.f : m, mx, ls);
+        const bool grow = mx > m + kLazyLog2;
+        if (first || __any_sync(0xffffffffu, grow)) {
+          const bool rescale = grow && m != -INFINITY;
+          if (__any_sync(0xffffffffu, rescale)) {
+            // O already holds earlier steps of this tile: wait for the last
+            // PV, then rescale O (alpha = 1 for rows that keep their max)
+            const int up = u - 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&pv_done[up & 1], (uint32_t)(up >> 1) & 1u, &abort_flag))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const float alpha = rescale ? ex2(m - mx) : 1.f;
+            const uint64_t alpha2 = pack_f2(alpha, alpha);
+#pragma unroll
+            for (int c = 0; c < DH / 8; ++c) {
+              uint32_t v[8];
+              tmem_ld8_nowait(ocol + 8u * c, v);
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 8; i += 2) {
+                float x0 = __uint_as_float(v[i]), x1 = __uint_as_float(v[i + 1]);
+                mul_f2(x0, x1, alpha2);
+                v[i] = __float_as_uint(x0);
+                v[i + 1] = __float_as_uint(x1);
+              }
+              tmem_st8(ocol + 8u * c, v);
+            }
+            lsum *= alpha;
+          }
+          if (grow) m = mx;
+          float mx2 = -INFINITY;
+          pass(true, m == -INFINITY ? 0.f : m, mx2, ls);
+        }
+        lsum += ls;
+        // P over the first half of this step's S columns: key row R0 + rr ->
+        // P columns 4 (R0 + rr) .. + 3
+#pragma unroll
+        for (int rr = 0; rr < WR; ++rr)
+          tmem_st4(scol + 4u * (uint32_t)(R0 + rr), pk[rr][0], pk[rr][1], pk[rr][2], pk[rr][3]);
+        // zeros in the key rows outside the warp's window
+        for (int kr = 0; kr < R0; ++kr) tmem_st4(scol + 4u * kr, 0u, 0u, 0u, 0u);
+        for (int kr = R0 + WR; kr < p.NPAD / 8; ++kr) tmem_st4(scol + 4u * kr, 0u, 0u, 0u, 0u);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&p_ready[u & 1]);
+        if (r == 0) {
+          // the previous tile's output, and the next tile's queries, while
+          // this tile's second step is computed
+          if (ti > 0 && !softmax_epilogue<DH>(p, ti - 1, lane, lane_base, prev_l, prev_orow, prev_valid, o_full,
+                                              o_empty, &abort_flag)) { ok = false; break; }
+          if (ti + 1 < my_tiles &&
+              !softmax_write_q<DH, KH, KW>(p, ti + 1, q, lane, lane_base, q_empty, q_full, &abort_flag)) {
+            ok = false;
+            break;
+          }
+        }
+      }
+      prev_l = lsum;
+      prev_orow = orow;
+      prev_valid = valid;
+    }
+    if (ok && my_tiles > 0)
+      ok = softmax_epilogue<DH>(p, my_tiles - 1, lane, lane_base, prev_l, prev_orow, prev_valid, o_full, o_empty,
+                                &abort_flag);
+    if (!ok) {
+      abort_flag = 1;
+      atomicExch(p.status, (int)WM_ERR_TIMEOUT);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host ----
+
+constexpr int kSmemLimit = 226 * 1024;   // dynamic shared memory; the rest of the 227 KB is static (barriers)
+
+struct Layout {
+  int HR, NPAD, NKS, NS, colO, colQ, oStride, qStride;
+  size_t smem;
+};
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Tensor-memory and shared-memory layout for a shape; false if the kernel
+// does not support it.
+bool layout_for(int H, int W, int dh, int kh, int kw, bool periodic, Layout* L) {
+  if (dh != 32 && dh != 48 && dh != 64) return false;
+  if (!((kh == 5 && kw == 5) || (kh == 7 && kw == 7))) return false;
+  L->HR = std::min(16 + kh - 1, H);
+  if (L->HR < kh + 3) return false;                       // a warp's key rows must fit the slab
+  if (!periodic && W < kw + 7) return false;
+  L->NPAD = round_up(L->HR * 8, 16);
+  if (L->NPAD > 256) return false;
+  L->NKS = L->NPAD + 1;
+  L->oStride = round_up(dh, 16);
+  L->qStride = round_up(dh / 2, 16);
+  L->colO = 2 * L->NPAD;
+  L->colQ = L->colO + 2 * L->oStride;
+  if (L->colQ + 2 * L->qStride > 512) return false;
+  const size_t stage = (size_t)4 * (dh / 8) * L->NKS * 16;
+  // room for the stages; and, from the last K region, for the whole span a
+  // K-major descriptor can address, so no read leaves the allocation
+  for (int ns = kMaxStages; ns >= 2; --ns) {
+    const size_t k_last = (size_t)(ns - 1) * stage + (size_t)(dh / 8) * L->NKS * 16;
+    const size_t span = (size_t)(L->NPAD / 8) * L->NKS * 16 + 1024;
+    const size_t need = std::max((size_t)ns * stage, k_last + span) + 1024;
+    if (need <= (size_t)kSmemLimit) {
+      L->NS = ns;
+      L->smem = need;
+      return true;
+    }
+  }
+  return false;
+}
+
+template <int DH, int KH, int KW>
+wm_status launch_t(const Params& p, const Layout& L, cudaStream_t s, bool pdl) {
+  auto kern = na_tc_kernel<DH, KH, KW>;   // shared-memory limit set by prepare_na_tc
+  const int grid = std::min(p.ntiles, num_sms());
+  WM_CUDA(launch_pdl(kern, dim3(grid), dim3(kThreads), L.smem, s, pdl, p));
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+}  // namespace natc
+
+bool na_tc_supported(int H, int W, int C, int heads, int kh, int kw, bool periodic) {
+  natc::Layout L;
+  return C % heads == 0 && natc::layout_for(H, W, C / heads, kh, kw, periodic, &L);
+}
+
+wm_status prepare_na_tc() {
+  using namespace natc;
+  WM_CUDA(cudaFuncSetAttribute(na_tc_kernel<32, 5, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+  WM_CUDA(cudaFuncSetAttribute(na_tc_kernel<48, 5, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+  WM_CUDA(cudaFuncSetAttribute(na_tc_kernel<64, 5, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+  WM_CUDA(cudaFuncSetAttribute(na_tc_kernel<32, 7, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+  WM_CUDA(cudaFuncSetAttribute(na_tc_kernel<48, 7, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+  return WM_OK;
+}
+
+wm_status launch_na_tc(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C, int heads,
+                       int kd, int kh, int kw, bool periodic, cudaStream_t s, bool pdl) {
+  using namespace natc;
+  if (B <= 0) return WM_OK;
+  const int dh = C / heads;
+  Layout L;
+  if (C % heads != 0 || !layout_for(H, W, dh, kh, kw, periodic, &L))
+    return fail(WM_ERR_INVALID_ARG, "shape not supported by the tcgen05 attention kernel");
+  if ((reinterpret_cast<uintptr_t>(qkv) | reinterpret_cast<uintptr_t>(out)) & 15)
+    return fail(WM_ERR_INVALID_ARG, "tcgen05 attention needs 16-byte aligned qkv and out");
+  Params p{};
+  p.qkv = qkv;
+  p.out = out;
+  p.status = device_status_word();
+  p.B = B; p.D = D; p.H = H; p.W = W; p.C = C; p.heads = heads; p.kd = kd; p.periodic = periodic ? 1 : 0;
+  p.HR = L.HR; p.NPAD = L.NPAD; p.NKS = L.NKS; p.NS = L.NS;
+  p.colO = L.colO; p.colQ = L.colQ; p.oStride = L.oStride; p.qStride = L.qStride;
+  p.tiles_h = (H + 15) / 16;
+  p.tiles_w = (W + 7) / 8;
+  const long nt = (long)p.tiles_h * p.tiles_w * D * heads * B;
+  if (nt > (1L << 30)) return fail(WM_ERR_INVALID_ARG, "too many attention tiles");
+  p.ntiles = (int)nt;
+  p.scale_log2 = 1.4426950408889634f / sqrtf((float)dh);
+  if (kh == 5 && kw == 5) {
+    if (dh == 32) return launch_t<32, 5, 5>(p, L, s, pdl);
+    if (dh == 48) return launch_t<48, 5, 5>(p, L, s, pdl);
+    if (dh == 64) return launch_t<64, 5, 5>(p, L, s, pdl);
+  } else {
+    if (dh == 32) return launch_t<32, 7, 7>(p, L, s, pdl);
+    if (dh == 48) return launch_t<48, 7, 7>(p, L, s, pdl);
+  }
+  return fail(WM_ERR_INVALID_ARG, "shape not supported by the tcgen05 attention kernel");
+}
+
+}  // namespace wm

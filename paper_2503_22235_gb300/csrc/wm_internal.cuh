@@ -219,6 +219,12 @@ wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
                          int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s, int variant = 0,
                          bool pdl = false);
+// The tcgen05 attention kernel (k_na_tc.cu): whether it supports a shape, and
+// its launch (same inputs and outputs as launch_na_bf16).
+bool na_tc_supported(int H, int W, int C, int heads, int kh, int kw, bool periodic);
+wm_status prepare_na_tc();
+wm_status launch_na_tc(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C, int heads,
+                       int kd, int kh, int kw, bool periodic, cudaStream_t s, bool pdl = false);
 // One line per autotuned attention shape: the plan chosen and its time.
 std::string describe_na_plans();
 // Times the candidate CTA plans of the attention kernel for this exact shape

@@ -180,13 +180,28 @@ def _na_bf16_run(case, variant):
 
 
 NA_VARIANTS = [wm.WM_NA_AUTO] + [fam | kind for fam in (wm.WM_NA_QK_CHUNK8, wm.WM_NA_QK_CHUNK4, wm.WM_NA_KQ)
-                                 for kind in (wm.WM_NA_PER_TILE, wm.WM_NA_PERSISTENT)]
+                                 for kind in (wm.WM_NA_PER_TILE, wm.WM_NA_PERSISTENT)] + [wm.WM_NA_TCGEN05]
+
+
+def _tc_supported(case):
+    """Shapes the tcgen05 kernel takes (include/wm.h, WM_NA_TCGEN05)."""
+    B, D, H, W, C, heads, kd, kh, kw, per = case
+    dh = C // heads
+    win = (kh, kw)
+    if not ((dh in (32, 48) and win in ((5, 5), (7, 7))) or (dh == 64 and win == (5, 5))):
+        return False
+    return min(16 + kh - 1, H) >= kh + 3 and (per or W >= kw + 7)
 
 
 @pytest.mark.parametrize("variant", NA_VARIANTS)
 @pytest.mark.parametrize("case", NA_CASES)
 def test_neighborhood_attention_bf16(case, variant):
     B, C = case[0], case[4]
+    if variant == wm.WM_NA_TCGEN05 and not _tc_supported(case):
+        with pytest.raises(wm.WmError) as e:
+            _na_bf16_run(case, variant)
+        assert e.value.status == wm.WM_ERR_INVALID_ARG
+        return
     out = _na_bf16_run(case, variant)
     # tokens = (query, head) pairs: each head's output is its own softmax average
     assert_close(host(out).reshape(B, -1, C), _na_bf16_ref(case), 1e-2, C // case[5], (case, variant))
@@ -200,6 +215,24 @@ def test_neighborhood_attention_kernel_kind_does_not_change_results(case, fam):
     a = _na_bf16_run(case, fam | wm.WM_NA_PER_TILE)
     b = _na_bf16_run(case, fam | wm.WM_NA_PERSISTENT)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("case", [c for c in NA_CASES if _tc_supported(c)])
+def test_tcgen05_attention_is_batch_independent(case):
+    """A query's result depends only on its own position: the batch-2 launch
+    equals two batch-1 launches bit for bit (the batched serving and ensemble
+    paths rely on it)."""
+    B, D, H, W, C, heads, kd, kh, kw, per = case
+    qkv = torch.from_numpy(_na_inputs(2, D, H, W, C, 9)).to(CUDA, torch.bfloat16)
+    both = torch.empty(2 * D * H * W, C, device=CUDA, dtype=torch.bfloat16)
+    wm.wm_op_neighborhood_attention(qkv, both, 2, D, H, W, C, heads, kd, kh, kw, per, wm.WM_PREC_BF16,
+                                    wm.WM_NA_TCGEN05)
+    for b in range(2):
+        one = torch.empty(D * H * W, C, device=CUDA, dtype=torch.bfloat16)
+        wm.wm_op_neighborhood_attention(qkv[b].contiguous(), one, 1, D, H, W, C, heads, kd, kh, kw, per,
+                                        wm.WM_PREC_BF16, wm.WM_NA_TCGEN05)
+        torch.cuda.synchronize()
+        assert torch.equal(one, both[b * D * H * W:(b + 1) * D * H * W]), b
 
 
 def test_neighborhood_attention_rejects_bad_variants():
@@ -396,7 +429,8 @@ def test_full_size_attention_every_token_against_the_oracle():
         nbr = orc.neighbor_index(D, H, W, s.kd, s.kh, s.kw, True)
         ref = na_oracle_parallel(qb.to(torch.float32).numpy(), C, heads, nbr)
         qd = qb.to(CUDA)
-        for variant in [wm.WM_NA_AUTO] + [fam | wm.WM_NA_PERSISTENT for fam in (wm.WM_NA_QK_CHUNK4, wm.WM_NA_QK_CHUNK8)]:
+        for variant in [wm.WM_NA_AUTO, wm.WM_NA_TCGEN05] + [fam | wm.WM_NA_PERSISTENT
+                                                             for fam in (wm.WM_NA_QK_CHUNK4, wm.WM_NA_QK_CHUNK8)]:
             out = torch.empty(B * s.N, C, device=CUDA, dtype=torch.bfloat16)
             wm.wm_op_neighborhood_attention(qd, out, B, D, H, W, C, heads, s.kd, s.kh, s.kw, 1, wm.WM_PREC_BF16,
                                             variant)
