@@ -199,6 +199,76 @@ def _small_latent_cpu():
             "rollout_336h_s_1_thread": 448 * one, "rollout_336h_s_all_cores": 448 * allc}
 
 
+ORACLE_ROLLOUT_THREADS = 8
+
+
+def start_oracle_rollout(lead=337):
+    """CPU-baseline leg: the FP64 oracle's 14-day rollout of the small latent
+    (4x24x48x128; 56 six-hour + 1 one-hour steps, 452 blocks), timed in a
+    fresh interpreter on ORACLE_ROLLOUT_THREADS host threads while the GPU
+    sections run. Its per-step latents are the reference of the rollout error
+    curve. Returns the running process and the file it writes."""
+    import tempfile
+    fd, path = tempfile.mkstemp(suffix=".npz", prefix="wm_oracle_rollout_")
+    os.close(fd)
+    code = ("import sys, time; sys.path.insert(0, %r); import numpy as np; import synth; "
+            "from oracle import wm_oracle as orc; s = synth.SMALL; p6, p1 = synth.processor_weights(s, seed=0); "
+            "x = synth.latent(s, 1, seed=1); steps = []; t = time.perf_counter(); "
+            "orc.rollout(x, %d, p6, p1, s, per_step=steps); dt = time.perf_counter() - t; "
+            "np.savez(%r, steps=np.stack(steps), seconds=dt)") % (ROOT, lead, path)
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(ORACLE_ROLLOUT_THREADS)
+    proc = subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.DEVNULL,
+                            stderr=subprocess.PIPE, text=True)
+    return proc, path
+
+
+def finish_oracle_rollout(proc, path, timeout=900):
+    """(per-step oracle latents [steps, 1, D, H, W, C] float64, seconds) or (None, error text)."""
+    try:
+        _, err = proc.communicate(timeout=timeout)
+        if proc.returncode != 0:
+            return None, (err or "")[-300:]
+        with np.load(path) as z:
+            return z["steps"], float(z["seconds"])
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        return None, "timed out"
+    finally:
+        if os.path.exists(path):
+            os.remove(path)
+
+
+def rollout_error_curve(wm, torch, dev, oracle_steps, lead=337):
+    """Relative L2 error against the FP64 oracle after every processor step of
+    the 337-hour rollout (small latent; the 336-hour forecast is step 56) in
+    FP32, BF16 and FP8-MLP. Each step runs through wm_processor_step on the
+    device; the comparison is in float64 on the host."""
+    s = synth.SMALL
+    p6, p1 = synth.processor_weights(s, seed=0)
+    n6, n1 = divmod(lead, 6)
+    ctx = wm.wm_create_from_host(wm.make_config(s, wm.WM_PREC_BF16), synth.pack_weights(p6, p1))
+    res = {"workload": f"latent 4x24x48x128, {lead} h = {n6} six-hour + {n1} one-hour steps "
+                       f"({n6 * s.blocks_p6 + n1 * s.blocks_p1} blocks), relative L2 vs the FP64 oracle after each step"}
+    try:
+        for prec, name in ((wm.WM_PREC_FP32, "fp32"), (wm.WM_PREC_BF16, "bf16"), (wm.WM_PREC_BF16_FP8MLP, "fp8mlp")):
+            wm.wm_set_precision(ctx, prec)
+            x = torch.from_numpy(synth.latent(s, 1, seed=1)).to(dev)
+            errs = []
+            for k in range(n6 + n1):
+                wm.wm_processor_step(ctx, x, wm.WM_P6 if k < n6 else wm.WM_P1)
+                got = x.detach().cpu().numpy().astype(np.float64)
+                ref = oracle_steps[k]
+                errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+            res[name] = {"per_step": errs, "after_step_1": errs[0], "final_336h": errs[n6 - 1],
+                         "final_337h": errs[-1], "max": max(errs),
+                         "nonfinite_final": wm.wm_count_nonfinite(x)}
+    finally:
+        wm.wm_destroy(ctx)
+    return res
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle on the host cores. Each step is
     one processor block on a 9 x 7 x 20 latitude band of the full-size latent
@@ -242,6 +312,7 @@ def run_ours(args):
     from paper_2503_22235_gb300 import build as wm_build
 
     ws, rank, local = _dist()
+    oracle_job = start_oracle_rollout() if (rank == 0 and ws == 1 and not args.no_cpu) else None
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
@@ -433,6 +504,14 @@ def run_ours(args):
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_oracle_baseline()
+        steps, info = finish_oracle_rollout(*oracle_job)
+        if steps is None:
+            out["cpu_baseline"]["rollout_337h_small"] = {"error": info}
+        else:
+            out["cpu_baseline"]["rollout_337h_small"] = {
+                "workload": "FP64 oracle rollout, latent 4x24x48x128, 337 h (452 blocks)", "seconds": info,
+                "forecasts_per_s": 1.0 / info, "threads": ORACLE_ROLLOUT_THREADS}
+            out["rollout_error_vs_oracle"] = rollout_error_curve(wm, torch, dev, steps)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
@@ -630,17 +709,21 @@ def hourly_ensemble_bench(wm, torch, dev, full_members=8, reps=2):
     return res
 
 
-def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0, bf16_only=False):
+def serve_bench(wm, torch, n_requests=2000, rate=4.0, seed=0, bf16_only=False, n_other=120):
     """Poisson request stream on the small latent through the continuous-batching server.
 
     Requests: exponential inter-arrivals (mean 1/rate s), lead times uniform in
     1..336 h, latent i seeded by its request index (generated when the request
-    is first needed). Reported per precision: p50/p99 latency (submit ->
-    finished) at the offered rate, forecasts/s closed-loop at saturation
-    (BF16, FP8-MLP and the FP32 plain path); for
-    BF16 also the first half (at most 240) of the requests under an HBM budget
-    of one resident request (later arrivals queue until the slot frees); the
-    BF16-vs-FP32 error of the served results.
+    is first needed). BF16 serves the whole stream (n_requests, 2,000 by
+    default: about 500 s in real time); FP8-MLP and the FP32 plain path serve
+    its first n_other requests. Reported per precision: p50/p99 latency
+    (submit -> finished) at the offered rate, most requests resident at once,
+    the largest batched step and how many steps advanced two or more requests
+    together, and forecasts/s closed-loop at saturation (the first 480 BF16
+    requests submitted at once; the others: 64). For BF16 also the first 240 requests
+    under an HBM budget of one resident request (later arrivals queue until
+    the slot frees); the BF16 and FP8-MLP results' error against FP32 on the
+    requests all three served.
     """
     s = synth.SMALL
     p6, p1 = synth.processor_weights(s, seed=0)
@@ -655,29 +738,37 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0, bf16_only=False):
         return cache[i]
 
     max_batch = 16
-    res = {"workload": (f"Poisson arrivals {rate}/s, {n_requests} requests, leads U{{1..336}} h, latent 4x24x48x128, "
-                        f"P6 8 + P1 4 blocks, max batch {max_batch}")}
+    res = {"workload": (f"Poisson arrivals {rate}/s, {n_requests} requests (BF16; FP8-MLP and FP32: the first "
+                        f"{min(n_other, n_requests)}), leads U{{1..336}} h, latent 4x24x48x128, P6 8 + P1 4 blocks, "
+                        f"max batch {max_batch}")}
     outs = {}
+
+    keep = min(n_other, n_requests)   # results kept for the precision comparison
+    n_sat_bf16 = min(480, n_requests)  # saturated BF16 run: these latents stay cached
 
     def open_loop(srv, n=n_requests):
         t0 = time.perf_counter()
         arrive = np.cumsum(gaps)
-        ids, got = [], {}
+        ids, got, results = [], set(), {}
+        buf = np.empty_like(latent(0))
         i = 0
         while len(got) < n:
             now = time.perf_counter() - t0
             while i < n and arrive[i] <= now:
                 ids.append(wm.wm_server_submit(srv, latent(i), int(leads[i])))
+                if i >= n_sat_bf16:
+                    cache.pop(i, None)        # submit copied it; no later run needs it
                 i += 1
             for j, rid in enumerate(ids):
                 if j in got:
                     continue
-                buf = np.empty_like(latent(0))
                 done, _ = wm.wm_server_poll(srv, rid, buf)
                 if done:
-                    got[j] = buf
+                    got.add(j)
+                    if j < keep:
+                        results[j] = buf.copy()
             time.sleep(0.0005)
-        return got, wm.wm_server_stats(srv)
+        return results, wm.wm_server_stats(srv)
 
     precs = ((wm.WM_PREC_BF16, "bf16"),) if bf16_only else ((wm.WM_PREC_BF16, "bf16"),
                                                             (wm.WM_PREC_BF16_FP8MLP, "fp8mlp"),
@@ -688,16 +779,20 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0, bf16_only=False):
         budget = ws + (max_batch + 64) * lat_floats * 4   # 64 resident request slots
         try:
             # ---- open loop at the offered rate
+            n_open = n_requests if name == "bf16" else min(n_other, n_requests)
             srv = wm.wm_server_start(ctx, budget, max_batch)
             try:
-                got, st = open_loop(srv)
+                got, st = open_loop(srv, n_open)
             finally:
                 wm.wm_server_stop(srv)
             outs[name] = got
+            res[f"{name}_requests"] = n_open
             res[f"{name}_p50_ms"] = st["p50_ms"]
             res[f"{name}_p99_ms"] = st["p99_ms"]
             res[f"{name}_open_loop_forecasts_per_s"] = st["forecasts_per_s"]
             res[f"{name}_max_resident"] = st["max_active"]
+            res[f"{name}_max_step_batch"] = st["max_step_batch"]
+            res[f"{name}_multi_request_steps"] = st["multi_request_steps"]
             if name == "bf16":
                 # ---- the stream's start with room for one resident request: arrivals queue
                 small = ws + (max_batch + 1) * lat_floats * 4
@@ -711,9 +806,10 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0, bf16_only=False):
                 res["bf16_budget1_p50_ms"] = st["p50_ms"]
                 res["bf16_budget1_p99_ms"] = st["p99_ms"]
                 res["bf16_budget1_max_resident"] = st["max_active"]
+                res["bf16_budget1_max_step_batch"] = st["max_step_batch"]
                 res["hbm_budget_bytes"] = {"default": int(budget), "small": int(small)}
             # ---- closed loop: all requests at once, throughput at saturation
-            n_sat = min(64, n_requests) if not bf16_only else n_requests
+            n_sat = n_sat_bf16 if name == "bf16" else min(64, n_requests)
             srv = wm.wm_server_start(ctx, budget, max_batch)
             try:
                 t0 = time.perf_counter()
@@ -726,17 +822,22 @@ def serve_bench(wm, torch, n_requests=120, rate=4.0, seed=0, bf16_only=False):
                             left.discard(rid)
                     time.sleep(0.0005)
                 dt = time.perf_counter() - t0
+                sst = wm.wm_server_stats(srv)
             finally:
                 wm.wm_server_stop(srv)
             res[f"{name}_saturated_forecasts_per_s"] = n_sat / dt
             res[f"{name}_saturated_requests"] = n_sat
+            res[f"{name}_saturated_max_resident"] = sst["max_active"]
+            res[f"{name}_saturated_max_step_batch"] = sst["max_step_batch"]
+            res[f"{name}_saturated_multi_request_steps"] = sst["multi_request_steps"]
         finally:
             wm.wm_destroy(ctx)
     if bf16_only:
         return res
+    common = sorted(set(outs["bf16"]) & set(outs["fp8mlp"]) & set(outs["fp32"]))
     for name in ("bf16", "fp8mlp"):
         errs = [float(np.linalg.norm(outs[name][j].astype(np.float64) - outs["fp32"][j]) /
-                      np.linalg.norm(outs["fp32"][j].astype(np.float64))) for j in range(n_requests)]
+                      np.linalg.norm(outs["fp32"][j].astype(np.float64))) for j in common]
         res[f"{name}_vs_fp32_rel_l2_median"] = float(np.median(errs))
         res[f"{name}_vs_fp32_rel_l2_max"] = float(np.max(errs))
     return res
@@ -755,7 +856,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fields", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-bf16-only", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

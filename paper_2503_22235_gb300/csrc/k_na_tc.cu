@@ -29,14 +29,17 @@
 //              bf16 pairs over the first half of its S columns, and zeros
 //              in the key rows its window does not reach. They also copy
 //              the next tile's queries into tensor memory (the A operand of
-//              Q K^T) and write each finished tile's O / l to global memory.
+//              Q K^T; loaded one step ahead) and write each finished tile's
+//              O / l to global memory one step into the next tile.
 //   warp 4     MMA issuer (one thread): QK(step + 2) is issued right after
 //              PV(step), so the other S buffer's softmax overlaps both.
 //   warps 5-7  loaders: cp.async 16-byte copies of the K/V slabs into a ring
-//              of NS stages, in a layout the MMA reads without swizzle:
-//              [K or V][half][channel chunk of 8][key][8 channels] with the
-//              chunk stride NKS = NPAD + 1 keys (conflict-free shared-memory
-//              stores; keys past HR * 8 are zero).
+//              of NS stages. Layout of one (K or V, half): [group of 8 keys]
+//              [16-channel atom][8 keys x 32 bytes] with the 32-byte swizzle
+//              (the two 16-byte units of keys 4..7 of a group swap places),
+//              which K (the K-major B operand of Q K^T: one atom per MMA) and
+//              V (the MN-major B operand of P V: atoms along N) share. Keys
+//              past HR * 8 and the spare slab columns stay zero.
 // Tensor memory (512 columns): S0, S1 (NPAD each), O0, O1 (dh each), Q0, Q1
 // (dh / 2 each, bf16 pairs). Every mbarrier wait is bounded in time; on a
 // timeout the CTA records WM_ERR_TIMEOUT, drains its own copies and MMAs,
@@ -63,7 +66,6 @@ struct Params {
   int B, D, H, W, C, heads, kd, periodic;
   int HR;      // key rows of a slab
   int NPAD;    // keys of a half as the MMA reads them (HR * 8 rounded up to 16)
-  int NKS;     // keys per channel chunk in shared memory (NPAD + 1)
   int NS;      // slab stages
   int tiles_h, tiles_w, ntiles;
   int colO, colQ;   // tensor-memory columns of O0 (O1 = +oStride) and Q0 (Q1 = +qStride)
@@ -99,13 +101,15 @@ __device__ __forceinline__ TileGeo tile_geo(const Params& p, int t) {
   return g;
 }
 
-// Shared-memory matrix descriptor without swizzle: core matrices of 8 rows x
-// 16 bytes stored contiguously; lbo = byte distance between core matrices
-// adjacent along K, sbo = along M/N (both for K-major and, in this layout
-// type, for MN-major operands).
-__device__ __forceinline__ uint64_t desc_noswz(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor, 32-byte swizzle (layout type 6): rows of
+// 32 bytes, 8-row groups. lbo, sbo: byte strides between atoms along the two
+// dimensions as the tensor core reads them (for K-major operands sbo is the
+// 8-row group stride along M/N and lbo is unused; for MN-major operands lbo is
+// the stride between 16-element atoms along M/N and sbo the 8-row group
+// stride along K).
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-         ((uint64_t)1 << 46);
+         ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
 }
 
 // Instruction descriptor, kind::f16: D f32, A and B bf16, A K-major, B K-major
@@ -141,30 +145,42 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Byte offset of (stage, K/V, half, chunk, key) in the slab ring.
-__device__ __forceinline__ uint32_t slab_off(const Params& p, int DHC, int stage, int kv, int h, int chunk, int key) {
-  return ((uint32_t)(((stage * 4 + kv * 2 + h) * DHC + chunk) * p.NKS + key)) * 16u;
+// Byte offset of the (stage, K or V, half) region in the slab ring; NA =
+// 16-channel atoms per head. A region is NPAD / 8 groups of NA atoms of
+// 8 keys x 32 bytes.
+__device__ __forceinline__ uint32_t region_off(const Params& p, int NA, int stage, int kv, int h) {
+  return (uint32_t)((stage * 4 + kv * 2 + h) * NA * p.NPAD) * 32u;
 }
 
-// Softmax warps: copy this lane's query of tile ti into tensor-memory Q
-// buffer ti & 1 (bf16 pairs, the A operand of Q K^T). Out of line: it runs
-// once per tile and keeps the step loop's registers free.
+// Softmax warps: this lane's query of tile ti (its dh channels as bf16
+// pairs) from global memory into registers. Issued one step before the
+// tensor-memory store, so the load latency is hidden behind a softmax step.
 template <int DH, int KH, int KW>
-__device__ __noinline__ bool softmax_write_q(const Params& p, int ti, int q, int lane, uint32_t lane_base,
-                                             uint64_t* q_empty, uint64_t* q_full, volatile int* abort_flag) {
-  // the wait's outcome is made warp-uniform: the tcgen05 stores below are warp-collective
-  if (!__all_sync(0xffffffffu, mbar_wait(&q_empty[ti & 1], ((uint32_t)(ti >> 1) & 1u) ^ 1u, abort_flag)))
-    return false;
-  tc_fence_after();
+__device__ __forceinline__ void softmax_load_q(const Params& p, int ti, int q, int lane, uint4 (&x)[DH / 8]) {
   const TileGeo G = tile_geo<KH, KW>(p, blockIdx.x + ti * gridDim.x);
   const int a = min(G.h0 + 4 * q + (lane >> 3), p.H - 1), w = min(G.w0 + (lane & 7), p.W - 1);
   const long tok = ((long)(G.b * p.D + G.d) * p.H + a) * p.W + w;
   const uint4* src = reinterpret_cast<const uint4*>(p.qkv + tok * (3L * p.C) + (long)G.head * DH);
+#pragma unroll
+  for (int c = 0; c < DH / 8; ++c) x[c] = __ldg(src + c);
+}
+
+// Softmax warps: the prefetched query into tensor-memory Q buffer ti & 1
+// (the A operand of Q K^T), once the tile that used that buffer before has
+// issued its last Q K^T.
+template <int DH>
+__device__ __forceinline__ bool softmax_store_q(const Params& p, int ti, int lane, uint32_t lane_base,
+                                                const uint4 (&x)[DH / 8], uint64_t* q_empty, uint64_t* q_full,
+                                                volatile int* abort_flag) {
+  // the wait's outcome is made warp-uniform: the tcgen05 stores below are warp-collective
+  if (!__all_sync(0xffffffffu, mbar_wait(&q_empty[ti & 1], ((uint32_t)(ti >> 1) & 1u) ^ 1u, abort_flag)))
+    return false;
+  tc_fence_after();
   const uint32_t qcol = lane_base + (uint32_t)(p.colQ + (ti & 1) * p.qStride);
 #pragma unroll
   for (int c = 0; c < DH / 16; ++c) {   // 16 channels = 8 columns per store
-    const uint4 x0 = __ldg(src + 2 * c), x1 = __ldg(src + 2 * c + 1);
-    const uint32_t r[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    const uint32_t r[8] = {x[2 * c].x, x[2 * c].y, x[2 * c].z, x[2 * c].w,
+                           x[2 * c + 1].x, x[2 * c + 1].y, x[2 * c + 1].z, x[2 * c + 1].w};
     tmem_st8(qcol + 8u * c, r);
   }
   tmem_wait_st();
@@ -212,7 +228,7 @@ __device__ __noinline__ bool softmax_epilogue(const Params& p, int ti, int lane,
 
 template <int DH, int KH, int KW>
 __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
-  constexpr int DHC = DH / 8;       // 16-byte channel chunks per head
+  constexpr int NA = DH / 16;       // 16-channel (32-byte) atoms per head
   constexpr int WR = KH + 3;        // key rows a softmax warp reads
   constexpr int RH = KH / 2, RW = KW / 2;
   static_assert(DH % 16 == 0 && DH <= 64, "head dim");
@@ -254,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
   // chunk, and the spare slab columns kw + 7 .. 15): masked scores, zero P,
   // so they must hold finite values. Zero the whole ring once.
   {
-    const int items = p.NS * 4 * DHC * p.NKS;
+    const int items = p.NS * 4 * NA * p.NPAD * 2;   // 16-byte units
     for (int i = threadIdx.x; i < items; i += blockDim.x)
       *reinterpret_cast<uint4*>(smem + (uint32_t)i * 16u) = make_uint4(0, 0, 0, 0);
     fence_async_smem();
@@ -279,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
       // ------------------------------------------------------------ MMA issuer
       constexpr uint32_t idesc_pv = idesc_bf16_ab(128, DH, 1);
       const uint32_t idesc_qk = idesc_bf16_ab(128, p.NPAD, 0);
-      const uint32_t chunk_bytes = (uint32_t)p.NKS * 16u;
+      const uint32_t group_bytes = (uint32_t)NA * 256u;   // 8 keys x all atoms
       auto issue_qk = [&](int v) -> bool {
         const int ti = v / steps_per_tile, r = v - ti * steps_per_tile, l = r >> 1, h = r & 1;
         const int g = ti * p.kd + l, stage = g % p.NS;
@@ -288,10 +304,10 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
         tc_fence_after();
         const uint32_t d = tmem + colS(v & 1);
         const uint32_t a = tmem + (uint32_t)(p.colQ + (ti & 1) * p.qStride);
-        const uint32_t kb = sbase + slab_off(p, DHC, stage, 0, h, 0, 0);
+        const uint32_t kb = sbase + region_off(p, NA, stage, 0, h);
 #pragma unroll
-        for (int k = 0; k < DH / 16; ++k)   // 16 channels = 2 chunks per MMA
-          umma_ts(d, a + 8u * k, desc_noswz(kb + 2u * k * chunk_bytes, chunk_bytes, 128u), idesc_qk, k > 0);
+        for (int k = 0; k < NA; ++k)   // one 16-channel atom per MMA
+          umma_ts(d, a + 8u * k, desc_sw32(kb + 256u * k, 16u, group_bytes), idesc_qk, k > 0);
         umma_commit(&s_full[v & 1]);
         if (r == steps_per_tile - 1) umma_commit(&q_empty[ti & 1]);
         return true;
@@ -304,10 +320,11 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(p.colO + (ti & 1) * p.oStride);
         const uint32_t a = tmem + colS(u & 1);
-        const uint32_t vb = sbase + slab_off(p, DHC, stage, 1, h, 0, 0);
+        const uint32_t vb = sbase + region_off(p, NA, stage, 1, h);
         const int nk = p.NPAD / 16;
-        for (int k = 0; k < nk; ++k)       // 16 keys = 2 core matrices per MMA
-          umma_ts(d, a + 8u * k, desc_noswz(vb + 256u * k, 128u, chunk_bytes), idesc_pv, (r > 0 || k > 0) ? 1u : 0u);
+        for (int k = 0; k < nk; ++k)       // 16 keys = 2 groups per MMA
+          umma_ts(d, a + 8u * k, desc_sw32(vb + 2u * group_bytes * k, 256u, group_bytes), idesc_pv,
+                  (r > 0 || k > 0) ? 1u : 0u);
         umma_commit(&pv_done[u & 1]);
         if (h == 1) umma_commit(&kv_empty[stage]);
         if (r == steps_per_tile - 1) umma_commit(&o_full[ti & 1]);
@@ -330,29 +347,31 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
     }
   } else if (warp > kMmaWarp) {
     // --------------------------------------------------------------- loaders
-    // lane = (column parity, K or V, channel chunk): one instruction copies 2
-    // longitude columns x K and V x the head's chunks of one slab row.
+    // lane = (atom, key of a quad, 16-byte unit): one instruction copies 4
+    // consecutive keys (longitude columns) x the head's channels of K or V;
+    // its 8-lane phases each write 4 keys x 32 bytes = 128 contiguous bytes.
     const int lw = warp - kMmaWarp - 1;
-    const int colpar = lane >> 4, kv = (lane >> 3) & 1, c8 = lane & 7;
-    const bool active = c8 < DHC;
+    const int la = lane >> 3, rk = (lane >> 1) & 3, lu = lane & 1;
+    const bool active = la < NA;
     const long C3 = 3L * p.C;
     bool ok = true;
     int g = 0, prev_stage = -1;
     for (int ti = 0; ti < my_tiles && ok; ++ti) {
       const TileGeo G = tile_geo<KH, KW>(p, blockIdx.x + ti * gridDim.x);
-      int lonoff[8];
+      int lonoff[4];   // slab column 4 hq + rk (hq = 2 half + quad)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        int lon = G.s_lon + 2 * j + colpar;
+      for (int hq = 0; hq < 4; ++hq) {
+        int lon = G.s_lon + 4 * hq + rk;
         if (p.periodic) {
           lon %= p.W;
           if (lon < 0) lon += p.W;
         } else {
-          lon = min(lon, p.W - 1);   // spare columns past the grid: any finite data (masked)
+          lon = min(lon, p.W - 1);   // columns past the grid are never loaded (spare) or masked
         }
-        lonoff[j] = lon * (int)C3;
+        lonoff[hq] = lon * (int)C3;
       }
-      const __nv_bfloat16* head_base = p.qkv + (long)(1 + kv) * p.C + (long)G.head * DH + c8 * 8;   // K or V
+      const __nv_bfloat16* chan = p.qkv + (long)G.head * DH + la * 16 + lu * 8;
+      const uint32_t lane_dst = (uint32_t)(la * 256 + rk * 32);
       for (int l = 0; l < p.kd; ++l, ++g) {
         const int stage = g % p.NS;
         if (!mbar_wait(&kv_empty[stage], ((uint32_t)(g / p.NS) & 1u) ^ 1u, &abort_flag)) {
@@ -360,18 +379,20 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
           break;
         }
         const long lev = (long)G.b * p.D + G.ld0 + l;
-        const __nv_bfloat16* row0 = head_base + ((lev * p.H + G.s_lat) * p.W) * C3;
-        const uint32_t d0 = sbase + slab_off(p, DHC, stage, kv, 0, c8, colpar);
-        const uint32_t d1 = sbase + slab_off(p, DHC, stage, kv, 1, c8, colpar);
+        const __nv_bfloat16* row0 = chan + ((lev * p.H + G.s_lat) * p.W) * C3;
         if (active) {
           for (int r = lw; r < p.HR; r += kLoadWarps) {
             const __nv_bfloat16* src = row0 + (long)r * p.W * C3;
-            const uint32_t o = (uint32_t)r * 128u;   // 8 keys of 16 bytes per slab row
+            const uint32_t rdst = sbase + lane_dst + (uint32_t)r * (uint32_t)(NA * 256);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) cp_async16(d0 + o + 32u * j, src + lonoff[j]);
-            // half 1: columns 8 .. kw + 6 (the spare columns stay zero)
+            for (int kv = 0; kv < 2; ++kv)
 #pragma unroll
-            for (int j = 0; j < (KW + 7) / 2 - 4; ++j) cp_async16(d1 + o + 32u * j, src + lonoff[4 + j]);
+              for (int hq = 0; hq < 4; ++hq) {
+                const int h = hq >> 1, qd = hq & 1;
+                if (4 * hq + rk < KW + 7)   // spare columns stay zero
+                  cp_async16(rdst + region_off(p, NA, stage, kv, h) + (uint32_t)(qd * 128 + ((lu ^ qd) << 4)),
+                             src + lonoff[hq] + (long)(1 + kv) * p.C);
+              }
           }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -399,10 +420,13 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
     const uint64_t scale2 = pack_f2(p.scale_log2, p.scale_log2);
     const uint64_t neg2 = pack_f2(-INFINITY, -INFINITY);
-    const long C3 = 3L * p.C;
     bool ok = true;
 
-    if (my_tiles > 0) ok = softmax_write_q<DH, KH, KW>(p, 0, q, lane, lane_base, q_empty, q_full, &abort_flag);
+    uint4 qnext[DH / 8];   // the next tile's query, prefetched one step before its store
+    if (my_tiles > 0) {
+      softmax_load_q<DH, KH, KW>(p, 0, q, lane, qnext);
+      ok = softmax_store_q<DH>(p, 0, lane, lane_base, qnext, q_empty, q_full, &abort_flag);
+    }
     float prev_l = 1.f;
     long prev_orow = 0;
     bool prev_valid = false;
@@ -539,13 +563,14 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&p_ready[u & 1]);
-        if (r == 0) {
-          // the previous tile's output, and the next tile's queries, while
-          // this tile's second step is computed
+        // the next tile's queries: loaded after step 0, stored after step 1;
+        // the previous tile's output after step 1 (its last P V is done by then)
+        if (r == 0 && ti + 1 < my_tiles) softmax_load_q<DH, KH, KW>(p, ti + 1, q, lane, qnext);
+        if (r == 1) {
           if (ti > 0 && !softmax_epilogue<DH>(p, ti - 1, lane, lane_base, prev_l, prev_orow, prev_valid, o_full,
                                               o_empty, &abort_flag)) { ok = false; break; }
           if (ti + 1 < my_tiles &&
-              !softmax_write_q<DH, KH, KW>(p, ti + 1, q, lane, lane_base, q_empty, q_full, &abort_flag)) {
+              !softmax_store_q<DH>(p, ti + 1, lane, lane_base, qnext, q_empty, q_full, &abort_flag)) {
             ok = false;
             break;
           }
@@ -577,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
 constexpr int kSmemLimit = 226 * 1024;   // dynamic shared memory; the rest of the 227 KB is static (barriers)
 
 struct Layout {
-  int HR, NPAD, NKS, NS, colO, colQ, oStride, qStride;
+  int HR, NPAD, NS, colO, colQ, oStride, qStride;
   size_t smem;
 };
 
@@ -593,19 +618,17 @@ bool layout_for(int H, int W, int dh, int kh, int kw, bool periodic, Layout* L) 
   if (!periodic && W < kw + 7) return false;
   L->NPAD = round_up(L->HR * 8, 16);
   if (L->NPAD > 256) return false;
-  L->NKS = L->NPAD + 1;
   L->oStride = round_up(dh, 16);
   L->qStride = round_up(dh / 2, 16);
   L->colO = 2 * L->NPAD;
   L->colQ = L->colO + 2 * L->oStride;
   if (L->colQ + 2 * L->qStride > 512) return false;
-  const size_t stage = (size_t)4 * (dh / 8) * L->NKS * 16;
-  // room for the stages; and, from the last K region, for the whole span a
-  // K-major descriptor can address, so no read leaves the allocation
+  const size_t stage = (size_t)4 * (dh / 16) * L->NPAD * 32;
+  // + 1024 bytes to align the base, + 1024 bytes past the last stage: a P V
+  // descriptor read with the two strides interchanged would end at most 512
+  // bytes past its region, so even that stays inside the allocation
   for (int ns = kMaxStages; ns >= 2; --ns) {
-    const size_t k_last = (size_t)(ns - 1) * stage + (size_t)(dh / 8) * L->NKS * 16;
-    const size_t span = (size_t)(L->NPAD / 8) * L->NKS * 16 + 1024;
-    const size_t need = std::max((size_t)ns * stage, k_last + span) + 1024;
+    const size_t need = (size_t)ns * stage + 2048;
     if (need <= (size_t)kSmemLimit) {
       L->NS = ns;
       L->smem = need;
@@ -656,7 +679,7 @@ wm_status launch_na_tc(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int 
   p.out = out;
   p.status = device_status_word();
   p.B = B; p.D = D; p.H = H; p.W = W; p.C = C; p.heads = heads; p.kd = kd; p.periodic = periodic ? 1 : 0;
-  p.HR = L.HR; p.NPAD = L.NPAD; p.NKS = L.NKS; p.NS = L.NS;
+  p.HR = L.HR; p.NPAD = L.NPAD; p.NS = L.NS;
   p.colO = L.colO; p.colQ = L.colQ; p.oStride = L.oStride; p.qStride = L.qStride;
   p.tiles_h = (H + 15) / 16;
   p.tiles_w = (W + 7) / 8;
