@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -141,6 +142,8 @@ void free_workspace(wm_ctx* ctx) {
   ctx->cap32 = ctx->cap16 = 0;
 }
 
+wm_status tune_block_gemms(wm_ctx* ctx, int batch);
+
 // Grow the workspace of one precision family to hold `batch` latents. Never
 // called during capture; growing invalidates captured graphs (they hold
 // workspace addresses).
@@ -212,6 +215,7 @@ wm_status ensure_workspace(wm_ctx* ctx, int batch, bool fp32) {
         !wm::make_tmap_out(&ctx->tmc_qkv, ctx->h_qkv, M, 3 * C, false) ||
         !wm::make_tmap_out(&ctx->tmc_h, ctx->h_h, M, 4 * C, false))
       return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspace");
+    if (check_bf16_shape(ctx->cfg) == WM_OK) WM_TRY(tune_block_gemms(ctx, batch));
   }
   return WM_OK;
 }
@@ -237,6 +241,189 @@ int pick_bn(long M, int N) {
   // wide tiles only when they still fill every SM at least once
   if (N % 256 == 0 && ((M + 127) / 128) * (N / 256) >= wm::num_sms()) return 256;
   return 128;
+}
+
+// ---- GEMM tile autotuner
+// Tile width BN (128 or 256 output columns) and, for the residual epilogue,
+// one or two staging tiles, chosen per GEMM of the block by timing every
+// candidate when a context's BF16 workspace is allocated. BN changes no
+// output of the LayerNorm-folded and GELU epilogues (every element's K sum
+// runs in the same order), so those are tuned per row count. The residual
+// epilogue writes one LayerNorm partial per half tile, so its BN fixes how a
+// row's statistics are split and merged: it is tuned once per (N, K,
+// operand type) and kept for every batch size, so that batched results stay
+// identical to single-latent results. Untuned shapes take pick_bn.
+struct GemmPick {
+  int bn = 0, dual = -1;
+  double ms = 0.0;
+};
+using GemmKey = std::array<long, 5>;   // rows (-1 for the residual epilogue), N, K, epilogue, e4m3
+std::mutex g_gemm_mu;
+std::map<GemmKey, GemmPick> g_gemm_picks;
+std::string g_gemm_log;
+
+GemmKey gemm_key(long M, int N, int K, int epi, bool f8) {
+  return GemmKey{epi == wm::EPI_RESID_LN ? -1L : M, (long)N, (long)K, (long)epi, f8 ? 1L : 0L};
+}
+
+GemmPick pick_gemm(long M, int N, int K, int epi, bool f8) {
+  {
+    std::lock_guard<std::mutex> lk(g_gemm_mu);
+    auto it = g_gemm_picks.find(gemm_key(M, N, K, epi, f8));
+    if (it != g_gemm_picks.end()) return it->second;
+  }
+  GemmPick g;
+  g.bn = pick_bn(M, N);
+  return g;
+}
+
+// Times the candidates of one GEMM (a: every field but bn / dual / tmB set;
+// tmB[0], tmB[1]: the W map for BN = 128 and 256) and records the fastest.
+wm_status tune_gemm(wm::GemmArgs a, const CUtensorMap (&tmB)[2], const char* name, cudaStream_t s) {
+  const GemmKey key = gemm_key(a.M, a.N, a.K, a.epi, a.f8);
+  {
+    std::lock_guard<std::mutex> lk(g_gemm_mu);
+    if (g_gemm_picks.count(key)) return WM_OK;   // residual epilogue: fixed at its first tuning
+  }
+  cudaEvent_t e0, e1;
+  WM_CUDA(cudaEventCreate(&e0));
+  WM_CUDA(cudaEventCreate(&e1));
+  GemmPick best;
+  best.ms = 1e30;
+  wm_status st = WM_OK;
+  for (int bn : {128, 256}) {
+    if (a.epi == wm::EPI_RESID_LN && a.N % bn != 0) continue;
+    for (int dual : {0, 1}) {
+      if (a.epi != wm::EPI_RESID_LN && dual == 1) continue;
+      a.bn = bn;
+      a.dual = a.epi == wm::EPI_RESID_LN ? dual : -1;
+      a.tmB = tmB[bn == 256];
+      st = wm::launch_gemm_tc(a, s);
+      if (st != WM_OK) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3 && st == WM_OK; ++r) st = wm::launch_gemm_tc(a, s);
+      cudaEventRecord(e1, s);
+      if (st != WM_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = fail(WM_ERR_CUDA, "GEMM autotune synchronisation failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      char line[200];
+      std::snprintf(line, sizeof line, "  candidate %s M=%d N=%d K=%d BN=%d staging=%s: %.4f ms\n", name, a.M, a.N,
+                    a.K, bn, a.epi == wm::EPI_RESID_LN ? (dual ? "two" : "one") : "-", ms / 3.0);
+      {
+        std::lock_guard<std::mutex> lk(g_gemm_mu);
+        g_gemm_log += line;
+      }
+      if (ms / 3.0 < best.ms) {
+        best.ms = ms / 3.0;
+        best.bn = bn;
+        best.dual = a.dual;
+      }
+    }
+    if (st != WM_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != WM_OK) return st;
+  if (best.bn) {
+    std::lock_guard<std::mutex> lk(g_gemm_mu);
+    g_gemm_picks[key] = best;
+  }
+  return WM_OK;
+}
+
+std::string describe_gemm_plans() {
+  std::lock_guard<std::mutex> lk(g_gemm_mu);
+  static const char* const names[] = {"store", "gelu", "resid", "store_f32", "gelu_e4m3", "resid_ln", "ln_store",
+                                      "ln_gelu"};
+  std::string out;
+  for (const auto& kv : g_gemm_picks) {
+    const GemmKey& k = kv.first;
+    char line[200];
+    std::snprintf(line, sizeof line, "gemm rows=%s N=%ld K=%ld epilogue=%s%s -> BN=%d staging=%s %.4f ms\n",
+                  k[0] < 0 ? "any" : std::to_string(k[0]).c_str(), k[1], k[2], names[k[3]], k[4] ? " e4m3" : "",
+                  kv.second.bn, kv.second.dual < 0 ? "-" : (kv.second.dual ? "two" : "one"), kv.second.ms);
+    out += line;
+  }
+  return out + g_gemm_log;
+}
+
+// Time the tile candidates of the block's GEMMs (QKV, output projection,
+// FC1, FC2 and the e4m3 FC1 / FC2) at `batch` latents with the first
+// six-hour block's weights, on the workspace and a scratch residual; the
+// outputs are discarded.
+wm_status tune_block_gemms(wm_ctx* ctx, int batch) {
+  const wm_config& c = ctx->cfg;
+  const BlockW& w = ctx->blk[0][0];
+  const long M = (long)batch * ctx->N;
+  const int C = c.C;
+  float* xt = nullptr;
+  if (cudaMalloc(&xt, (size_t)M * C * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(WM_ERR_OOM, "GEMM autotune scratch allocation failed");
+  }
+  wm_status st = WM_OK;
+  auto chk = [&](wm_status x) { if (st == WM_OK) st = x; };
+  const size_t np_max = 2 * ((C + 127) / 128);
+  if (cudaMemset(xt, 0, (size_t)M * C * 4) != cudaSuccess ||
+      cudaMemset(ctx->stats, 0, (size_t)M * np_max * 2 * 4) != cudaSuccess)
+    st = fail(WM_ERR_CUDA, "GEMM autotune scratch clear failed");
+  CUtensorMap tm_x;
+  if (st == WM_OK && !wm::make_tmap_out(&tm_x, xt, (uint64_t)M, (uint64_t)C, true))
+    st = fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the autotune scratch");
+  if (st == WM_OK) {
+    wm::GemmArgs a;
+    a.M = (int)M; a.K = C; a.N = 3 * C;
+    a.tmA = ctx->tm_xb; a.tmC = ctx->tmc_qkv;
+    a.bias = w.bb_qkv; a.colsum = w.cs_qkv; a.stats = ctx->stats; a.np = 1; a.eps = c.ln_eps;
+    a.epi = wm::EPI_LNF_STORE;
+    chk(tune_gemm(a, w.tm_fqkv, "qkv", 0));
+    a = wm::GemmArgs();
+    a.M = (int)M; a.K = C; a.N = C;
+    a.tmA = ctx->tm_o; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
+    a.bias = w.bo; a.x = xt; a.stats = ctx->stats;
+    a.epi = wm::EPI_RESID_LN;
+    chk(tune_gemm(a, w.tm_o, "proj", 0));
+    a = wm::GemmArgs();
+    a.M = (int)M; a.K = C; a.N = 4 * C;
+    a.tmA = ctx->tm_xb; a.tmC = ctx->tmc_h;
+    a.bias = w.bb_1; a.colsum = w.cs_1; a.stats = ctx->stats; a.np = 1; a.eps = c.ln_eps;
+    a.epi = wm::EPI_LNF_GELU;
+    chk(tune_gemm(a, w.tm_f1, "fc1", 0));
+    a = wm::GemmArgs();
+    a.M = (int)M; a.K = 4 * C; a.N = C;
+    a.tmA = ctx->tm_h; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
+    a.bias = w.b2; a.x = xt; a.stats = ctx->stats;
+    a.epi = wm::EPI_RESID_LN;
+    chk(tune_gemm(a, w.tm_2, "fc2", 0));
+    if (C == 128 || C == 256 || C == 384 || C == 512 || C == 768 || C == 1024) {
+      a = wm::GemmArgs();
+      a.f8 = true;
+      a.M = (int)M; a.K = C; a.N = 4 * C;
+      a.tmA = ctx->tm_qu; a.tmC = ctx->tmc_qh;
+      a.bias = w.b1; a.epi = wm::EPI_GELU_F8; a.alpha = w.s_u * w.s_w1; a.out_scale = 1.f / w.s_h;
+      chk(tune_gemm(a, w.tm_q1, "fc1_e4m3", 0));
+      a = wm::GemmArgs();
+      a.f8 = true;
+      a.M = (int)M; a.K = 4 * C; a.N = C;
+      a.tmA = ctx->tm_qh; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
+      a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.alpha = w.s_h * w.s_w2; a.x = xt; a.stats = ctx->stats;
+      chk(tune_gemm(a, w.tm_q2, "fc2_e4m3", 0));
+    }
+  }
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (st == WM_OK && e != cudaSuccess) st = wm::cuda_fail(e, "GEMM autotune");
+  cudaFree(xt);
+  return st;
+}
+
+void set_tile(wm::GemmArgs& a, long M, int epi, bool f8) {
+  const GemmPick g = pick_gemm(M, a.N, a.K, epi, f8);
+  a.bn = g.bn;
+  a.dual = g.dual;
 }
 
 // ---- optional per-launch timing: an event pair around each hot-path kernel
@@ -306,7 +493,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   a.M = (int)M;
   a.K = C;
   a.N = 3 * C;
-  a.bn = pick_bn(M, a.N);
+  set_tile(a, M, wm::EPI_LNF_STORE, false);
   a.tmA = ctx->tm_xb; a.tmB = w.tm_fqkv[a.bn == 256]; a.tmC = ctx->tmc_qkv;
   a.bias = w.bb_qkv; a.colsum = w.cs_qkv; a.stats = ctx->stats; a.np = ctx->np_next; a.eps = c.ln_eps;
   a.epi = wm::EPI_LNF_STORE;
@@ -318,7 +505,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   // output projection + residual; in BF16 it also leaves LayerNorm 2's statistics
   a = wm::GemmArgs();
   a.M = (int)M; a.K = C; a.N = C;
-  a.bn = pick_bn(M, a.N);
+  set_tile(a, M, fp8 ? wm::EPI_RESID_F32 : wm::EPI_RESID_LN, false);
   a.tmA = ctx->tm_o; a.tmB = w.tm_o[a.bn == 256]; a.tmC = tm_x;
   a.bias = w.bo;
   if (fp8) {
@@ -337,14 +524,14 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
     a = wm::GemmArgs();
     a.f8 = true;
     a.M = (int)M; a.K = C; a.N = 4 * C;
-    a.bn = pick_bn(M, a.N);
+    set_tile(a, M, wm::EPI_GELU_F8, true);
     a.tmA = ctx->tm_qu; a.tmB = w.tm_q1[a.bn == 256]; a.tmC = ctx->tmc_qh;
     a.bias = w.b1; a.epi = wm::EPI_GELU_F8; a.alpha = w.s_u * w.s_w1; a.out_scale = 1.f / w.s_h;
     { TimedLaunch t(ctx, WM_K_FC1, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
     a = wm::GemmArgs();
     a.f8 = true;
     a.M = (int)M; a.K = 4 * C; a.N = C;
-    a.bn = pick_bn(M, a.N);
+    set_tile(a, M, wm::EPI_RESID_LN, true);
     a.tmA = ctx->tm_qh; a.tmB = w.tm_q2[a.bn == 256]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
     a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.alpha = w.s_h * w.s_w2; a.x = x; a.stats = ctx->stats;
     { TimedLaunch t(ctx, WM_K_FC2, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
@@ -354,7 +541,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   // LayerNorm 2 folded into FC1 (+ GELU)
   a = wm::GemmArgs();
   a.M = (int)M; a.K = C; a.N = 4 * C;
-  a.bn = pick_bn(M, a.N);
+  set_tile(a, M, wm::EPI_LNF_GELU, false);
   a.tmA = ctx->tm_xb; a.tmB = w.tm_f1[a.bn == 256]; a.tmC = ctx->tmc_h;
   a.bias = w.bb_1; a.colsum = w.cs_1; a.stats = ctx->stats; a.np = np2; a.eps = c.ln_eps;
   a.epi = wm::EPI_LNF_GELU;
@@ -362,7 +549,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   // FC2 + residual, leaving the next block's LayerNorm-1 statistics
   a = wm::GemmArgs();
   a.M = (int)M; a.K = 4 * C; a.N = C;
-  a.bn = pick_bn(M, a.N);
+  set_tile(a, M, wm::EPI_RESID_LN, false);
   a.tmA = ctx->tm_h; a.tmB = w.tm_2[a.bn == 256]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
   a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.x = x; a.stats = ctx->stats;
   { TimedLaunch t(ctx, WM_K_FC2, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
@@ -888,7 +1075,7 @@ wm_status wm_ctx_sizes(wm_ctx* ctx, int batch, size_t* latent_floats, size_t* wo
 
 wm_status wm_autotune_report(char* buf, size_t len) {
   if (!buf || len == 0) return fail(WM_ERR_INVALID_ARG, "bad report buffer");
-  const std::string r = wm::describe_na_plans();
+  const std::string r = wm::describe_na_plans() + describe_gemm_plans();
   const size_t n = std::min(len - 1, r.size());
   std::memcpy(buf, r.data(), n);
   buf[n] = 0;

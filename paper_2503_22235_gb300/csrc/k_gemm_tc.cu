@@ -613,7 +613,8 @@ static wm_status launch_bn(const GemmArgs& a, cudaStream_t s) {
       case EPI_STORE_F32: return launch_one<BN, EPI_STORE_F32, true>(a, s);
       case EPI_RESID_LN:
         // short K: the epilogue dominates, give it a second staging tile (one stage fewer)
-        return a.K <= 1024 ? launch_one<BN, EPI_RESID_LN, true, true>(a, s) : launch_one<BN, EPI_RESID_LN, true>(a, s);
+        return (a.dual >= 0 ? a.dual == 1 : a.K <= 1024) ? launch_one<BN, EPI_RESID_LN, true, true>(a, s)
+                                                           : launch_one<BN, EPI_RESID_LN, true>(a, s);
       default: return fail(WM_ERR_INVALID_ARG, "unsupported epilogue for the e4m3 GEMM");
     }
   }
@@ -623,7 +624,8 @@ static wm_status launch_bn(const GemmArgs& a, cudaStream_t s) {
     case EPI_RESID_F32: return launch_one<BN, EPI_RESID_F32, false>(a, s);
     case EPI_STORE_F32: return launch_one<BN, EPI_STORE_F32, false>(a, s);
     case EPI_RESID_LN:
-      return a.K <= 1024 ? launch_one<BN, EPI_RESID_LN, false, true>(a, s) : launch_one<BN, EPI_RESID_LN, false>(a, s);
+      return (a.dual >= 0 ? a.dual == 1 : a.K <= 1024) ? launch_one<BN, EPI_RESID_LN, false, true>(a, s)
+                                                         : launch_one<BN, EPI_RESID_LN, false>(a, s);
     case EPI_LNF_STORE: return launch_one<BN, EPI_LNF_STORE, false>(a, s);
     case EPI_LNF_GELU: return launch_one<BN, EPI_LNF_GELU, false>(a, s);
     default: return fail(WM_ERR_INVALID_ARG, "unsupported epilogue for the bf16 GEMM");

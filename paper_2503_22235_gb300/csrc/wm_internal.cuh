@@ -210,6 +210,7 @@ struct GemmArgs {
   float out_scale = 1.f;  // EPI_GELU_F8: 1 / output scale
   const RopeArgs* rope = nullptr;  // device pointer; EPI_LNF_STORE rotates q and k
   bool pdl = false;    // launch as a programmatic dependent of the previous kernel
+  int dual = -1;       // EPI_RESID_LN: second staging tile (1) or not (0); -1: by K (K <= 1024)
 };
 // Rotate q and k in an fp32 qkv [M, 3C] (the FP32 plain path).
 wm_status launch_rope_f32(float* qkv, long M, const RopeArgs* rope_dev, const RopeArgs& rope_host, cudaStream_t s);

@@ -439,6 +439,25 @@ def test_full_size_attention_every_token_against_the_oracle():
         wm.wm_destroy(ctx)
 
 
+def test_gemm_autotuner_reports_the_block_gemms():
+    """Creating a BF16 context times the tile candidates of the block's GEMMs;
+    the report lists QKV and FC1 per row count and the residual GEMMs for
+    every row count (their tile width is fixed at the first tuning, so that a
+    batched step rounds as a single-latent step does)."""
+    s = synth.SMALL
+    ctx, _, _ = make_ctx(s, wm.WM_PREC_BF16)
+    try:
+        rep = wm.wm_autotune_report()
+        M = s.N
+        assert f"gemm rows={M} N={3 * s.C} K={s.C} epilogue=ln_store" in rep
+        assert f"gemm rows={M} N={4 * s.C} K={s.C} epilogue=ln_gelu" in rep
+        assert f"gemm rows=any N={s.C} K={s.C} epilogue=resid_ln" in rep
+        assert f"gemm rows=any N={s.C} K={4 * s.C} epilogue=resid_ln" in rep
+        assert "candidate fc2" in rep
+    finally:
+        wm.wm_destroy(ctx)
+
+
 # ------------------------------------------------------------------ misc ---
 
 def test_rel_l2_fp64_reduction():
