@@ -424,9 +424,27 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         fp32_ms = e0.elapsed_time(e1)
+        # per-kernel times of one more FP32 step (CUDA events per launch)
+        wm.wm_timing_begin(ctx, 8 * shape.blocks_p6 + 16)
+        wm.wm_processor_step(ctx, xc, wm.WM_P6)
+        torch.cuda.synchronize()
+        f32_kt = wm.wm_timing_end(ctx)
         wm.wm_set_precision(ctx, wm.WM_PREC_BF16)
+        # FP32 FMA peak (nominal): 128 FP32 lanes per SM, one FMA (2 flop) per lane per clock
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        f32_peak = 2.0 * 128 * n_sm * ((clk.summary() or {}).get("sm_mhz") or 2070.0) * 1e6 / 1e12
+        f32_tf = {k: flops[k] / (f32_kt[k][0] / f32_kt[k][1] * 1e-3) / 1e12
+                  for k in ("qkv", "proj", "fc1", "fc2", "attn") if f32_kt[k][1]}
+        f32_dom = max((k for k in f32_kt if f32_kt[k][1] > 0), key=lambda k: f32_kt[k][0])
         out["fp32_plain"] = {"value": 1e3 / fp32_ms, "unit": UNIT, "ms_per_step": fp32_ms,
-                             "bf16_vs_fp32_rel_l2": err, "speedup_bf16": fp32_ms / ms_per_step}
+                             "bf16_vs_fp32_rel_l2": err, "speedup_bf16": fp32_ms / ms_per_step,
+                             "kernels_ms_per_step": {k: v[0] for k, v in f32_kt.items() if v[1]},
+                             "roofline": {"bound": "alu", "kernel": f32_dom, "achieved": f32_tf.get(f32_dom),
+                                          "peak": f32_peak, "unit": "TFLOP/s",
+                                          "frac": (f32_tf.get(f32_dom) or 0.0) / f32_peak,
+                                          "tflops": f32_tf, "frac_by_kernel": {k: v / f32_peak for k, v in f32_tf.items()},
+                                          "peak_source": "nominal FP32 FMA rate: 128 lanes x 2 flop x SMs x median "
+                                                         "SM clock under load (no TF32)"}}
         del xa, xb, xc
 
     # ---------------- FP8-MLP precision on the same step

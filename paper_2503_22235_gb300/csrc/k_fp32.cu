@@ -458,8 +458,145 @@ __global__ void na_f32_kernel(const float* __restrict__ qkv, float* __restrict__
   }
 }
 
+// Tiled FP32 attention: CTA = batch element, head, query level and an 8 x 8
+// block of queries; two threads per query, each owning half of the head's
+// channels (a score is the two halves' dot products added with one shuffle).
+// For every key level the CTA stages the tile's K and V halo slabs (rows of
+// dh + 4 floats: 128-bit loads of consecutive keys hit distinct banks) in
+// shared memory; each query walks its own window row by row with an online
+// softmax (running max and sum in FP32, O rescaled once per window row).
+// Strict FP32 FMA and expf throughout.
+template <int DH>
+__global__ void __launch_bounds__(128, 2) na_f32_tile_kernel(const float* __restrict__ qkv, float* __restrict__ out,
+                                                          int B, int D, int H, int W, int C, int heads, int kd, int kh,
+                                                          int kw, int periodic, int tiles_h, int tiles_w) {
+  constexpr int TH = 8, TW = 8, HD = DH / 2, KS = DH + 4;   // KS: key row stride in shared memory (floats)
+  constexpr int KW_MAX = 9;
+  extern __shared__ __align__(16) float sm[];
+  const int HR = min(TH + kh - 1, H);
+  const int WC = periodic ? TW + kw - 1 : min(TW + kw - 1, W);
+  float* Ks = sm;
+  float* Vs = sm + HR * WC * KS;
+  int t = blockIdx.x;
+  const int tw = t % tiles_w;
+  t /= tiles_w;
+  const int th = t % tiles_h;
+  t /= tiles_h;
+  const int d = t % D;
+  t /= D;
+  const int head = t % heads, b = t / heads;
+  const int h0 = th * TH, w0 = tw * TW, rh = kh / 2, rw = kw / 2;
+  const int hs0 = clampi(h0 - rh, 0, H - HR);
+  const int ws0 = periodic ? w0 - rw : clampi(w0 - rw, 0, W - WC);
+  const int ld0 = clampi(d - kd / 2, 0, D - kd);
+  const int pair = threadIdx.x >> 1, half = threadIdx.x & 1;
+  const int hq = h0 + pair / TW, wq = w0 + pair % TW;
+  const bool valid = hq < H && wq < W;
+  const int hc = min(hq, H - 1), wc = min(wq, W - 1);
+  const int ra = clampi(hc - rh, 0, H - kh) - hs0;                                   // window rows in the slab
+  const int cb = (periodic ? wc - rw : clampi(wc - rw, 0, W - kw)) - ws0;            // window columns
+  const long N = (long)D * H * W, C3 = 3L * C;
+  const float scale = rsqrtf((float)DH);
+  float q[HD], o[HD];
+  {
+    const float4* qs = reinterpret_cast<const float4*>(qkv + ((long)b * N + ((long)d * H + hc) * W + wc) * C3 +
+                                                       head * DH + half * HD);
+#pragma unroll
+    for (int i = 0; i < HD / 4; ++i) {
+      const float4 v = qs[i];
+      q[4 * i] = v.x; q[4 * i + 1] = v.y; q[4 * i + 2] = v.z; q[4 * i + 3] = v.w;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < HD; ++i) o[i] = 0.f;
+  float m = -INFINITY, l = 0.f;
+  const int slab_keys = HR * WC;
+  for (int li = 0; li < kd; ++li) {
+    __syncthreads();   // the previous level's slabs are no longer read
+    const long lev = (long)b * D + ld0 + li;
+    for (int idx = threadIdx.x; idx < 2 * slab_keys * (DH / 4); idx += blockDim.x) {
+      const int kv = idx / (slab_keys * (DH / 4));
+      const int rem = idx - kv * slab_keys * (DH / 4);
+      const int key = rem / (DH / 4), c4 = rem - key * (DH / 4);
+      const int r = key / WC, c = key - r * WC;
+      int lon = ws0 + c;
+      if (periodic) lon = ((lon % W) + W) % W;
+      const float4 v = *reinterpret_cast<const float4*>(qkv + ((lev * H + hs0 + r) * W + lon) * C3 + (1 + kv) * C +
+                                                        head * DH + 4 * c4);
+      *reinterpret_cast<float4*>((kv ? Vs : Ks) + key * KS + 4 * c4) = v;
+    }
+    __syncthreads();
+    for (int a = 0; a < kh; ++a) {
+      const int row = (ra + a) * WC + cb;
+      float sc[KW_MAX];
+      float rmax = -INFINITY;
+#pragma unroll
+      for (int j = 0; j < KW_MAX; ++j) {
+        if (j < kw) {
+          const float4* kr = reinterpret_cast<const float4*>(Ks + (row + j) * KS + half * HD);
+          float acc = 0.f;
+#pragma unroll
+          for (int i = 0; i < HD / 4; ++i) {
+            const float4 k4 = kr[i];
+            acc = fmaf(q[4 * i], k4.x, acc);
+            acc = fmaf(q[4 * i + 1], k4.y, acc);
+            acc = fmaf(q[4 * i + 2], k4.z, acc);
+            acc = fmaf(q[4 * i + 3], k4.w, acc);
+          }
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);   // the other half of the channels
+          sc[j] = acc * scale;
+          rmax = fmaxf(rmax, sc[j]);
+        }
+      }
+      if (rmax > m) {
+        const float alpha = expf(m - rmax);   // 0 while m = -inf: O and l are still zero
+        l *= alpha;
+#pragma unroll
+        for (int i = 0; i < HD; ++i) o[i] *= alpha;
+        m = rmax;
+      }
+#pragma unroll
+      for (int j = 0; j < KW_MAX; ++j) {
+        if (j < kw) {
+          const float p = expf(sc[j] - m);
+          l += p;
+          const float4* vr = reinterpret_cast<const float4*>(Vs + (row + j) * KS + half * HD);
+#pragma unroll
+          for (int i = 0; i < HD / 4; ++i) {
+            const float4 v4 = vr[i];
+            o[4 * i] = fmaf(p, v4.x, o[4 * i]);
+            o[4 * i + 1] = fmaf(p, v4.y, o[4 * i + 1]);
+            o[4 * i + 2] = fmaf(p, v4.z, o[4 * i + 2]);
+            o[4 * i + 3] = fmaf(p, v4.w, o[4 * i + 3]);
+          }
+        }
+      }
+    }
+  }
+  if (!valid) return;
+  const float inv = 1.f / l;
+  float4* orow = reinterpret_cast<float4*>(out + ((long)b * N + ((long)d * H + hq) * W + wq) * C + head * DH +
+                                           half * HD);
+#pragma unroll
+  for (int i = 0; i < HD / 4; ++i)
+    orow[i] = make_float4(o[4 * i] * inv, o[4 * i + 1] * inv, o[4 * i + 2] * inv, o[4 * i + 3] * inv);
+}
+
+// Shared memory of the tiled FP32 attention (K and V slabs), or 0 if the
+// shape does not fit it.
+static size_t na_f32_tile_smem(int H, int W, int dh, int kh, int kw, bool periodic) {
+  if (kw > 9 || (dh != 16 && dh != 32 && dh != 48 && dh != 64)) return 0;
+  const int HR = std::min(8 + kh - 1, H), WC = periodic ? 8 + kw - 1 : std::min(8 + kw - 1, W);
+  const size_t bytes = (size_t)2 * HR * WC * (dh + 4) * sizeof(float);
+  return bytes <= 227 * 1024 ? bytes : 0;
+}
+
 wm_status prepare_na_f32() {
   WM_CUDA(cudaFuncSetAttribute(na_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  WM_CUDA(cudaFuncSetAttribute(na_f32_tile_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  WM_CUDA(cudaFuncSetAttribute(na_f32_tile_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  WM_CUDA(cudaFuncSetAttribute(na_f32_tile_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  WM_CUDA(cudaFuncSetAttribute(na_f32_tile_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   return WM_OK;
 }
 
@@ -467,6 +604,24 @@ wm_status launch_na_f32(const float* qkv, float* out, int B, int D, int H, int W
                         int kw, bool periodic, cudaStream_t s) {
   const long total = (long)B * D * H * W * heads;
   if (total <= 0) return WM_OK;
+  const int dh0 = C / heads;
+  const size_t tsm = na_f32_tile_smem(H, W, dh0, kh, kw, periodic);
+  if (tsm && (C % 4) == 0 && (reinterpret_cast<uintptr_t>(qkv) & 15) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+    const int tiles_h = (H + 7) / 8, tiles_w = (W + 7) / 8;
+    const long ctas = (long)tiles_h * tiles_w * D * heads * B;
+    if (ctas > (1L << 31) - 1) return fail(WM_ERR_INVALID_ARG, "too many attention tiles");
+    const dim3 grid((unsigned)ctas), block(128);
+    const int per = periodic ? 1 : 0;
+    switch (dh0) {
+      case 16: na_f32_tile_kernel<16><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w); break;
+      case 32: na_f32_tile_kernel<32><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w); break;
+      case 48: na_f32_tile_kernel<48><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w); break;
+      default: na_f32_tile_kernel<64><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w); break;
+    }
+    WM_CUDA(cudaGetLastError());
+    return WM_OK;
+  }
+  // other shapes: one warp per (query, head)
   const int warps = 8;
   const int K = kd * kh * kw, dh = C / heads;
   const size_t smem = (size_t)warps * (K + dh) * sizeof(float);
