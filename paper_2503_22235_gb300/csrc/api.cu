@@ -604,6 +604,25 @@ wm_status run_graph(wm_ctx* ctx, const std::vector<uintptr_t>& key, cudaStream_t
   return WM_OK;
 }
 
+}  // namespace
+
+namespace wm {
+// One processor step on `batch` contiguous latents, replayed from a CUDA
+// graph captured once per (latent buffer, batch, processor, precision): the
+// server's ticks launch one graph instead of every kernel of the step.
+wm_status processor_step_graphed(wm_ctx* ctx, float* x, int batch, int which, cudaStream_t s) {
+  WM_TRY(check_compute(ctx, x, batch));
+  if (which != WM_P6 && which != WM_P1) return fail(WM_ERR_INVALID_ARG, "which must be WM_P6 or WM_P1");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  WM_TRY(ensure_workspace(ctx, batch));
+  const std::vector<uintptr_t> key = {4, (uintptr_t)x, (uintptr_t)batch, (uintptr_t)which,
+                                      (uintptr_t)ctx->cfg.precision};
+  return run_graph(ctx, key, s, [&](cudaStream_t st) -> wm_status { return processor_step(ctx, x, batch, which, st); });
+}
+}  // namespace wm
+
+namespace {
+
 // Rotary embedding tables: pair m of an axis at position pos has angle
 // pos * w_m (w_m = 10000^(-m/n) for level and latitude, 2 pi (m + 1) / W for
 // longitude); stored as (cos, sin) computed in double.

@@ -459,18 +459,19 @@ __global__ void na_f32_kernel(const float* __restrict__ qkv, float* __restrict__
 }
 
 // Tiled FP32 attention: CTA = batch element, head, query level and an 8 x 8
-// block of queries; two threads per query, each owning half of the head's
-// channels (a score is the two halves' dot products added with one shuffle).
+// block of queries; four threads per query, each owning a quarter of the
+// head's channels (a score is the quarters' dot products added with two
+// shuffles).
 // For every key level the CTA stages the tile's K and V halo slabs (rows of
 // dh + 4 floats: 128-bit loads of consecutive keys hit distinct banks) in
 // shared memory; each query walks its own window row by row with an online
 // softmax (running max and sum in FP32, O rescaled once per window row).
 // Strict FP32 FMA and expf throughout.
 template <int DH>
-__global__ void __launch_bounds__(128, 2) na_f32_tile_kernel(const float* __restrict__ qkv, float* __restrict__ out,
+__global__ void __launch_bounds__(256, 2) na_f32_tile_kernel(const float* __restrict__ qkv, float* __restrict__ out,
                                                           int B, int D, int H, int W, int C, int heads, int kd, int kh,
                                                           int kw, int periodic, int tiles_h, int tiles_w) {
-  constexpr int TH = 8, TW = 8, HD = DH / 2, KS = DH + 4;   // KS: key row stride in shared memory (floats)
+  constexpr int TH = 8, TW = 8, TPQ = 4, HD = DH / TPQ, KS = DH + 4;   // KS: key row stride in shared memory (floats)
   constexpr int KW_MAX = 9;
   extern __shared__ __align__(16) float sm[];
   const int HR = min(TH + kh - 1, H);
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(128, 2) na_f32_tile_kernel(const float* __rest
   const int hs0 = clampi(h0 - rh, 0, H - HR);
   const int ws0 = periodic ? w0 - rw : clampi(w0 - rw, 0, W - WC);
   const int ld0 = clampi(d - kd / 2, 0, D - kd);
-  const int pair = threadIdx.x >> 1, half = threadIdx.x & 1;
+  const int pair = threadIdx.x / TPQ, half = threadIdx.x % TPQ;   // query of the tile, channel quarter
   const int hq = h0 + pair / TW, wq = w0 + pair % TW;
   const bool valid = hq < H && wq < W;
   const int hc = min(hq, H - 1), wc = min(wq, W - 1);
@@ -543,7 +544,8 @@ __global__ void __launch_bounds__(128, 2) na_f32_tile_kernel(const float* __rest
             acc = fmaf(q[4 * i + 2], k4.z, acc);
             acc = fmaf(q[4 * i + 3], k4.w, acc);
           }
-          acc += __shfl_xor_sync(0xffffffffu, acc, 1);   // the other half of the channels
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);   // the other channel quarters
+          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
           sc[j] = acc * scale;
           rmax = fmaxf(rmax, sc[j]);
         }
@@ -585,7 +587,7 @@ __global__ void __launch_bounds__(128, 2) na_f32_tile_kernel(const float* __rest
 // Shared memory of the tiled FP32 attention (K and V slabs), or 0 if the
 // shape does not fit it.
 static size_t na_f32_tile_smem(int H, int W, int dh, int kh, int kw, bool periodic) {
-  if (kw > 9 || (dh != 16 && dh != 32 && dh != 48 && dh != 64)) return 0;
+  if (kw > 9 || (dh != 16 && dh != 32 && dh != 48 && dh != 64)) return 0;   // dh / 4 channels per thread in float4
   const int HR = std::min(8 + kh - 1, H), WC = periodic ? 8 + kw - 1 : std::min(8 + kw - 1, W);
   const size_t bytes = (size_t)2 * HR * WC * (dh + 4) * sizeof(float);
   return bytes <= 227 * 1024 ? bytes : 0;
@@ -610,7 +612,7 @@ wm_status launch_na_f32(const float* qkv, float* out, int B, int D, int H, int W
     const int tiles_h = (H + 7) / 8, tiles_w = (W + 7) / 8;
     const long ctas = (long)tiles_h * tiles_w * D * heads * B;
     if (ctas > (1L << 31) - 1) return fail(WM_ERR_INVALID_ARG, "too many attention tiles");
-    const dim3 grid((unsigned)ctas), block(128);
+    const dim3 grid((unsigned)ctas), block(256);
     const int per = periodic ? 1 : 0;
     switch (dh0) {
       case 16: na_f32_tile_kernel<16><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w); break;

@@ -6,8 +6,9 @@
 // with steps left takes exactly one processor step (six-hour steps first,
 // then one-hour steps, the greedy schedule of Section 2.1). The requests due
 // for the same processor are gathered into one contiguous batch (at most
-// max_batch latents per launch), stepped together and scattered back, so a
-// request that arrives while others run joins at the next tick. Kernels are
+// max_batch latents per launch), stepped together -- the step replayed from
+// a CUDA graph captured once per batch size and processor -- and scattered
+// back, so a request that arrives while others run joins at the next tick. Kernels are
 // row independent, so a result does not depend on what it was batched with.
 // A finished request keeps its result in its slot until it is collected by
 // wm_server_poll, which frees the slot for the next admission.
@@ -87,19 +88,15 @@ wm_status run_tick(wm_server* s, const std::vector<uint64_t>& ids, const std::ve
         s->max_step_batch = std::max(s->max_step_batch, g);
         if (g >= 2) ++s->multi_request_steps;
       }
-      if (g == 1) {
-        wm_status st = wm_processor_step(s->ctx, s->slab + (size_t)due[b0] * lat, 1, w, s->stream);
-        if (st != WM_OK) return st;
-      } else {
-        for (int j = 0; j < g; ++j)
-          WM_CUDA(cudaMemcpyAsync(s->stage + (size_t)j * lat, s->slab + (size_t)due[b0 + j] * lat, lat * 4,
-                                  cudaMemcpyDeviceToDevice, s->stream));
-        wm_status st = wm_processor_step(s->ctx, s->stage, g, w, s->stream);
-        if (st != WM_OK) return st;
-        for (int j = 0; j < g; ++j)
-          WM_CUDA(cudaMemcpyAsync(s->slab + (size_t)due[b0 + j] * lat, s->stage + (size_t)j * lat, lat * 4,
-                                  cudaMemcpyDeviceToDevice, s->stream));
-      }
+      // gather into the staging batch, one graph-replayed step, scatter back
+      for (int j = 0; j < g; ++j)
+        WM_CUDA(cudaMemcpyAsync(s->stage + (size_t)j * lat, s->slab + (size_t)due[b0 + j] * lat, lat * 4,
+                                cudaMemcpyDeviceToDevice, s->stream));
+      wm_status st = wm::processor_step_graphed(s->ctx, s->stage, g, w, s->stream);
+      if (st != WM_OK) return st;
+      for (int j = 0; j < g; ++j)
+        WM_CUDA(cudaMemcpyAsync(s->slab + (size_t)due[b0 + j] * lat, s->stage + (size_t)j * lat, lat * 4,
+                                cudaMemcpyDeviceToDevice, s->stream));
       ++s->batched_steps;
     }
   }

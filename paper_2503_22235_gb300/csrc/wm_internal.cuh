@@ -17,6 +17,9 @@ namespace wm {
 
 // The configuration a context was created with.
 const wm_config* ctx_config(const wm_ctx* ctx);
+// One processor step on `batch` contiguous latents, replayed from a CUDA graph
+// captured per (latent buffer, batch, processor, precision).
+wm_status processor_step_graphed(wm_ctx* ctx, float* x, int batch, int which, cudaStream_t s);
 
 // ------------------------------------------------------------ errors ----
 void set_error(const std::string& msg);
