@@ -81,6 +81,7 @@ _SIGS = {
     "wm_op_linear_e4m3": (_c_int, [_vp, _vp, _c_float, _vp, _vp, _c_float, _c_int, _c_int, _c_int, _c_int, _vp]),
     "wm_op_layernorm_e4m3": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_float, _c_float, _vp]),
     "wm_fp8_scales": (_c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_c_float)]),
+    "wm_gemm_tile_override": (_c_int, [_c_int]),
     "wm_codec_create": (_c_int, [ctypes.POINTER(wm_codec_config), _vp, _sz, ctypes.POINTER(_vp)]),
     "wm_codec_destroy": (_c_int, [_vp]),
     "wm_encode": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -387,6 +388,14 @@ def wm_fp8_scales(ctx, which, block) -> tuple:
     out = (_c_float * 4)()
     _check(lib().wm_fp8_scales(ctx, int(which), int(block), out))
     return tuple(out)
+
+
+GEMM_TILES_TUNED, GEMM_TILES_128, GEMM_TILES_256, GEMM_TILES_PAIR = 0, 1, 2, 3
+
+
+def wm_gemm_tile_override(mode) -> None:
+    """Test hook: force the block GEMMs' tiles (GEMM_TILES_*); GEMM_TILES_TUNED restores the tuned plans."""
+    _check(lib().wm_gemm_tile_override(int(mode)))
 
 
 # ------------------------------------------------------- encoder / decoder ---

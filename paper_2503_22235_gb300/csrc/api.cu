@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -244,9 +245,10 @@ int pick_bn(long M, int N) {
 }
 
 // ---- GEMM tile autotuner
-// Tile width BN (128 or 256 output columns) and, for the residual epilogue,
-// one or two staging tiles, chosen per GEMM of the block by timing every
-// candidate when a context's BF16 workspace is allocated. BN changes no
+// Tile width BN (128 or 256 output columns; 256 also as 256 x 256 tiles on
+// CTA pairs) and, for the residual epilogue, one or two staging tiles,
+// chosen per GEMM of the block by timing every candidate when a context's
+// BF16 workspace is allocated. BN changes no
 // output of the LayerNorm-folded and GELU epilogues (every element's K sum
 // runs in the same order), so those are tuned per row count. The residual
 // epilogue writes one LayerNorm partial per half tile, so its BN fixes how a
@@ -255,8 +257,11 @@ int pick_bn(long M, int N) {
 // identical to single-latent results. Untuned shapes take pick_bn.
 struct GemmPick {
   int bn = 0, dual = -1;
+  bool pair = false;
   double ms = 0.0;
 };
+// Test hook (wm_gemm_tile_override): 0 = tuned plans, 1 = BN 128, 2 = BN 256, 3 = BN 256 on CTA pairs.
+std::atomic<int> g_gemm_override{0};
 using GemmKey = std::array<long, 5>;   // rows (-1 for the residual epilogue), N, K, epilogue, e4m3
 std::mutex g_gemm_mu;
 std::map<GemmKey, GemmPick> g_gemm_picks;
@@ -267,6 +272,14 @@ GemmKey gemm_key(long M, int N, int K, int epi, bool f8) {
 }
 
 GemmPick pick_gemm(long M, int N, int K, int epi, bool f8) {
+  const int ov = g_gemm_override.load();
+  if (ov != 0) {
+    GemmPick g;
+    g.bn = (ov == 1 || N % 256 != 0) ? 128 : 256;
+    // the pair kernel carries the block's epilogues (not the FP8-MLP path's plain residual add)
+    g.pair = ov == 3 && g.bn == 256 && epi != wm::EPI_RESID_F32;
+    return g;
+  }
   {
     std::lock_guard<std::mutex> lk(g_gemm_mu);
     auto it = g_gemm_picks.find(gemm_key(M, N, K, epi, f8));
@@ -291,13 +304,17 @@ wm_status tune_gemm(wm::GemmArgs a, const CUtensorMap (&tmB)[2], const char* nam
   GemmPick best;
   best.ms = 1e30;
   wm_status st = WM_OK;
-  for (int bn : {128, 256}) {
+  for (int cand : {128, 256, 512}) {   // 512: BN = 256 on CTA pairs
+    const int bn = cand == 512 ? 256 : cand;
+    const bool pair = cand == 512;
     if (a.epi == wm::EPI_RESID_LN && a.N % bn != 0) continue;
+    if (pair && a.N % 256 != 0) continue;
     for (int dual : {0, 1}) {
       if (a.epi != wm::EPI_RESID_LN && dual == 1) continue;
       a.bn = bn;
+      a.pair = pair;
       a.dual = a.epi == wm::EPI_RESID_LN ? dual : -1;
-      a.tmB = tmB[bn == 256];
+      a.tmB = tmB[bn == 256 && !pair];
       st = wm::launch_gemm_tc(a, s);
       if (st != WM_OK) break;
       cudaEventRecord(e0, s);
@@ -311,8 +328,8 @@ wm_status tune_gemm(wm::GemmArgs a, const CUtensorMap (&tmB)[2], const char* nam
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       char line[200];
-      std::snprintf(line, sizeof line, "  candidate %s M=%d N=%d K=%d BN=%d staging=%s: %.4f ms\n", name, a.M, a.N,
-                    a.K, bn, a.epi == wm::EPI_RESID_LN ? (dual ? "two" : "one") : "-", ms / 3.0);
+      std::snprintf(line, sizeof line, "  candidate %s M=%d N=%d K=%d BN=%d%s staging=%s: %.4f ms\n", name, a.M, a.N,
+                    a.K, bn, pair ? " pair" : "", a.epi == wm::EPI_RESID_LN ? (dual ? "two" : "one") : "-", ms / 3.0);
       {
         std::lock_guard<std::mutex> lk(g_gemm_mu);
         g_gemm_log += line;
@@ -320,6 +337,7 @@ wm_status tune_gemm(wm::GemmArgs a, const CUtensorMap (&tmB)[2], const char* nam
       if (ms / 3.0 < best.ms) {
         best.ms = ms / 3.0;
         best.bn = bn;
+        best.pair = pair;
         best.dual = a.dual;
       }
     }
@@ -343,9 +361,10 @@ std::string describe_gemm_plans() {
   for (const auto& kv : g_gemm_picks) {
     const GemmKey& k = kv.first;
     char line[200];
-    std::snprintf(line, sizeof line, "gemm rows=%s N=%ld K=%ld epilogue=%s%s -> BN=%d staging=%s %.4f ms\n",
+    std::snprintf(line, sizeof line, "gemm rows=%s N=%ld K=%ld epilogue=%s%s -> BN=%d%s staging=%s %.4f ms\n",
                   k[0] < 0 ? "any" : std::to_string(k[0]).c_str(), k[1], k[2], names[k[3]], k[4] ? " e4m3" : "",
-                  kv.second.bn, kv.second.dual < 0 ? "-" : (kv.second.dual ? "two" : "one"), kv.second.ms);
+                  kv.second.bn, kv.second.pair ? " pair" : "", kv.second.dual < 0 ? "-" : (kv.second.dual ? "two" : "one"),
+                  kv.second.ms);
     out += line;
   }
   return out + g_gemm_log;
@@ -423,8 +442,13 @@ wm_status tune_block_gemms(wm_ctx* ctx, int batch) {
 void set_tile(wm::GemmArgs& a, long M, int epi, bool f8) {
   const GemmPick g = pick_gemm(M, a.N, a.K, epi, f8);
   a.bn = g.bn;
+  a.pair = g.pair;
   a.dual = g.dual;
 }
+
+// Which of a weight's two W maps the tile reads: boxes of 256 rows for
+// single-CTA BN = 256 tiles, of 128 rows for BN = 128 and for each CTA of a pair.
+int wmap(const wm::GemmArgs& a) { return a.bn == 256 && !a.pair ? 1 : 0; }
 
 // ---- optional per-launch timing: an event pair around each hot-path kernel
 const char* const kKernelNames[WM_KERNEL_KINDS] = {"ln1", "qkv", "attention", "proj", "ln2", "fc1", "fc2"};
@@ -494,7 +518,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   a.K = C;
   a.N = 3 * C;
   set_tile(a, M, wm::EPI_LNF_STORE, false);
-  a.tmA = ctx->tm_xb; a.tmB = w.tm_fqkv[a.bn == 256]; a.tmC = ctx->tmc_qkv;
+  a.tmA = ctx->tm_xb; a.tmB = w.tm_fqkv[wmap(a)]; a.tmC = ctx->tmc_qkv;
   a.bias = w.bb_qkv; a.colsum = w.cs_qkv; a.stats = ctx->stats; a.np = ctx->np_next; a.eps = c.ln_eps;
   a.epi = wm::EPI_LNF_STORE;
   a.rope = c.rope ? ctx->d_rope : nullptr;
@@ -506,7 +530,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   a = wm::GemmArgs();
   a.M = (int)M; a.K = C; a.N = C;
   set_tile(a, M, fp8 ? wm::EPI_RESID_F32 : wm::EPI_RESID_LN, false);
-  a.tmA = ctx->tm_o; a.tmB = w.tm_o[a.bn == 256]; a.tmC = tm_x;
+  a.tmA = ctx->tm_o; a.tmB = w.tm_o[wmap(a)]; a.tmC = tm_x;
   a.bias = w.bo;
   if (fp8) {
     a.epi = wm::EPI_RESID_F32;
@@ -525,14 +549,14 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
     a.f8 = true;
     a.M = (int)M; a.K = C; a.N = 4 * C;
     set_tile(a, M, wm::EPI_GELU_F8, true);
-    a.tmA = ctx->tm_qu; a.tmB = w.tm_q1[a.bn == 256]; a.tmC = ctx->tmc_qh;
+    a.tmA = ctx->tm_qu; a.tmB = w.tm_q1[wmap(a)]; a.tmC = ctx->tmc_qh;
     a.bias = w.b1; a.epi = wm::EPI_GELU_F8; a.alpha = w.s_u * w.s_w1; a.out_scale = 1.f / w.s_h;
     { TimedLaunch t(ctx, WM_K_FC1, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
     a = wm::GemmArgs();
     a.f8 = true;
     a.M = (int)M; a.K = 4 * C; a.N = C;
     set_tile(a, M, wm::EPI_RESID_LN, true);
-    a.tmA = ctx->tm_qh; a.tmB = w.tm_q2[a.bn == 256]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
+    a.tmA = ctx->tm_qh; a.tmB = w.tm_q2[wmap(a)]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
     a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.alpha = w.s_h * w.s_w2; a.x = x; a.stats = ctx->stats;
     { TimedLaunch t(ctx, WM_K_FC2, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
     ctx->np_next = 2 * ((C + a.bn - 1) / a.bn);
@@ -542,7 +566,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   a = wm::GemmArgs();
   a.M = (int)M; a.K = C; a.N = 4 * C;
   set_tile(a, M, wm::EPI_LNF_GELU, false);
-  a.tmA = ctx->tm_xb; a.tmB = w.tm_f1[a.bn == 256]; a.tmC = ctx->tmc_h;
+  a.tmA = ctx->tm_xb; a.tmB = w.tm_f1[wmap(a)]; a.tmC = ctx->tmc_h;
   a.bias = w.bb_1; a.colsum = w.cs_1; a.stats = ctx->stats; a.np = np2; a.eps = c.ln_eps;
   a.epi = wm::EPI_LNF_GELU;
   { TimedLaunch t(ctx, WM_K_FC1, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
@@ -550,7 +574,7 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   a = wm::GemmArgs();
   a.M = (int)M; a.K = 4 * C; a.N = C;
   set_tile(a, M, wm::EPI_RESID_LN, false);
-  a.tmA = ctx->tm_h; a.tmB = w.tm_2[a.bn == 256]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
+  a.tmA = ctx->tm_h; a.tmB = w.tm_2[wmap(a)]; a.tmC = tm_x; a.tmC2 = ctx->tmc_xb;
   a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.x = x; a.stats = ctx->stats;
   { TimedLaunch t(ctx, WM_K_FC2, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
   ctx->np_next = 2 * ((C + a.bn - 1) / a.bn);
@@ -1258,15 +1282,23 @@ wm_status wm_op_linear(const void* A, const void* W, const float* bias, void* ou
   if (M == 0) return WM_OK;
   if (K % 8 != 0 || N % 8 != 0) return fail(WM_ERR_INVALID_ARG, "BF16 linear needs K % 8 == 0 and N % 8 == 0");
   wm::GemmArgs a;
-  a.bn = pick_bn(M, N);
+  const int ov = g_gemm_override.load();
+  a.bn = ov == 1 ? 128 : (ov >= 2 && N % 256 == 0) ? 256 : pick_bn(M, N);
+  a.pair = ov == 3 && a.bn == 256 && epilogue == wm::EPI_STORE;
   const bool out_f32 = epilogue == wm::EPI_RESID_F32 || epilogue == wm::EPI_STORE_F32;
   if (!wm::make_tmap_bf16(&a.tmA, A, (uint64_t)M, (uint64_t)K, 128) ||
-      !wm::make_tmap_bf16(&a.tmB, W, (uint64_t)N, (uint64_t)K, (uint32_t)a.bn) ||
+      !wm::make_tmap_bf16(&a.tmB, W, (uint64_t)N, (uint64_t)K, (uint32_t)(a.pair ? 128 : a.bn)) ||
       !wm::make_tmap_out(&a.tmC, out, (uint64_t)M, (uint64_t)N, out_f32))
     return fail(WM_ERR_INVALID_ARG, "cannot build TMA descriptors (pointer alignment or sizes)");
   a.M = M; a.N = N; a.K = K;
   a.bias = bias; a.epi = epilogue;
   return wm::launch_gemm_tc(a, s);
+}
+
+wm_status wm_gemm_tile_override(int mode) {
+  if (mode < 0 || mode > 3) return fail(WM_ERR_INVALID_ARG, "GEMM tile override must be 0..3");
+  g_gemm_override.store(mode);
+  return WM_OK;
 }
 
 wm_status wm_fp8_scales(wm_ctx* ctx, int which, int block, float* out) {

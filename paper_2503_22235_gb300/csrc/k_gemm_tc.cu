@@ -13,6 +13,17 @@
 //   warps 2-9  epilogue: tcgen05.ld (32x32b) rows out of TMEM, add bias, then
 //              bf16 store, GELU + bf16 store, or FP32 residual add, while the
 //              MMA warp already fills the other accumulator.
+// Pair mode (BN = 256, PAIR): a cluster of two CTAs on two SMs computes a
+// 256 x 256 tile with tcgen05.mma.cta_group::2 (M = 256). Each CTA loads its
+// own 128 A rows and its own 128 of the tile's 256 W rows, so each SM's
+// shared memory takes 32 KB per 64-deep k-slice instead of 48 KB and its
+// tensor core reads the same, while each SM still produces a 128 x 256
+// accumulator in its own TMEM for its own epilogue. The even CTA's MMA
+// thread issues for both. Both CTAs' tensor copies (cta_group::2) complete
+// on the even CTA's stage barrier, which expects the bytes of both; the even
+// CTA's commits arrive on both CTAs' stage and accumulator barriers
+// (multicast); every epilogue warp of both CTAs releases an accumulator on
+// the even CTA's barrier.
 // Every mbarrier wait is bounded in time; on a timeout the CTA records
 // WM_ERR_TIMEOUT in the device status word, drains its own copies and MMAs,
 // frees TMEM and returns.
@@ -28,12 +39,13 @@ constexpr int BKB = 128;               // bytes per k-slice row (bf16: 64 elemen
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + NUM_EPI_WARPS);
 
-template <int BN, bool DUAL = false>   // DUAL: a second (bf16) staging tile per epilogue warp
+// DUAL: a second (bf16) staging tile per epilogue warp; PAIR: this CTA holds half of the W tile
+template <int BN, bool DUAL = false, bool PAIR = false>
 struct Cfg {
   static constexpr int A_BYTES = BM * BKB;
-  static constexpr int B_BYTES = BN * BKB;
+  static constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * BKB;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int STAGES = (BN >= 256) ? (DUAL ? 3 : 4) : (DUAL ? 5 : 6);
+  static constexpr int STAGES = PAIR ? (DUAL ? 5 : 6) : (BN >= 256) ? (DUAL ? 3 : 4) : (DUAL ? 5 : 6);
   static constexpr int EPI_STRIDE = DUAL ? 6144 : 4096;     // per epilogue warp: 32x32 fp32 (+ 32x32 bf16)
   static constexpr int EPI_BYTES = NUM_EPI_WARPS * EPI_STRIDE;
   static constexpr int SMEM = STAGES * STAGE_BYTES + EPI_BYTES + 1024;   // + alignment slack
@@ -42,6 +54,16 @@ struct Cfg {
 
 using namespace ptx;
 
+// The same into this CTA's shared memory, completing on the mbarrier of either
+// CTA of the pair (bar_cluster: a shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster, int c0,
+                                                 int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar_cluster), "r"(c0), "r"(c1)
+      : "memory");
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
@@ -71,22 +93,38 @@ __host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+template <bool PAIR>
 __device__ __forceinline__ void umma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if constexpr (PAIR)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
+template <bool PAIR>
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if constexpr (PAIR)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 // GELU(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)) with erf from Abramowitz &
 // Stegun, Handbook of Mathematical Functions, formula 7.1.26 (Hastings):
@@ -208,7 +246,7 @@ __device__ __forceinline__ void stage_row(uint8_t* buf, const float (&x)[32], in
   }
 }
 
-template <int BN, int EPI, bool F8, bool DUAL = false>
+template <int BN, int EPI, bool F8, bool DUAL = false, bool PAIR = false>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmC2, int M,
@@ -218,7 +256,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   constexpr bool kResLN = (EPI == EPI_RESID_LN);
   constexpr bool kLNF = (EPI == EPI_LNF_STORE || EPI == EPI_LNF_GELU);
   constexpr int BKE = F8 ? 128 : 64;     // elements per k-slice
-  using CF = Cfg<BN, DUAL>;
+  using CF = Cfg<BN, DUAL, PAIR>;
+  static_assert(!PAIR || BN == 256, "pair tiles are 256 x 256");
+  constexpr int TM = PAIR ? 2 * BM : BM;  // output rows per tile (of the CTA pair)
   constexpr int STAGES = CF::STAGES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
@@ -233,17 +273,22 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t smem_base = smem_u32(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_n = (N + BN - 1) / BN;
-  const int num_tiles = ((M + BM - 1) / BM) * num_n;
+  const int num_tiles = ((M + TM - 1) / TM) * num_n;
   const int nk = (K + BKE - 1) / BKE;
+  // tiles are walked per CTA, or per CTA pair (both CTAs of a pair walk the same list)
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int nunits = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
+      // (a pair's stage completes on the even CTA's barrier, with the bytes of both CTAs)
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf_bar[b], 1);
-      mbar_init(&acce_bar[b], NUM_EPI_WARPS);
+      mbar_init(&acce_bar[b], PAIR ? 2 * NUM_EPI_WARPS : NUM_EPI_WARPS);
     }
     mbar_init(&drain_bar, 1);
     abort_flag = 0;
@@ -251,13 +296,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(CF::TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) {
+      // one warp of each CTA of the pair, collectively: the same columns in both SMs
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                   "r"(CF::TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                   "r"(CF::TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();   // both CTAs' barriers and TMEM exist before any cross-CTA traffic
   tc_fence_after();
   const uint32_t tmem_base = tmem_slot;
   pdl_wait();      // the previous kernel's outputs (A, x, row statistics) are complete from here on
@@ -272,14 +326,21 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t phase = 0;
       uint32_t issued_mask = 0, last_parity = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-        const int m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
+      for (int tile = unit; tile < num_tiles && ok; tile += nunits) {
+        const int m0 = (tile / num_n) * TM + (int)rank * BM, n0 = (tile % num_n) * BN + (int)rank * (BN / 2);
         for (int kb = 0; kb < nk; ++kb) {
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag)) { ok = false; break; }
           const uint32_t sa = smem_base + stage * CF::STAGE_BYTES;
-          mbar_expect_tx(&full_bar[stage], CF::STAGE_BYTES);
-          tma_load_2d(sa, &tmA, &full_bar[stage], kb * BKE, m0);
-          tma_load_2d(sa + CF::A_BYTES, &tmB, &full_bar[stage], kb * BKE, n0);
+          if constexpr (PAIR) {
+            if (rank == 0) mbar_expect_tx(&full_bar[stage], 2 * CF::STAGE_BYTES);
+            const uint32_t fb = mapa_shared(smem_u32(&full_bar[stage]), 0);
+            tma_load_2d_pair(sa, &tmA, fb, kb * BKE, m0);
+            tma_load_2d_pair(sa + CF::A_BYTES, &tmB, fb, kb * BKE, n0);
+          } else {
+            mbar_expect_tx(&full_bar[stage], CF::STAGE_BYTES);
+            tma_load_2d(sa, &tmA, &full_bar[stage], kb * BKE, m0);
+            tma_load_2d(sa + CF::A_BYTES, &tmB, &full_bar[stage], kb * BKE, n0);
+          }
           issued_mask |= 1u << stage;
           last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -289,49 +350,64 @@ __global__ void __launch_bounds__(THREADS, 1)
         abort_flag = 1;
         atomicExch(status, (int)WM_ERR_TIMEOUT);
         // let our own copies land before the CTA's shared memory is released
-        for (int s = 0; s < STAGES; ++s)
-          if (issued_mask & (1u << s)) {
-            volatile int never = 0;
-            mbar_wait(&full_bar[s], (last_parity >> s) & 1u, &never);
-          }
+        if (PAIR && rank != 0) {
+          // they complete on the even CTA's barriers: give them a fixed 50 us
+          const unsigned long long t0 = globaltimer();
+          if (issued_mask != 0)
+            while (globaltimer() - t0 < 50000ull) {
+            }
+        } else {
+          for (int s = 0; s < STAGES; ++s)
+            if (issued_mask & (1u << s)) {
+              volatile int never = 0;
+              mbar_wait(&full_bar[s], (last_parity >> s) & 1u, &never);
+            }
+        }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    // (the odd CTA of a pair issues nothing here: the even CTA's thread issues the pair's MMAs)
+    if (lane == 0 && !(PAIR && rank != 0)) {
       // ------------------------------------------------------ MMA issuer
-      constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
+      constexpr uint32_t idesc = F8 ? idesc_e4m3(TM, BN) : idesc_bf16(TM, BN);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
       int it = 0;
-      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++it) {
+      for (int tile = unit; tile < num_tiles && ok; tile += nunits, ++it) {
         const int buf = it & 1;
         const uint32_t acc_par = (uint32_t)(it >> 1) & 1u;
-        if (!mbar_wait(&acce_bar[buf], acc_par ^ 1u, &abort_flag)) { ok = false; break; }
+        if (!(PAIR ? mbar_wait_cluster(&acce_bar[buf], acc_par ^ 1u, &abort_flag)
+                   : mbar_wait(&acce_bar[buf], acc_par ^ 1u, &abort_flag))) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
         for (int kb = 0; kb < nk; ++kb) {
-          if (!mbar_wait(&full_bar[stage], phase, &abort_flag)) { ok = false; break; }
+          if (!(PAIR ? mbar_wait_cluster(&full_bar[stage], phase, &abort_flag)
+                     : mbar_wait(&full_bar[stage], phase, &abort_flag))) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_base + stage * CF::STAGE_BYTES;
           const uint64_t adesc = sw128_desc(sa), bdesc = sw128_desc(sa + CF::A_BYTES);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {   // 4 MMAs of 32 bytes of K (16 bf16 / 32 e4m3) per slice
             if constexpr (F8)
-              umma_e4m3(d_tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (kb | k) != 0);
+              umma_e4m3<PAIR>(d_tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (kb | k) != 0);
             else
-              umma_bf16(d_tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (kb | k) != 0);
+              umma_bf16<PAIR>(d_tmem, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (kb | k) != 0);
           }
-          umma_commit(&empty_bar[stage]);
+          if constexpr (PAIR) umma_commit_pair(&empty_bar[stage], 0x3);
+          else umma_commit(&empty_bar[stage]);
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
-        umma_commit(&accf_bar[buf]);
+        if constexpr (PAIR) umma_commit_pair(&accf_bar[buf], 0x3);
+        else umma_commit(&accf_bar[buf]);
       }
       if (!ok) {
         abort_flag = 1;
         atomicExch(status, (int)WM_ERR_TIMEOUT);
-        umma_commit(&drain_bar);  // completes once every MMA issued above has finished
+        // completes once every MMA issued above has finished
+        if constexpr (PAIR) umma_commit_pair(&drain_bar, 0x1);
+        else umma_commit(&drain_bar);
         volatile int never = 0;
         mbar_wait(&drain_bar, 0, &never);
       }
@@ -351,16 +427,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     constexpr int kChunkBytes = EPI == EPI_GELU_F8 ? 1024 : 2048;
     uint32_t staged = 0;                          // chunks this warp has staged (all tiles)
     int it = 0;
-    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+    for (int tile = unit; tile < num_tiles; tile += nunits, ++it) {
       const int buf = it & 1;
       const uint32_t acc_par = (uint32_t)(it >> 1) & 1u;
-      if (!mbar_wait(&accf_bar[buf], acc_par, &abort_flag)) {
+      if (!(PAIR ? mbar_wait_cluster(&accf_bar[buf], acc_par, &abort_flag)
+                 : mbar_wait(&accf_bar[buf], acc_par, &abort_flag))) {
         abort_flag = 1;
         atomicExch(status, (int)WM_ERR_TIMEOUT);
         break;
       }
       tc_fence_after();
-      const int m0 = (tile / num_n) * BM, n0 = (tile % num_n) * BN;
+      const int m0 = (tile / num_n) * TM + (int)rank * BM, n0 = (tile % num_n) * BN;
       const int row0 = m0 + quarter * 32;
       const int m = row0 + lane;
       const uint32_t tbase = tmem_base + (uint32_t)(buf * BN) + ((uint32_t)(quarter * 32) << 16);
@@ -402,9 +479,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         tmem_ld32(tbase + (uint32_t)c, v);
         if (c + 32 >= c_end) {
           // last TMEM read of this tile: hand the accumulator back to the MMA warp
+          // (of the even CTA, for a pair)
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&acce_bar[buf]);
+          if (lane == 0) {
+            if constexpr (PAIR) mbar_arrive_remote(mapa_shared(smem_u32(&acce_bar[buf]), 0));
+            else mbar_arrive(&acce_bar[buf]);
+          }
         }
         const int n = n0 + c;
         if (row0 >= M || n >= N) continue;   // whole chunk outside the output (warp-uniform)
@@ -548,19 +629,61 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   tc_fence_before();
   __syncthreads();
+  // a pair leaves together: the even CTA's MMAs read the odd CTA's shared
+  // memory, and both CTAs signal the even CTA's barriers
+  if constexpr (PAIR) cluster_sync();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(CF::TMEM_COLS)
-                 : "memory");
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(CF::TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(CF::TMEM_COLS)
+                   : "memory");
   }
 }
 
-template <int BN, int EPI, bool F8, bool DUAL = false>
+// How many two-CTA clusters of this kernel fit on the GPU at once (0 if none).
+template <int BN, int EPI, bool F8, bool DUAL>
+static int pair_capacity() {
+  static int cap = -1;
+  if (cap < 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * num_sms());
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = Cfg<BN, DUAL, true>::SMEM;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, gemm_bf16_tc_kernel<BN, EPI, F8, DUAL, true>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    cap = n;
+  }
+  return cap;
+}
+
+template <int BN, int EPI, bool F8, bool DUAL = false, bool PAIR = false>
 static wm_status launch_one(const GemmArgs& a, cudaStream_t s) {
-  using CF = Cfg<BN, DUAL>;
-  auto kern = gemm_bf16_tc_kernel<BN, EPI, F8, DUAL>;
-  const int tiles = ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
-  const int grid = tiles < num_sms() ? tiles : num_sms();
+  using CF = Cfg<BN, DUAL, PAIR>;
+  auto kern = gemm_bf16_tc_kernel<BN, EPI, F8, DUAL, PAIR>;
+  int grid;
+  if constexpr (PAIR) {
+    // persistent: every pair resident at once, each walking its share of the 256 x 256 tiles
+    const int tiles = ((a.M + 2 * BM - 1) / (2 * BM)) * ((a.N + BN - 1) / BN);
+    const int cap = pair_capacity<BN, EPI, F8, DUAL>();
+    if (cap < 1) return fail(WM_ERR_CUDA, "no two-CTA cluster of the pair GEMM fits on this GPU");
+    grid = 2 * (tiles < cap ? tiles : cap);
+  } else {
+    const int tiles = ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
+    grid = tiles < num_sms() ? tiles : num_sms();
+  }
   EpiArgs e;
   e.bias = a.bias;
   e.colsum = a.colsum;
@@ -571,16 +694,20 @@ static wm_status launch_one(const GemmArgs& a, cudaStream_t s) {
   e.alpha = a.alpha;
   e.out_scale = a.out_scale;
   e.rope = a.rope;
-  WM_CUDA(launch_pdl(kern, dim3(grid), dim3(THREADS), CF::SMEM, s, a.pdl, a.tmA, a.tmB, a.tmC, a.tmC2, a.M, a.N, a.K, e,
-                     device_status_word()));
+  if constexpr (PAIR)
+    WM_CUDA(launch_pdl_pairs(kern, dim3(grid), dim3(THREADS), CF::SMEM, s, a.pdl, a.tmA, a.tmB, a.tmC, a.tmC2, a.M, a.N,
+                             a.K, e, device_status_word()));
+  else
+    WM_CUDA(launch_pdl(kern, dim3(grid), dim3(THREADS), CF::SMEM, s, a.pdl, a.tmA, a.tmB, a.tmC, a.tmC2, a.M, a.N, a.K,
+                       e, device_status_word()));
   WM_CUDA(cudaGetLastError());
   return WM_OK;
 }
 
-template <int BN, int EPI, bool F8, bool DUAL = false>
+template <int BN, int EPI, bool F8, bool DUAL = false, bool PAIR = false>
 static wm_status set_attr() {
-  WM_CUDA(cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, EPI, F8, DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               Cfg<BN, DUAL>::SMEM));
+  WM_CUDA(cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, EPI, F8, DUAL, PAIR>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN, DUAL, PAIR>::SMEM));
   return WM_OK;
 }
 
@@ -601,7 +728,42 @@ static wm_status set_attrs_bn() {
   chk(set_attr<BN, EPI_STORE_F32, true>());
   chk(set_attr<BN, EPI_RESID_LN, true>());
   chk(set_attr<BN, EPI_RESID_LN, true, true>());
+  if constexpr (BN == 256) {
+    // pair tiles: the epilogues of the processor block's GEMMs
+    chk(set_attr<BN, EPI_RESID_LN, false, false, true>());
+    chk(set_attr<BN, EPI_RESID_LN, false, true, true>());
+    chk(set_attr<BN, EPI_LNF_STORE, false, false, true>());
+    chk(set_attr<BN, EPI_LNF_GELU, false, false, true>());
+    chk(set_attr<BN, EPI_GELU_F8, true, false, true>());
+    chk(set_attr<BN, EPI_RESID_LN, true, false, true>());
+    chk(set_attr<BN, EPI_RESID_LN, true, true, true>());
+    chk(set_attr<BN, EPI_STORE, false, false, true>());
+  }
   return st;
+}
+
+// The processor block's epilogues on 256 x 256 pair tiles (and a plain bf16
+// store for the per-op tests).
+static wm_status launch_pair(const GemmArgs& a, cudaStream_t s) {
+  const bool dual = a.dual >= 0 ? a.dual == 1 : a.K <= 1024;
+  if (a.f8) {
+    switch (a.epi) {
+      case EPI_GELU_F8: return launch_one<256, EPI_GELU_F8, true, false, true>(a, s);
+      case EPI_RESID_LN:
+        return dual ? launch_one<256, EPI_RESID_LN, true, true, true>(a, s)
+                    : launch_one<256, EPI_RESID_LN, true, false, true>(a, s);
+      default: return fail(WM_ERR_INVALID_ARG, "unsupported epilogue for the e4m3 pair GEMM");
+    }
+  }
+  switch (a.epi) {
+    case EPI_STORE: return launch_one<256, EPI_STORE, false, false, true>(a, s);
+    case EPI_RESID_LN:
+      return dual ? launch_one<256, EPI_RESID_LN, false, true, true>(a, s)
+                  : launch_one<256, EPI_RESID_LN, false, false, true>(a, s);
+    case EPI_LNF_STORE: return launch_one<256, EPI_LNF_STORE, false, false, true>(a, s);
+    case EPI_LNF_GELU: return launch_one<256, EPI_LNF_GELU, false, false, true>(a, s);
+    default: return fail(WM_ERR_INVALID_ARG, "unsupported epilogue for the bf16 pair GEMM");
+  }
 }
 
 template <int BN>
@@ -648,6 +810,10 @@ wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s) {
       (!a.stats || !a.colsum || !a.bias || a.np < 1 || a.N % 32 != 0))
     return fail(WM_ERR_INVALID_ARG, "LayerNorm-folded epilogue needs stats, colsum, bias, np >= 1, N % 32 == 0");
   if (a.K <= 0 || a.K % (a.f8 ? 16 : 8) != 0) return fail(WM_ERR_INVALID_ARG, "tcgen05 GEMM needs K > 0 and 16-byte rows");
+  if (a.pair) {
+    if (a.bn != 256 || a.N % 256 != 0) return fail(WM_ERR_INVALID_ARG, "pair GEMM tiles need BN = 256 and N % 256 == 0");
+    return tc::launch_pair(a, s);
+  }
   if (a.bn == 256) return tc::launch_bn<256>(a, s);
   if (a.bn == 128) return tc::launch_bn<128>(a, s);
   return fail(WM_ERR_INVALID_ARG, "GEMM tile width must be 128 or 256");

@@ -80,6 +80,27 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// launch_pdl for a grid of two-CTA clusters (consecutive blockIdx.x pairs).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl_pairs(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                    bool enable, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = enable ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Paired FP32 arithmetic (f32x2 instructions: one instruction, two lanes,
 // each rounded exactly as the scalar instruction) and a three-input max.
 __device__ __forceinline__ uint64_t pack_f2(float lo, float hi) {
@@ -214,6 +235,7 @@ struct GemmArgs {
   const RopeArgs* rope = nullptr;  // device pointer; EPI_LNF_STORE rotates q and k
   bool pdl = false;    // launch as a programmatic dependent of the previous kernel
   int dual = -1;       // EPI_RESID_LN: second staging tile (1) or not (0); -1: by K (K <= 1024)
+  bool pair = false;   // BN = 256 only: 256 x 256 tiles on CTA pairs (cta_group::2); tmB box of 128 rows
 };
 // Rotate q and k in an fp32 qkv [M, 3C] (the FP32 plain path).
 wm_status launch_rope_f32(float* qkv, long M, const RopeArgs* rope_dev, const RopeArgs& rope_host, cudaStream_t s);
