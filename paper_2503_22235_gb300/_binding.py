@@ -277,9 +277,13 @@ def wm_ctx_sizes(ctx, batch=1) -> tuple[int, int]:
 
 
 def wm_autotune_report() -> str:
-    buf = ctypes.create_string_buffer(1 << 16)
-    _check(lib().wm_autotune_report(buf, len(buf)))
-    return buf.value.decode()
+    size = 1 << 16
+    while True:   # the library truncates to the buffer: grow until the report fits
+        buf = ctypes.create_string_buffer(size)
+        _check(lib().wm_autotune_report(buf, len(buf)))
+        if len(buf.value) < size - 1 or size >= 1 << 26:
+            return buf.value.decode()
+        size *= 4
 
 
 def wm_ctx_reserve(ctx, batch):
