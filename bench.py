@@ -598,7 +598,7 @@ def fields_bench(wm, torch, dev, ctx, shape, lead=336, reps=2):
             "forecasts_per_s": 1e3 / fc_ms}
 
 
-def small_rollout(wm, torch, dev, reps=3):
+def small_rollout(wm, torch, dev, reps=10):
     s = synth.SMALL
     p6, p1 = synth.processor_weights(s, seed=0)
     ctx = wm.wm_create_from_host(wm.make_config(s, wm.WM_PREC_BF16), synth.pack_weights(p6, p1))
@@ -610,7 +610,9 @@ def small_rollout(wm, torch, dev, reps=3):
             wm.wm_set_precision(ctx, prec)
             for T in (336, 337):
                 x = x0.clone()
-                wm.wm_latent_rollout(ctx, x, T)         # capture + first replay
+                for _ in range(3):                      # capture + warm-up replays
+                    x.copy_(x0)
+                    wm.wm_latent_rollout(ctx, x, T)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
