@@ -16,24 +16,25 @@
 // (N = HR * 8, padded to 16), the softmax warps turn S into P in place, and
 // the tensor core accumulates O += P V.
 //
-// Warp roles (persistent CTAs, one per SM, 8 warps: two per SM sub-partition,
-// so each thread may use up to 255 registers):
-//   warps 0-3  softmax: warp q owns tensor-memory lanes 32q..32q+31, i.e.
-//              query rows 4q..4q+3 of the tile. Their windows cover kh + 3
-//              key rows, so each thread reads only those rows of S (8
-//              columns per key row, one 8-column tcgen05.ld each), masks
+// Warp roles (persistent CTAs, one per SM, 12 warps, up to 168 registers a thread):
+//   warps 0-7  softmax: warps q and q + 4 own tensor-memory lanes 32q..32q+31,
+//              i.e. query rows 4q..4q+3 of the tile. Their windows cover
+//              kh + 3 key rows; each of the two warps reads half of them
+//              (8 columns per key row, one 8-column tcgen05.ld each), masks
 //              keys outside its own window (bump rows, periodic or clamped
-//              columns), keeps a running max m and sum l in FP32 (the max
-//              moves only when a row's maximum grows by more than 2^8, and
-//              then O is rescaled in tensor memory), writes P = 2^(S - m) as
-//              bf16 pairs over the first half of its S columns, and zeros
-//              in the key rows its window does not reach. They also copy
-//              the next tile's queries into tensor memory (the A operand of
-//              Q K^T; loaded one step ahead) and write each finished tile's
-//              O / l to global memory one step into the next tile.
-//   warp 4     MMA issuer (one thread): QK(step + 2) is issued right after
+//              columns), and the pair combines its row maxima through shared
+//              memory once per step, so both keep the same running max m
+//              (which moves only when a row's maximum grows by more than
+//              2^8; then O is rescaled in tensor memory). Each writes
+//              P = 2^(S - m) as bf16 pairs over the first half of its rows'
+//              S columns, and zeros in alternate key rows the quarter's
+//              window does not reach. Warp q + 4 also copies the next tile's
+//              queries into tensor memory (the A operand of Q K^T; loaded
+//              one step ahead); warp q writes each finished tile's O / l to
+//              global memory one step into the next tile.
+//   warp 8     MMA issuer (one thread): QK(step + 2) is issued right after
 //              PV(step), so the other S buffer's softmax overlaps both.
-//   warps 5-7  loaders: cp.async 16-byte copies of the K/V slabs into a ring
+//   warps 9-11 loaders: cp.async 16-byte copies of the K/V slabs into a ring
 //              of NS stages. Layout of one (K or V, half): [group of 8 keys]
 //              [16-channel atom][8 keys x 32 bytes] with the 32-byte swizzle
 //              (the two 16-byte units of keys 4..7 of a group swap places),
@@ -54,7 +55,9 @@ namespace natc {
 
 using namespace ptx;
 
-constexpr int kSoftWarps = 4, kMmaWarp = 4, kLoadWarps = 3;
+// Two softmax warps per tensor-memory lane quarter (each takes half of the
+// quarter's key rows), one MMA warp, three loader warps.
+constexpr int kSoftWarps = 8, kMmaWarp = 8, kLoadWarps = 3;
 constexpr int kThreads = 32 * (kSoftWarps + 1 + kLoadWarps);
 constexpr int kMaxStages = 4;
 constexpr float kLazyLog2 = 8.f;   // the running max moves when a row max grows by more than this
@@ -65,7 +68,7 @@ struct Params {
   int* status;
   int B, D, H, W, C, heads, kd, periodic;
   int HR;      // key rows of a slab
-  int NPAD;    // keys of a half as the MMA reads them (HR * 8 rounded up to 16)
+  int NPAD;    // keys of a half as the MMA reads them: npad_for<KH>() ((16 + KH - 1) * 8, rounded up to 16)
   int NS;      // slab stages
   int tiles_h, tiles_w, ntiles;
   int colO, colQ;   // tensor-memory columns of O0 (O1 = +oStride) and Q0 (Q1 = +qStride)
@@ -226,9 +229,16 @@ __device__ __noinline__ bool softmax_epilogue(const Params& p, int ti, int lane,
   return true;
 }
 
+// Keys of a slab half as the MMAs read them: (16 + KH - 1) latitude rows x 8
+// columns, rounded up to 16, whatever the grid's height (rows past a short
+// grid's last latitude are zero padding, never in a window).
+template <int KH>
+constexpr int npad_for() { return ((16 + KH - 1) * 8 + 15) / 16 * 16; }
+
 template <int DH, int KH, int KW>
 __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
   constexpr int NA = DH / 16;       // 16-channel (32-byte) atoms per head
+  constexpr int kNpad = npad_for<KH>();   // p.NPAD, as a constant
   constexpr int WR = KH + 3;        // key rows a softmax warp reads
   constexpr int RH = KH / 2, RW = KW / 2;
   static_assert(DH % 16 == 0 && DH <= 64, "head dim");
@@ -238,6 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
   __shared__ __align__(8) uint64_t kv_full[kMaxStages], kv_empty[kMaxStages];
   __shared__ __align__(8) uint64_t s_full[2], p_ready[2], pv_done[2], q_full[2], q_empty[2], o_full[2], o_empty[2];
   __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ __align__(8) uint64_t xch_bar[4];   // per lane quarter: the two softmax warps' exchanges
+  __shared__ float xch_val[2][2][128];           // [exchange parity][warp of the quarter][query]
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
@@ -257,12 +269,13 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
       mbar_init(&s_full[i], 1);
       mbar_init(&p_ready[i], kSoftWarps);
       mbar_init(&pv_done[i], 1);
-      mbar_init(&q_full[i], kSoftWarps);
+      mbar_init(&q_full[i], kSoftWarps / 2);     // the second warp of each quarter stores Q
       mbar_init(&q_empty[i], 1);
       mbar_init(&o_full[i], 1);
-      mbar_init(&o_empty[i], kSoftWarps);
+      mbar_init(&o_empty[i], kSoftWarps / 2);    // the first warp of each quarter writes O out
     }
     mbar_init(&drain_bar, 1);
+    for (int i = 0; i < 4; ++i) mbar_init(&xch_bar[i], 64);   // every thread of a quarter's two warps
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -293,49 +306,82 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
   if (warp == kMmaWarp) {
     if (lane == 0) {
       // ------------------------------------------------------------ MMA issuer
+      // One thread issues every MMA of the CTA. Its instruction stream is on
+      // the critical path (an MMA waits for its operands' scalar arithmetic),
+      // so the step indices advance incrementally, descriptors are offsets
+      // from two precomputed ones, and both MMA loops are fully unrolled.
+      constexpr int NKV = kNpad / 16;                          // P V MMAs per step (16 keys each)
+      constexpr uint32_t GB = (uint32_t)NA * 256u;             // 8 keys x all atoms
+      constexpr uint32_t REGION = (uint32_t)NA * kNpad * 32u;  // one (stage, K or V, half) region
       constexpr uint32_t idesc_pv = idesc_bf16_ab(128, DH, 1);
-      const uint32_t idesc_qk = idesc_bf16_ab(128, p.NPAD, 0);
-      const uint32_t group_bytes = (uint32_t)NA * 256u;   // 8 keys x all atoms
-      auto issue_qk = [&](int v) -> bool {
-        const int ti = v / steps_per_tile, r = v - ti * steps_per_tile, l = r >> 1, h = r & 1;
-        const int g = ti * p.kd + l, stage = g % p.NS;
-        if (r == 0 && !mbar_wait(&q_full[ti & 1], (uint32_t)(ti >> 1) & 1u, &abort_flag)) return false;
-        if (h == 0 && !mbar_wait(&kv_full[stage], (uint32_t)(g / p.NS) & 1u, &abort_flag)) return false;
+      constexpr uint32_t idesc_qk = idesc_bf16_ab(128, kNpad, 0);
+      const uint64_t kdesc0 = desc_sw32(sbase, 16u, GB);       // region 0 as the K-major B of Q K^T
+      const uint64_t vdesc0 = desc_sw32(sbase, 256u, GB);      // region 0 as the MN-major B of P V
+      struct Cursor {   // a step: its tile, its index in the tile, the ring slot of its level
+        int ti = 0, r = 0, stage = 0;
+        uint32_t par = 0;
+      };
+      auto advance = [&](Cursor& c) {
+        if (c.r & 1) {   // a level ends with its second half
+          if (++c.stage == p.NS) {
+            c.stage = 0;
+            c.par ^= 1u;
+          }
+        }
+        if (++c.r == steps_per_tile) {
+          c.r = 0;
+          ++c.ti;
+        }
+      };
+      auto issue_qk = [&](const Cursor& c, int v) -> bool {
+        const int h = c.r & 1;
+        if (c.r == 0 && !mbar_wait(&q_full[c.ti & 1], (uint32_t)(c.ti >> 1) & 1u, &abort_flag)) return false;
+        if (h == 0 && !mbar_wait(&kv_full[c.stage], c.par, &abort_flag)) return false;
         tc_fence_after();
-        const uint32_t d = tmem + colS(v & 1);
-        const uint32_t a = tmem + (uint32_t)(p.colQ + (ti & 1) * p.qStride);
-        const uint32_t kb = sbase + region_off(p, NA, stage, 0, h);
+        const uint32_t d = tmem + (uint32_t)((v & 1) * kNpad);
+        const uint32_t a = tmem + (uint32_t)(p.colQ + (c.ti & 1) * p.qStride);
+        const uint64_t kd = kdesc0 + (uint64_t)(((uint32_t)(c.stage * 4 + h) * REGION) >> 4);
 #pragma unroll
-        for (int k = 0; k < NA; ++k)   // one 16-channel atom per MMA
-          umma_ts(d, a + 8u * k, desc_sw32(kb + 256u * k, 16u, group_bytes), idesc_qk, k > 0);
+        for (int k = 0; k < NA; ++k)   // one 16-channel atom (256 bytes along a group) per MMA
+          umma_ts(d, a + 8u * k, kd + (uint64_t)(16 * k), idesc_qk, k > 0);
         umma_commit(&s_full[v & 1]);
-        if (r == steps_per_tile - 1) umma_commit(&q_empty[ti & 1]);
+        if (c.r == steps_per_tile - 1) umma_commit(&q_empty[c.ti & 1]);
         return true;
       };
-      auto issue_pv = [&](int u) -> bool {
-        const int ti = u / steps_per_tile, r = u - ti * steps_per_tile, l = r >> 1, h = r & 1;
-        const int g = ti * p.kd + l, stage = g % p.NS;
+      auto issue_pv = [&](const Cursor& c, int u) -> bool {
+        const int h = c.r & 1;
         if (!mbar_wait(&p_ready[u & 1], (uint32_t)(u >> 1) & 1u, &abort_flag)) return false;
-        if (r == 0 && !mbar_wait(&o_empty[ti & 1], ((uint32_t)(ti >> 1) & 1u) ^ 1u, &abort_flag)) return false;
+        if (c.r == 0 && !mbar_wait(&o_empty[c.ti & 1], ((uint32_t)(c.ti >> 1) & 1u) ^ 1u, &abort_flag)) return false;
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(p.colO + (ti & 1) * p.oStride);
-        const uint32_t a = tmem + colS(u & 1);
-        const uint32_t vb = sbase + region_off(p, NA, stage, 1, h);
-        const int nk = p.NPAD / 16;
-        for (int k = 0; k < nk; ++k)       // 16 keys = 2 groups per MMA
-          umma_ts(d, a + 8u * k, desc_sw32(vb + 2u * group_bytes * k, 256u, group_bytes), idesc_pv,
-                  (r > 0 || k > 0) ? 1u : 0u);
+        const uint32_t d = tmem + (uint32_t)(p.colO + (c.ti & 1) * p.oStride);
+        const uint32_t a = tmem + (uint32_t)((u & 1) * kNpad);
+        const uint64_t vd = vdesc0 + (uint64_t)(((uint32_t)(c.stage * 4 + 2 + h) * REGION) >> 4);
+        const uint32_t acc0 = c.r > 0 ? 1u : 0u;
+#pragma unroll
+        for (int k = 0; k < NKV; ++k)       // 16 keys = 2 groups per MMA
+          umma_ts(d, a + 8u * k, vd + (uint64_t)((2u * GB * k) >> 4), idesc_pv, k > 0 ? 1u : acc0);
         umma_commit(&pv_done[u & 1]);
-        if (h == 1) umma_commit(&kv_empty[stage]);
-        if (r == steps_per_tile - 1) umma_commit(&o_full[ti & 1]);
+        if (h == 1) umma_commit(&kv_empty[c.stage]);
+        if (c.r == steps_per_tile - 1) umma_commit(&o_full[c.ti & 1]);
         return true;
       };
+      Cursor cq, cv;
       bool ok = true;
-      if (nsteps > 0) ok = issue_qk(0);
-      if (ok && nsteps > 1) ok = issue_qk(1);
+      if (nsteps > 0) {
+        ok = issue_qk(cq, 0);
+        advance(cq);
+      }
+      if (ok && nsteps > 1) {
+        ok = issue_qk(cq, 1);
+        advance(cq);
+      }
       for (int u = 0; u < nsteps && ok; ++u) {
-        ok = issue_pv(u);
-        if (ok && u + 2 < nsteps) ok = issue_qk(u + 2);
+        ok = issue_pv(cv, u);
+        advance(cv);
+        if (ok && u + 2 < nsteps) {
+          ok = issue_qk(cq, u + 2);
+          advance(cq);
+        }
       }
       if (!ok) {
         abort_flag = 1;
@@ -416,14 +462,42 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
     }
   } else {
     // --------------------------------------------------------------- softmax
-    const int q = warp;   // tensor-memory lane quarter = query rows 4q..4q+3
+    // Warp w: tensor-memory lane quarter q = w % 4 (query rows 4q..4q+3 of
+    // the tile) and half `part` = w / 4 of the quarter's WR key rows. The two
+    // warps of a quarter share the running max: they exchange their partial
+    // row maxima once per step (and their row sums once per tile) through
+    // shared memory and a bounded mbarrier. The first warp of a quarter
+    // rescales O and writes it out; the second loads the next tile's Q.
+    constexpr int WN = WR / 2;   // key rows of one warp (WR = KH + 3 is even)
+    static_assert(WR % 2 == 0, "the two warps of a quarter split its key rows evenly");
+    const int q = warp & 3, part = warp >> 2;
+    const int RB = part * WN;    // this warp's first row among the quarter's WR
+    const int qlane = 32 * q + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
     const uint64_t scale2 = pack_f2(p.scale_log2, p.scale_log2);
     const uint64_t neg2 = pack_f2(-INFINITY, -INFINITY);
     bool ok = true;
+    uint32_t xcnt = 0;   // exchanges so far (the mbarrier's phase)
+    // this lane's value against the other warp's for the same query
+    auto exchange = [&](float v, float& other) -> bool {
+      const int sl = (int)(xcnt & 1u);   // two slots: the partner is at most one exchange ahead
+      xch_val[sl][part][qlane] = v;
+      mbar_arrive(&xch_bar[q]);
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&xch_bar[q], xcnt & 1u, &abort_flag));
+      ++xcnt;
+      if (got) other = xch_val[sl][part ^ 1][qlane];
+      return got;
+    };
+    // both warps of the quarter have passed this point (the same mbarrier)
+    auto pair_sync = [&]() -> bool {
+      mbar_arrive(&xch_bar[q]);
+      const bool got = __all_sync(0xffffffffu, mbar_wait(&xch_bar[q], xcnt & 1u, &abort_flag));
+      ++xcnt;
+      return got;
+    };
 
     uint4 qnext[DH / 8];   // the next tile's query, prefetched one step before its store
-    if (my_tiles > 0) {
+    if (my_tiles > 0 && part == 1) {
       softmax_load_q<DH, KH, KW>(p, 0, q, lane, qnext);
       ok = softmax_store_q<DH>(p, 0, lane, lane_base, qnext, q_empty, q_full, &abort_flag);
     }
@@ -439,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
       const int ra = clampi(ac - RH, 0, p.H - KH) - G.s_lat;                  // first window row in the slab
       const int cb = p.periodic ? wc - G.w0 : clampi(wc - RW, 0, p.W - KW) - G.s_lon;   // first window column
       const int a0 = min(G.h0 + 4 * q, p.H - 1);
-      const int R0 = min(clampi(a0 - RH, 0, p.H - KH) - G.s_lat, p.HR - WR);  // the warp's first key row
+      const int R0 = min(clampi(a0 - RH, 0, p.H - KH) - G.s_lat, p.HR - WR);  // the quarter's first key row
       const int rlo = ra - R0;                                                // 0 .. 3
       uint64_t cbias[2][4];   // per half: (0 | -inf) pairs for the 8 columns of a key row
 #pragma unroll
@@ -466,26 +540,27 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
         uint64_t cbh[4];   // this half's column bias pairs
 #pragma unroll
         for (int j = 0; j < 4; ++j) cbh[j] = h ? cbias[1][j] : cbias[0][j];
-        // One pass over this step's key rows (read from tensor memory in
-        // groups of RG rows): scale and mask, track the row max, and -- when
-        // with_p -- P = 2^(t - mref) as bf16 pairs into pk with its row sum.
-        constexpr int RG = (WR + 1) / 2;
-        uint32_t pk[WR][4];
+        // One pass over this warp's key rows of the step (read from tensor
+        // memory in groups of RG rows): scale and mask, track the row max,
+        // and -- when with_p -- P = 2^(t - mref) as bf16 pairs into pk with
+        // its row sum.
+        constexpr int RG = (WN + 1) / 2;
+        uint32_t pk[WN][4];
         auto pass = [&](bool with_p, float mref, float& mx, float& ls) {
           const uint64_t mref2 = pack_f2(mref, mref);
           float ls0 = 0.f, ls1 = 0.f;
 #pragma unroll
-          for (int g0 = 0; g0 < WR; g0 += RG) {
+          for (int g0 = 0; g0 < WN; g0 += RG) {
             uint32_t sr[RG][8];
 #pragma unroll
             for (int i = 0; i < RG; ++i)
-              if (g0 + i < WR) tmem_ld8_nowait(scol + 8u * (uint32_t)(R0 + g0 + i), sr[i]);
+              if (g0 + i < WN) tmem_ld8_nowait(scol + 8u * (uint32_t)(R0 + RB + g0 + i), sr[i]);
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < RG; ++i) {
-              const int rr = g0 + i;
-              if (rr < WR) {
-                const bool rok = (unsigned)(rr - rlo) < (unsigned)KH;
+              const int wi = g0 + i;
+              if (wi < WN) {
+                const bool rok = (unsigned)(RB + wi - rlo) < (unsigned)KH;
                 float t[8];
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
@@ -500,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
                     sub_f2(d0, d1, t[2 * j], t[2 * j + 1], mref2);
                     const float e0 = ex2(d0), e1 = ex2(d1);
                     add_f2(ls0, ls1, ls0, ls1, e0, e1);
-                    pk[rr][j] = pack_bf16(e0, e1);
+                    pk[wi][j] = pack_bf16(e0, e1);
                   }
                 }
               }
@@ -510,39 +585,49 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
         };
         // Single pass against the current running max; the step is redone
         // only when some row's max grows by more than 2^kLazyLog2 (always on
-        // a tile's first step, where the max is not set yet). The decision is
-        // warp-uniform: the tensor-memory loads are warp-collective, and a
-        // row whose max did not move recomputes the same values.
+        // a tile's first step, where the max is not set yet). The row max is
+        // the two warps' combined one, so both warps of a quarter take the
+        // same decisions; they are warp-uniform (the tensor-memory loads are
+        // warp-collective), and a row whose max did not move recomputes the
+        // same values.
         const bool first = (r == 0);
         float mx = -INFINITY, ls = 0.f;
         pass(!first, m == -INFINITY ? 0.f : m, mx, ls);
+        float mo = -INFINITY;
+        if (!exchange(mx, mo)) {
+          ok = false;
+          break;
+        }
+        mx = fmaxf(mx, mo);
         const bool grow = mx > m + kLazyLog2;
         if (first || __any_sync(0xffffffffu, grow)) {
           const bool rescale = grow && m != -INFINITY;
           if (__any_sync(0xffffffffu, rescale)) {
-            // O already holds earlier steps of this tile: wait for the last
-            // PV, then rescale O (alpha = 1 for rows that keep their max)
-            const int up = u - 1;
-            if (!__all_sync(0xffffffffu, mbar_wait(&pv_done[up & 1], (uint32_t)(up >> 1) & 1u, &abort_flag))) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
             const float alpha = rescale ? ex2(m - mx) : 1.f;
-            const uint64_t alpha2 = pack_f2(alpha, alpha);
-#pragma unroll
-            for (int c = 0; c < DH / 8; ++c) {
-              uint32_t v[8];
-              tmem_ld8_nowait(ocol + 8u * c, v);
-              tmem_wait_ld();
-#pragma unroll
-              for (int i = 0; i < 8; i += 2) {
-                float x0 = __uint_as_float(v[i]), x1 = __uint_as_float(v[i + 1]);
-                mul_f2(x0, x1, alpha2);
-                v[i] = __float_as_uint(x0);
-                v[i + 1] = __float_as_uint(x1);
+            if (part == 0) {
+              // O already holds earlier steps of this tile: wait for the last
+              // PV, then rescale O (alpha = 1 for rows that keep their max)
+              const int up = u - 1;
+              if (!__all_sync(0xffffffffu, mbar_wait(&pv_done[up & 1], (uint32_t)(up >> 1) & 1u, &abort_flag))) {
+                ok = false;
+                break;
               }
-              tmem_st8(ocol + 8u * c, v);
+              tc_fence_after();
+              const uint64_t alpha2 = pack_f2(alpha, alpha);
+#pragma unroll
+              for (int c = 0; c < DH / 8; ++c) {
+                uint32_t v[8];
+                tmem_ld8_nowait(ocol + 8u * c, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 8; i += 2) {
+                  float x0 = __uint_as_float(v[i]), x1 = __uint_as_float(v[i + 1]);
+                  mul_f2(x0, x1, alpha2);
+                  v[i] = __float_as_uint(x0);
+                  v[i + 1] = __float_as_uint(x1);
+                }
+                tmem_st8(ocol + 8u * c, v);
+              }
             }
             lsum *= alpha;
           }
@@ -551,36 +636,56 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
           pass(true, m == -INFINITY ? 0.f : m, mx2, ls);
         }
         lsum += ls;
-        // P over the first half of this step's S columns: key row R0 + rr ->
-        // P columns 4 (R0 + rr) .. + 3
+        // P of key row k goes to the S columns of key row k / 2, and the zeros
+        // of rows past the window land on S rows of this quarter too: both
+        // warps must have read all their S rows first
+        if (!pair_sync()) {
+          ok = false;
+          break;
+        }
+        // P over the first half of this step's S columns: key row R0 + RB + i
+        // -> P columns 4 (R0 + RB + i) .. + 3
 #pragma unroll
-        for (int rr = 0; rr < WR; ++rr)
-          tmem_st4(scol + 4u * (uint32_t)(R0 + rr), pk[rr][0], pk[rr][1], pk[rr][2], pk[rr][3]);
-        // zeros in the key rows outside the warp's window
-        for (int kr = 0; kr < R0; ++kr) tmem_st4(scol + 4u * kr, 0u, 0u, 0u, 0u);
-        for (int kr = R0 + WR; kr < p.NPAD / 8; ++kr) tmem_st4(scol + 4u * kr, 0u, 0u, 0u, 0u);
+        for (int i = 0; i < WN; ++i)
+          tmem_st4(scol + 4u * (uint32_t)(R0 + RB + i), pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+        // zeros in the key rows outside the quarter's window (alternate rows per warp)
+        for (int kr = part; kr < R0; kr += 2) tmem_st4(scol + 4u * kr, 0u, 0u, 0u, 0u);
+        for (int kr = R0 + WR + ((R0 + WR + part) & 1); kr < p.NPAD / 8; kr += 2)
+          tmem_st4(scol + 4u * kr, 0u, 0u, 0u, 0u);
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&p_ready[u & 1]);
-        // the next tile's queries: loaded after step 0, stored after step 1;
-        // the previous tile's output after step 1 (its last P V is done by then)
-        if (r == 0 && ti + 1 < my_tiles) softmax_load_q<DH, KH, KW>(p, ti + 1, q, lane, qnext);
+        // the next tile's queries (second warp): loaded after step 0, stored
+        // after step 1; the previous tile's output (first warp) after step 1
+        // (its last P V is done by then)
+        if (part == 1 && r == 0 && ti + 1 < my_tiles) softmax_load_q<DH, KH, KW>(p, ti + 1, q, lane, qnext);
         if (r == 1) {
-          if (ti > 0 && !softmax_epilogue<DH>(p, ti - 1, lane, lane_base, prev_l, prev_orow, prev_valid, o_full,
-                                              o_empty, &abort_flag)) { ok = false; break; }
-          if (ti + 1 < my_tiles &&
+          if (part == 0 && ti > 0 &&
+              !softmax_epilogue<DH>(p, ti - 1, lane, lane_base, prev_l, prev_orow, prev_valid, o_full, o_empty,
+                                    &abort_flag)) {
+            ok = false;
+            break;
+          }
+          if (part == 1 && ti + 1 < my_tiles &&
               !softmax_store_q<DH>(p, ti + 1, lane, lane_base, qnext, q_empty, q_full, &abort_flag)) {
             ok = false;
             break;
           }
         }
       }
-      prev_l = lsum;
+      if (!ok) break;
+      // the quarter's row sum: this warp's keys plus the other warp's
+      float lo = 0.f;
+      if (!exchange(lsum, lo)) {
+        ok = false;
+        break;
+      }
+      prev_l = lsum + lo;
       prev_orow = orow;
       prev_valid = valid;
     }
-    if (ok && my_tiles > 0)
+    if (ok && my_tiles > 0 && part == 0)
       ok = softmax_epilogue<DH>(p, my_tiles - 1, lane, lane_base, prev_l, prev_orow, prev_valid, o_full, o_empty,
                                 &abort_flag);
     if (!ok) {
@@ -599,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
 
 // ------------------------------------------------------------------ host ----
 
-constexpr int kSmemLimit = 226 * 1024;   // dynamic shared memory; the rest of the 227 KB is static (barriers)
+constexpr int kSmemLimit = 224 * 1024;   // dynamic shared memory; the rest of the 227 KB is static (barriers, exchanges)
 
 struct Layout {
   int HR, NPAD, NS, colO, colQ, oStride, qStride;
@@ -616,7 +721,7 @@ bool layout_for(int H, int W, int dh, int kh, int kw, bool periodic, Layout* L) 
   L->HR = std::min(16 + kh - 1, H);
   if (L->HR < kh + 3) return false;                       // a warp's key rows must fit the slab
   if (!periodic && W < kw + 7) return false;
-  L->NPAD = round_up(L->HR * 8, 16);
+  L->NPAD = round_up((16 + kh - 1) * 8, 16);   // npad_for<kh>(): the kernel's constant
   if (L->NPAD > 256) return false;
   L->oStride = round_up(dh, 16);
   L->qStride = round_up(dh / 2, 16);
