@@ -49,7 +49,9 @@ typedef enum {
   WM_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out; the context stays usable */
   WM_ERR_BUSY = 5,         /* server admission: the HBM budget or slot table is full */
   WM_ERR_IO = 6,           /* weight file missing, short or malformed */
-  WM_ERR_NOT_FOUND = 7     /* unknown request id */
+  WM_ERR_NOT_FOUND = 7,    /* unknown request id */
+  WM_ERR_BOUNDS = 8        /* debug build (libwm_debug.so) only: a device-side index check failed
+                              (attention window or slab geometry, tail tile); the access was skipped */
 } wm_status;
 
 typedef enum { WM_P6 = 0 /* six-hour processor */, WM_P1 = 1 /* one-hour processor */ } wm_processor;
@@ -225,7 +227,9 @@ wm_status wm_rel_l2_noalloc(const float* a, const float* b, size_t n, double* ou
 wm_status wm_count_nonfinite(const float* x, size_t n, unsigned long long* count, void* stream);
 
 /* Reads (and clears) the device status word that bounded device-side waits
- * write; synchronises the device. WM_OK or WM_ERR_TIMEOUT. (Library service.) */
+ * (and, in the debug build, the device-side index checks) write; synchronises
+ * the device. WM_OK, WM_ERR_TIMEOUT or (debug build) WM_ERR_BOUNDS.
+ * (Library service.) */
 wm_status wm_device_status(void);
 
 /* Self-test of the bounded-wait path: launches one kernel that waits on a

@@ -12,10 +12,12 @@ import os
 import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libwm.so")
+# WM_LIBRARY=debug loads the debug build (device-side bounds checks, see build.py)
+LIB_PATH = os.path.join(HERE, "libwm_debug.so" if os.environ.get("WM_LIBRARY") == "debug" else "libwm.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "wm.h")
 
-WM_OK, WM_ERR_INVALID_ARG, WM_ERR_OOM, WM_ERR_CUDA, WM_ERR_TIMEOUT, WM_ERR_BUSY, WM_ERR_IO, WM_ERR_NOT_FOUND = range(8)
+WM_OK, WM_ERR_INVALID_ARG, WM_ERR_OOM, WM_ERR_CUDA, WM_ERR_TIMEOUT, WM_ERR_BUSY, WM_ERR_IO, WM_ERR_NOT_FOUND, \
+    WM_ERR_BOUNDS = range(9)
 WM_P6, WM_P1 = 0, 1
 WM_PREC_FP32, WM_PREC_BF16, WM_PREC_BF16_FP8MLP = 0, 1, 2
 EPI_STORE, EPI_GELU, EPI_RESID_F32, EPI_STORE_F32, EPI_GELU_F8 = 0, 1, 2, 3, 4

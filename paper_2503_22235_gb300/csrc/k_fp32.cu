@@ -470,7 +470,8 @@ __global__ void na_f32_kernel(const float* __restrict__ qkv, float* __restrict__
 template <int DH>
 __global__ void __launch_bounds__(256, 2) na_f32_tile_kernel(const float* __restrict__ qkv, float* __restrict__ out,
                                                           int B, int D, int H, int W, int C, int heads, int kd, int kh,
-                                                          int kw, int periodic, int tiles_h, int tiles_w) {
+                                                          int kw, int periodic, int tiles_h, int tiles_w,
+                                                          int* __restrict__ dstatus) {
   constexpr int TH = 8, TW = 8, TPQ = 4, HD = DH / TPQ, KS = DH + 4;   // KS: key row stride in shared memory (floats)
   constexpr int KW_MAX = 9;
   extern __shared__ __align__(16) float sm[];
@@ -492,10 +493,17 @@ __global__ void __launch_bounds__(256, 2) na_f32_tile_kernel(const float* __rest
   const int ld0 = clampi(d - kd / 2, 0, D - kd);
   const int pair = threadIdx.x / TPQ, half = threadIdx.x % TPQ;   // query of the tile, channel quarter
   const int hq = h0 + pair / TW, wq = w0 + pair % TW;
-  const bool valid = hq < H && wq < W;
+  bool valid = hq < H && wq < W;
   const int hc = min(hq, H - 1), wc = min(wq, W - 1);
-  const int ra = clampi(hc - rh, 0, H - kh) - hs0;                                   // window rows in the slab
-  const int cb = (periodic ? wc - rw : clampi(wc - rw, 0, W - kw)) - ws0;            // window columns
+  int ra = clampi(hc - rh, 0, H - kh) - hs0;                                   // window rows in the slab
+  int cb = (periodic ? wc - rw : clampi(wc - rw, 0, W - kw)) - ws0;            // window columns
+  // debug builds: the window lies inside the staged slab; on a failure it is
+  // clamped into the slab and the query is not written
+  if (!WM_DCHECK(ra >= 0 && ra + kh <= HR && cb >= 0 && cb + kw <= WC && ld0 >= 0 && ld0 + kd <= D, dstatus)) {
+    ra = clampi(ra, 0, HR - kh);
+    cb = clampi(cb, 0, WC - kw);
+    valid = false;
+  }
   const long N = (long)D * H * W, C3 = 3L * C;
   const float scale = rsqrtf((float)DH);
   float q[HD], o[HD];
@@ -615,10 +623,10 @@ wm_status launch_na_f32(const float* qkv, float* out, int B, int D, int H, int W
     const dim3 grid((unsigned)ctas), block(256);
     const int per = periodic ? 1 : 0;
     switch (dh0) {
-      case 16: na_f32_tile_kernel<16><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w); break;
-      case 32: na_f32_tile_kernel<32><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w); break;
-      case 48: na_f32_tile_kernel<48><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w); break;
-      default: na_f32_tile_kernel<64><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w); break;
+      case 16: na_f32_tile_kernel<16><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w, device_status_word()); break;
+      case 32: na_f32_tile_kernel<32><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w, device_status_word()); break;
+      case 48: na_f32_tile_kernel<48><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w, device_status_word()); break;
+      default: na_f32_tile_kernel<64><<<grid, block, tsm, s>>>(qkv, out, B, D, H, W, C, heads, kd, kh, kw, per, tiles_h, tiles_w, device_status_word()); break;
     }
     WM_CUDA(cudaGetLastError());
     return WM_OK;

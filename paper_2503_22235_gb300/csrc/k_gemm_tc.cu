@@ -467,7 +467,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       if constexpr (kResLN) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) xa[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (row0 < M && m < M && n0 + c_begin < N) {
+        // debug builds: the tile's half lies inside the row (N % BN == 0 for this epilogue)
+        if (row0 < M && m < M && n0 + c_begin < N && WM_DCHECK(n0 + c_end <= N, status)) {
           const float4* xo = reinterpret_cast<const float4*>(e.x + (size_t)m * N + n0 + c_begin);
 #pragma unroll
           for (int q = 0; q < 8; ++q) xa[q] = xo[q];

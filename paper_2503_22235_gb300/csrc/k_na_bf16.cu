@@ -41,6 +41,7 @@ struct Params {
   int slab;               // elements between the K and V slabs (and between ring buffers / 2); multiple of 64
   int tma;                // persistent kernel: non-wrapping slabs by one tensor copy each for K and V
   float scale_log2;       // log2(e) / sqrt(dh)
+  int* dstatus;           // the device status word (debug builds record index-check failures there)
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -123,6 +124,12 @@ __device__ __forceinline__ Tile make_tile(const Params& p, int t) {
   T.hs0 = clampi(T.h0 - rh, 0, p.H - p.kh);
   T.HR = clampi(min(T.h0 + TH, p.H) - 1 - rh, 0, p.H - p.kh) + p.kh - T.hs0;
   T.ws0 = p.periodic ? (T.w0 - rw) : clampi(T.w0 - rw, 0, p.W - p.kw);
+  // debug builds: the key levels, the slab rows and its first column lie where
+  // the loaders and the warps assume; a tile that fails loads nothing
+  bool ok = WM_DCHECK(T.ld0 >= 0 && T.ld0 + p.kd <= p.D, p.dstatus);
+  ok = WM_DCHECK(T.hs0 >= 0 && T.HR >= p.kh && T.HR <= p.HRmax && T.hs0 + T.HR <= p.H, p.dstatus) && ok;
+  ok = WM_DCHECK(p.periodic ? (T.ws0 >= -rw && T.ws0 < p.W) : (T.ws0 >= 0 && T.ws0 + p.kw <= p.W), p.dstatus) && ok;
+  if (!ok) T.HR = 0;
   return T;
 }
 
@@ -204,6 +211,17 @@ __device__ __forceinline__ void warp_begin(WarpQ<DH, LS>& q, const Params& p, co
   q.wc0 = p.periodic ? (ww0 - T.w0) : (clampi(min(ww0, W - 1) - rw, 0, W - p.kw) - T.ws0);
   q.nkeys = (wr1 - q.wr0) << LS;
   q.ngroups = (q.nkeys + 15) / 16;
+  // debug builds: the warp's key rectangle lies inside the slab, and each
+  // query's window inside the rectangle; a warp that fails computes nothing
+  if (q.live) {
+    bool ok = WM_DCHECK(q.wr0 >= 0 && wr1 <= T.HR && q.wc0 >= 0 && q.wc0 + (1 << LS) <= p.WC, p.dstatus);
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+      ok = WM_DCHECK(qsr[rr] >= q.wr0 && qsr[rr] + p.kh <= wr1 && qsc[rr] >= q.wc0 &&
+                         qsc[rr] + p.kw <= q.wc0 + (1 << LS),
+                     p.dstatus) && ok;
+    if (!ok) q.live = false;
+  }
   uint32_t colmask[2];
 #pragma unroll
   for (int rr = 0; rr < 2; ++rr) {
@@ -492,6 +510,10 @@ __device__ __forceinline__ void warp_begin_t(WarpQT<DH, LS>& q, const Params& p,
   q.wc0 = p.periodic ? (ww0 - T.w0) : (clampi(min(ww0, W - 1) - rw, 0, W - p.kw) - T.ws0);
   q.nkeys = (wr1 - q.wr0) << LS;
   q.ngroups = (q.nkeys + 15) / 16;
+  // debug builds: the warp's key rectangle lies inside the slab (each query's
+  // window is checked below); a warp that fails computes nothing
+  if (q.live && !WM_DCHECK(q.wr0 >= 0 && wr1 <= T.HR && q.wc0 >= 0 && q.wc0 + (1 << LS) <= p.WC, p.dstatus))
+    q.live = false;
   // the thread's two softmax queries (columns 2 t4, 2 t4 + 1)
   float cb[2][2][2];
 #pragma unroll
@@ -500,6 +522,10 @@ __device__ __forceinline__ void warp_begin_t(WarpQT<DH, LS>& q, const Params& p,
     const int hc = min(wh0 + qi / p.WW, H - 1), wc = min(ww0 + qi % p.WW, W - 1);
     q.rlo[k] = clampi(hc - rh, 0, H - p.kh) - T.hs0 - q.wr0;
     const int qsc = p.periodic ? (wc - T.w0) : (clampi(wc - rw, 0, W - p.kw) - T.ws0);
+    if (q.live && !WM_DCHECK(q.rlo[k] >= 0 && q.rlo[k] + p.kh <= wr1 - q.wr0 && qsc >= q.wc0 &&
+                                 qsc + p.kw <= q.wc0 + (1 << LS),
+                             p.dstatus))
+      q.live = false;
     const uint32_t colmask = (0xFFFFFFFFu >> (32 - p.kw)) << max(qsc - q.wc0, 0);
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf)
@@ -1135,6 +1161,7 @@ na::Params make_params(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int 
   p.out = out;
   p.B = B; p.D = D; p.H = H; p.W = W; p.C = C; p.heads = heads;
   p.kd = kd; p.kh = kh; p.kw = kw; p.periodic = periodic ? 1 : 0;
+  p.dstatus = device_status_word();
   return p;
 }
 

@@ -414,6 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
         } else {
           lon = min(lon, p.W - 1);   // columns past the grid are never loaded (spare) or masked
         }
+        if (!WM_DCHECK(lon >= 0 && lon < p.W, p.status)) lon = 0;   // debug builds
         lonoff[hq] = lon * (int)C3;
       }
       const __nv_bfloat16* chan = p.qkv + (long)G.head * DH + la * 16 + lu * 8;
@@ -508,13 +509,23 @@ __global__ void __launch_bounds__(kThreads, 1) na_tc_kernel(const Params p) {
       const TileGeo G = tile_geo<KH, KW>(p, blockIdx.x + ti * gridDim.x);
       // this lane's query and its window inside the slab
       const int a = G.h0 + 4 * q + (lane >> 3), w = G.w0 + (lane & 7);
-      const bool valid = a < p.H && w < p.W;
       const int ac = min(a, p.H - 1), wc = min(w, p.W - 1);
       const int ra = clampi(ac - RH, 0, p.H - KH) - G.s_lat;                  // first window row in the slab
       const int cb = p.periodic ? wc - G.w0 : clampi(wc - RW, 0, p.W - KW) - G.s_lon;   // first window column
       const int a0 = min(G.h0 + 4 * q, p.H - 1);
-      const int R0 = min(clampi(a0 - RH, 0, p.H - KH) - G.s_lat, p.HR - WR);  // the quarter's first key row
-      const int rlo = ra - R0;                                                // 0 .. 3
+      int R0 = min(clampi(a0 - RH, 0, p.H - KH) - G.s_lat, p.HR - WR);  // the quarter's first key row
+      int rlo = ra - R0;                                                // 0 .. 3
+      // debug builds: the quarter's key rows lie inside the slab and this
+      // query's window inside them and inside the slab's 16 columns; on a
+      // failure the rows are clamped into the slab and the query is not written
+      const bool geo = WM_DCHECK(R0 >= 0 && R0 + WR <= p.HR && p.HR <= kNpad / 8, p.status) &&
+                       WM_DCHECK(rlo >= 0 && rlo + KH <= WR && cb >= 0 && cb + KW <= 16, p.status);
+      bool valid = a < p.H && w < p.W;
+      if (!geo) {
+        R0 = clampi(R0, 0, kNpad / 8 - WR);
+        rlo = clampi(rlo, 0, WR - KH);
+        valid = false;
+      }
       uint64_t cbias[2][4];   // per half: (0 | -inf) pairs for the 8 columns of a key row
 #pragma unroll
       for (int h = 0; h < 2; ++h)

@@ -45,6 +45,23 @@ struct NvtxRange {
 // Device status word written by bounded device-side waits (one per device).
 int* device_status_word();
 
+// Debug builds (WM_DEBUG_CHECKS=1, libwm_debug.so): WM_DCHECK(cond, status)
+// is a device-side index check; when cond is false it records
+// WM_ERR_BOUNDS in the status word (first failure wins) and yields false so
+// that the caller skips the access. Release builds compile it to true.
+#ifndef WM_DEBUG_CHECKS
+#define WM_DEBUG_CHECKS 0
+#endif
+#if WM_DEBUG_CHECKS
+__device__ __forceinline__ bool dcheck_fail(int* status) {
+  if (status) atomicCAS(status, 0, (int)WM_ERR_BOUNDS);
+  return false;
+}
+#define WM_DCHECK(cond, status) ((cond) ? true : ::wm::dcheck_fail(status))
+#else
+#define WM_DCHECK(cond, status) true
+#endif
+
 // Upper bound on any single device-side spin-wait (nanoseconds).
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;
 

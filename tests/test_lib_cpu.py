@@ -23,6 +23,22 @@ def test_library_exports_every_declared_function():
     assert not missing, missing
 
 
+def test_debug_build_exports_the_same_functions_and_status_codes():
+    """libwm_debug.so (WM_DEBUG_CHECKS=1: device-side index checks) builds from
+    the same sources, exports every declared function, and the header's
+    WM_ERR_BOUNDS is the binding's."""
+    path = wm_build.build(debug=True)
+    assert path.endswith("libwm_debug.so")
+    D = ctypes.CDLL(path)
+    missing = [n for n in wm.header_functions() if not hasattr(D, n)]
+    assert not missing, missing
+    import os
+    import re
+    with open(os.path.join(os.path.dirname(wm_build.HERE), "include", "wm.h")) as f:
+        hdr = f.read()
+    assert int(re.search(r"WM_ERR_BOUNDS = (\d+)", hdr).group(1)) == wm.WM_ERR_BOUNDS
+
+
 def test_schedule_matches_oracle():
     for T in range(0, 1001):
         assert wm.wm_schedule(T) == orc.greedy_schedule(T)
