@@ -354,6 +354,15 @@ wm_status wm_fp8_scales(wm_ctx* ctx, int which, int block, float* out);
  * WM_ERR_INVALID_ARG for a mode outside 0..3. */
 wm_status wm_gemm_tile_override(int mode);
 
+/* Process-wide switch: enable = 1 runs a BF16 block's MLP at C = 128 as one
+ * fused kernel (FC1 with LayerNorm 2 folded, GELU, FC2 and the residual, the
+ * hidden activations in shared memory; bit-identical to the two GEMMs),
+ * enable = 0 (default) as two GEMMs, which were measured as fast or faster
+ * inside captured rollouts (the fused kernel runs one CTA per 128 rows, the
+ * first GEMM one per 128 x 128 output tile). Applies to blocks launched or
+ * captured afterwards. WM_ERR_INVALID_ARG for another value. */
+wm_status wm_set_fused_mlp(int enable);
+
 /* ------------------------------------------------------------------------
  * Encoder and decoder (Section 2.1 "Encoder-processor-decoder architecture";
  * Appendix A.1 variables, A.2 architecture). The paper gives the grid (0.25

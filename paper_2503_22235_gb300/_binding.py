@@ -84,6 +84,7 @@ _SIGS = {
     "wm_op_layernorm_e4m3": (_c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _c_float, _c_float, _vp]),
     "wm_fp8_scales": (_c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_c_float)]),
     "wm_gemm_tile_override": (_c_int, [_c_int]),
+    "wm_set_fused_mlp": (_c_int, [_c_int]),
     "wm_codec_create": (_c_int, [ctypes.POINTER(wm_codec_config), _vp, _sz, ctypes.POINTER(_vp)]),
     "wm_codec_destroy": (_c_int, [_vp]),
     "wm_encode": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -397,6 +398,11 @@ def wm_fp8_scales(ctx, which, block) -> tuple:
 
 
 GEMM_TILES_TUNED, GEMM_TILES_128, GEMM_TILES_256, GEMM_TILES_PAIR = 0, 1, 2, 3
+
+
+def wm_set_fused_mlp(enable) -> None:
+    """1 runs the C = 128 MLP as one fused kernel, 0 (default) as two GEMMs."""
+    _check(lib().wm_set_fused_mlp(int(enable)))
 
 
 def wm_gemm_tile_override(mode) -> None:

@@ -262,6 +262,8 @@ struct GemmPick {
 };
 // Test hook (wm_gemm_tile_override): 0 = tuned plans, 1 = BN 128, 2 = BN 256, 3 = BN 256 on CTA pairs.
 std::atomic<int> g_gemm_override{0};
+// wm_set_fused_mlp: 1 runs the C = 128 MLP as the fused kernel, 0 (default) as two GEMMs.
+std::atomic<int> g_mlp_fused{0};
 using GemmKey = std::array<long, 5>;   // rows (-1 for the residual epilogue), N, K, epilogue, e4m3
 std::mutex g_gemm_mu;
 std::map<GemmKey, GemmPick> g_gemm_picks;
@@ -560,6 +562,18 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
     a.bias = w.b2; a.epi = wm::EPI_RESID_LN; a.alpha = w.s_h * w.s_w2; a.x = x; a.stats = ctx->stats;
     { TimedLaunch t(ctx, WM_K_FC2, s); a.pdl = pdl; WM_TRY(wm::launch_gemm_tc(a, s)); }
     ctx->np_next = 2 * ((C + a.bn - 1) / a.bn);
+    return WM_OK;
+  }
+  if (C == 128 && g_mlp_fused.load() == 1) {
+    // the small latent's MLP as one kernel (bit-identical to the two GEMMs below)
+    wm::MlpArgs m;
+    m.tmA = ctx->tm_xb; m.tmW1 = w.tm_f1[0]; m.tmW2 = w.tm_2[0];
+    m.M = (int)M;
+    m.colsum1 = w.cs_1; m.bias1 = w.bb_1; m.bias2 = w.b2;
+    m.stats_in = ctx->stats; m.stats_out = ctx->stats; m.np_in = np2; m.eps = c.ln_eps;
+    m.x = x; m.xb = ctx->xb; m.pdl = pdl;
+    { TimedLaunch t(ctx, WM_K_FC1, s); WM_TRY(wm::launch_mlp_small(m, s)); }
+    ctx->np_next = 2;
     return WM_OK;
   }
   // LayerNorm 2 folded into FC1 (+ GELU)
@@ -1293,6 +1307,12 @@ wm_status wm_op_linear(const void* A, const void* W, const float* bias, void* ou
   a.M = M; a.N = N; a.K = K;
   a.bias = bias; a.epi = epilogue;
   return wm::launch_gemm_tc(a, s);
+}
+
+wm_status wm_set_fused_mlp(int enable) {
+  if (enable < 0 || enable > 1) return fail(WM_ERR_INVALID_ARG, "fused MLP switch must be 0 or 1");
+  g_mlp_fused.store(enable);
+  return WM_OK;
 }
 
 wm_status wm_gemm_tile_override(int mode) {

@@ -795,12 +795,419 @@ static wm_status launch_bn(const GemmArgs& a, cudaStream_t s) {
   }
 }
 
+
+// ------------------------------------------------------------ fused MLP ----
+// The small latent's MLP (C = 128, hidden 4C = 512) in one persistent kernel
+// per 128-row tile: FC1 with LayerNorm 2 folded into its epilogue and GELU,
+// in four 128-column hidden chunks whose bf16 activations go to shared
+// memory (never HBM), each chunk then the K slice of FC2 accumulating in
+// tensor memory, and FC2's residual epilogue with the next LayerNorm's row
+// statistics. Every output element is computed exactly as by the two
+// separate GEMMs with 128-column tiles (the same K order in the MMAs, the
+// same epilogue arithmetic, the same two statistics partials per row), so
+// the results are bit for bit those of the unfused path.
+//   warp 0     TMA producer: the tile's x rows (A of FC1), W1 and W2 chunks
+//              (two-slot rings each).
+//   warp 1     MMA issuer: FC1(0), FC1(1), then FC2(j) and FC1(j + 2).
+//   warps 2-9  epilogue: lane quarter q = warp % 4 (rows 32q..32q+31), half
+//              h = (warp - 2) / 4 (columns 64h..64h+63) of every chunk.
+namespace mlp {
+constexpr int C = 128, HID = 512, NCH = HID / C;
+constexpr int SLICE = 128 * BKB;          // one 128-row x 64-column bf16 k-slice (16 KB)
+constexpr int TILE = 2 * SLICE;           // 128 x 128 bf16 (32 KB)
+constexpr int OFF_A = 0, OFF_W1 = TILE, OFF_H = 3 * TILE, OFF_W2 = 5 * TILE;
+constexpr int SMEM = 7 * TILE + 1024;     // + alignment slack
+constexpr uint32_t TMEM_ACC2 = 256;       // FC1 accumulators at columns 0 and 128, FC2's at 256
+}  // namespace mlp
+
+struct MlpEpi {
+  const float* colsum1;   // column sums of the folded bf16 W1
+  const float* bias1;     // folded FC1 bias
+  const float* bias2;     // FC2 bias
+  const float* stats_in;  // [M, np_in, 2] LayerNorm-2 partials (from the output projection)
+  float* stats_out;       // [M, 2, 2] LayerNorm-1 partials of the new residual
+  float* x;               // fp32 residual [M, C], read and rewritten
+  __nv_bfloat16* xb;      // bf16 copy of the new residual [M, C]
+  int np_in;
+  float eps;
+};
+
+// bf16 rows of 32 columns into a 128-byte-swizzled K-major k-slice (the layout
+// the MMA descriptors and a 128B-swizzled tensor copy use): 16-byte unit u
+// of row r at u ^ (r & 7).
+__device__ __forceinline__ void store_h_row(uint8_t* slice, int r, int unit0, const float (&v)[32]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __nv_bfloat162 pr = __floats2bfloat162_rn(v[8 * k + 2 * e], v[8 * k + 2 * e + 1]);
+      w[e] = *reinterpret_cast<uint32_t*>(&pr);
+    }
+    *reinterpret_cast<uint4*>(slice + r * 128 + (((unit0 + k) ^ (r & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    mlp_small_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW1,
+                     const __grid_constant__ CUtensorMap tmW2, int M, const MlpEpi e, int* __restrict__ status) {
+  using namespace mlp;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t a_full, a_empty, acc2_full, acc2_empty, drain_bar;
+  __shared__ __align__(8) uint64_t w1_full[2], w1_empty[2], w2_full[2], w2_empty[2];
+  __shared__ __align__(8) uint64_t acc1_full[2], acc1_empty[2], h_full[2], h_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int num_tiles = (M + BM - 1) / BM;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&a_full, 1);
+    mbar_init(&a_empty, 1);
+    mbar_init(&acc2_full, 1);
+    mbar_init(&acc2_empty, NUM_EPI_WARPS);
+    mbar_init(&drain_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&w1_full[b], 1);
+      mbar_init(&w1_empty[b], 1);
+      mbar_init(&w2_full[b], 1);
+      mbar_init(&w2_empty[b], 1);
+      mbar_init(&acc1_full[b], 1);
+      mbar_init(&acc1_empty[b], NUM_EPI_WARPS);
+      mbar_init(&h_full[b], NUM_EPI_WARPS);
+      mbar_init(&h_empty[b], 1);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_slot;
+  pdl_wait();
+  pdl_trigger();
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------- TMA producer
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmW1) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmW2) : "memory");
+      // weight chunks in the order the MMA thread consumes them
+      constexpr int kKind[8] = {1, 1, 2, 1, 2, 1, 2, 2};   // 1: W1 chunk, 2: W2 chunk
+      constexpr int kChunk[8] = {0, 1, 0, 2, 1, 3, 2, 3};
+      bool ok = true;
+      // for the drain after a timeout: the parity of each barrier's last copies (-1: none)
+      int last_a = -1, last_w1[2] = {-1, -1}, last_w2[2] = {-1, -1};
+      int it = 0;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++it) {
+        const int m0 = tile * BM;
+        const uint32_t tp = (uint32_t)it & 1u;
+        if (!mbar_wait(&a_empty, tp ^ 1u, &abort_flag)) { ok = false; break; }
+        mbar_expect_tx(&a_full, TILE);
+        for (int s = 0; s < 2; ++s) tma_load_2d(sbase + OFF_A + s * SLICE, &tmA, &a_full, s * 64, m0);
+        last_a = (int)tp;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = kChunk[q], b = j & 1;
+          const uint32_t use = (uint32_t)(2 * it + (j >> 1)) & 1u;
+          uint64_t* full = kKind[q] == 1 ? &w1_full[b] : &w2_full[b];
+          uint64_t* empty = kKind[q] == 1 ? &w1_empty[b] : &w2_empty[b];
+          if (!mbar_wait(empty, use ^ 1u, &abort_flag)) { ok = false; break; }
+          mbar_expect_tx(full, TILE);
+          const uint32_t dst = sbase + (kKind[q] == 1 ? OFF_W1 : OFF_W2) + b * TILE;
+          for (int s = 0; s < 2; ++s) {
+            if (kKind[q] == 1) tma_load_2d(dst + s * SLICE, &tmW1, full, s * 64, j * C);
+            else tma_load_2d(dst + s * SLICE, &tmW2, full, j * C + s * 64, 0);
+          }
+          if (kKind[q] == 1) last_w1[b] = (int)use;
+          else last_w2[b] = (int)use;
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(status, (int)WM_ERR_TIMEOUT);
+        // let our own copies land before the CTA's shared memory is released
+        volatile int never = 0;
+        if (last_a >= 0) mbar_wait(&a_full, (uint32_t)last_a, &never);
+        for (int b = 0; b < 2; ++b) {
+          if (last_w1[b] >= 0) mbar_wait(&w1_full[b], (uint32_t)last_w1[b], &never);
+          if (last_w2[b] >= 0) mbar_wait(&w2_full[b], (uint32_t)last_w2[b], &never);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BM, C);
+      bool ok = true;
+      int it = 0;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++it) {
+        const uint32_t tp = (uint32_t)it & 1u;
+        if (!mbar_wait(&a_full, tp, &abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        // FC1 of hidden chunk j into accumulator j % 2 (K = C: two k-slices of 4 MMAs)
+        auto fc1 = [&](int j) -> bool {
+          const int b = j & 1;
+          const uint32_t use = (uint32_t)(2 * it + (j >> 1)) & 1u;
+          if (!mbar_wait(&w1_full[b], use, &abort_flag)) return false;
+          if (!mbar_wait(&acc1_empty[b], use ^ 1u, &abort_flag)) return false;
+          tc_fence_after();
+          const uint32_t d = tmem_base + (uint32_t)(b * C);
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const uint64_t adesc = sw128_desc(sbase + OFF_A + s * SLICE);
+            const uint64_t bdesc = sw128_desc(sbase + OFF_W1 + b * TILE + s * SLICE);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              umma_bf16<false>(d, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (s | k) != 0);
+          }
+          umma_commit(&w1_empty[b]);
+          umma_commit(&acc1_full[b]);
+          if (j == NCH - 1) umma_commit(&a_empty);
+          return true;
+        };
+        // FC2's K slice of hidden chunk j (the chunk's activations from shared memory)
+        auto fc2 = [&](int j) -> bool {
+          const int b = j & 1;
+          const uint32_t use = (uint32_t)(2 * it + (j >> 1)) & 1u;
+          if (j == 0 && !mbar_wait(&acc2_empty, tp ^ 1u, &abort_flag)) return false;
+          if (!mbar_wait(&h_full[b], use, &abort_flag)) return false;
+          if (!mbar_wait(&w2_full[b], use, &abort_flag)) return false;
+          tc_fence_after();
+          const uint32_t d = tmem_base + TMEM_ACC2;
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const uint64_t adesc = sw128_desc(sbase + OFF_H + b * TILE + s * SLICE);
+            const uint64_t bdesc = sw128_desc(sbase + OFF_W2 + b * TILE + s * SLICE);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              umma_bf16<false>(d, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), idesc, (j | s | k) != 0);
+          }
+          umma_commit(&w2_empty[b]);
+          umma_commit(&h_empty[b]);
+          if (j == NCH - 1) umma_commit(&acc2_full);
+          return true;
+        };
+        ok = fc1(0) && fc1(1);
+        for (int j = 0; j < NCH && ok; ++j) {
+          ok = fc2(j);
+          if (ok && j + 2 < NCH) ok = fc1(j + 2);
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(status, (int)WM_ERR_TIMEOUT);
+        umma_commit(&drain_bar);  // completes once every MMA issued above has finished
+        volatile int never = 0;
+        mbar_wait(&drain_bar, 0, &never);
+      }
+    }
+  } else {
+    // -------------------------------------------------------- epilogue
+    const int quarter = warp & 3;                 // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;             // columns 64 half .. 64 half + 63 of every chunk
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const int r = quarter * 32 + lane;            // this thread's row in the tile
+    int it = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++it) {
+      const uint32_t tp = (uint32_t)it & 1u;
+      const int m0 = tile * BM, row0 = m0 + quarter * 32, m = m0 + r;
+      // LayerNorm 2 of the row from the projection's partial (mean, M2) pairs
+      // (equal counts C / np each): its mean and 1 / sqrt(var + eps)
+      float ln_mean = 0.f, ln_rstd = 0.f;
+      if (m < M) {
+        const float* st = e.stats_in + (size_t)m * e.np_in * 2;
+        float mu = 0.f;
+        for (int i = 0; i < e.np_in; ++i) mu += st[2 * i];
+        mu /= (float)e.np_in;
+        const float cnt = (float)C / (float)e.np_in;
+        float m2 = 0.f;
+        for (int i = 0; i < e.np_in; ++i) {
+          const float d = st[2 * i] - mu;
+          m2 += st[2 * i + 1] + cnt * d * d;
+        }
+        ln_mean = mu;
+        ln_rstd = rsqrtf(m2 / (float)C + e.eps);
+      }
+      bool ok = true;
+      // ---- FC1 chunks: rstd (acc - mean colsum) + b', GELU, bf16 into the H slot
+      for (int j = 0; j < NCH && ok; ++j) {
+        const int b = j & 1;
+        const uint32_t use = (uint32_t)(2 * it + (j >> 1)) & 1u;
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc1_full[b], use, &abort_flag))) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll 1
+        for (int sub = 0; sub < 2; ++sub) {
+          const int c = half * 64 + sub * 32;      // column in the chunk
+          float v[32];
+          tmem_ld32(tmem_base + (uint32_t)(b * C + c) + lane_off, v);
+          if (sub == 1) {
+            // last TMEM read of this chunk: the accumulator may be refilled
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc1_empty[b]);
+          }
+          const int n = j * C + c;                 // hidden column
+          float lcs[32], lbb[32];
+          {
+            const float4* c4 = reinterpret_cast<const float4*>(e.colsum1 + n);
+            const float4* b4 = reinterpret_cast<const float4*>(e.bias1 + n);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 a = __ldg(c4 + q), bb = __ldg(b4 + q);
+              lcs[4 * q] = a.x; lcs[4 * q + 1] = a.y; lcs[4 * q + 2] = a.z; lcs[4 * q + 3] = a.w;
+              lbb[4 * q] = bb.x; lbb[4 * q + 1] = bb.y; lbb[4 * q + 2] = bb.z; lbb[4 * q + 3] = bb.w;
+            }
+          }
+          const uint64_t nmean2 = pack_f2(-ln_mean, -ln_mean), rstd2 = pack_f2(ln_rstd, ln_rstd);
+#pragma unroll
+          for (int jj = 0; jj < 32; jj += 2) {
+            float t0, t1;
+            fma_f2(t0, t1, lcs[jj], lcs[jj + 1], nmean2, pack_f2(v[jj], v[jj + 1]));
+            fma_f2(v[jj], v[jj + 1], t0, t1, rstd2, pack_f2(lbb[jj], lbb[jj + 1]));
+            gelu_erf2(v[jj], v[jj + 1]);
+          }
+          if (sub == 0) {
+            // the slot's previous chunk (j - 2) has been read by FC2
+            if (!__all_sync(0xffffffffu, mbar_wait(&h_empty[b], use ^ 1u, &abort_flag))) { ok = false; break; }
+          }
+          store_h_row(smem + OFF_H + b * TILE + half * SLICE, r, sub * 4, v);
+        }
+        if (!ok) break;
+        fence_async_smem();   // generic-proxy stores, read by the tensor core next
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&h_full[b]);
+      }
+      if (ok && !__all_sync(0xffffffffu, mbar_wait(&acc2_full, tp, &abort_flag))) ok = false;
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(status, (int)WM_ERR_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      // ---- FC2: x_new = x_old + acc + b2, its bf16 copy, and Welford (count,
+      // mean, M2) over this half's 64 columns: the next LayerNorm's partial
+      float wn = 0.f, wmean = 0.f, wm2 = 0.f;
+      float4 xa[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xa[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < M) {
+        const float4* xo = reinterpret_cast<const float4*>(e.x + (size_t)m * C + half * 64);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xa[q] = xo[q];
+      }
+#pragma unroll 1
+      for (int sub = 0; sub < 2; ++sub) {
+        const int c = half * 64 + sub * 32;
+        float v[32];
+        tmem_ld32(tmem_base + TMEM_ACC2 + (uint32_t)c + lane_off, v);
+        if (sub == 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc2_empty);
+        }
+        if (row0 >= M) continue;   // the whole 32-row group is past the end (warp-uniform)
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) v[jj] += __ldg(e.bias2 + c + jj);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          v[4 * q] += xa[q].x; v[4 * q + 1] += xa[q].y; v[4 * q + 2] += xa[q].z; v[4 * q + 3] += xa[q].w;
+        }
+        if (sub == 0 && m < M) {
+          const float4* xo = reinterpret_cast<const float4*>(e.x + (size_t)m * C + c + 32);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xa[q] = xo[q];
+        }
+        float cs = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) cs += v[jj];
+        const float cm = cs * (1.f / 32.f);
+        float cq = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) cq += (v[jj] - cm) * (v[jj] - cm);
+        const float nt = wn + 32.f, d = cm - wmean;
+        wmean += d * (32.f / nt);
+        wm2 += cq + d * d * (wn * 32.f / nt);
+        wn = nt;
+        if (m < M) {
+          float4* xd = reinterpret_cast<float4*>(e.x + (size_t)m * C + c);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xd[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          uint4* bd = reinterpret_cast<uint4*>(e.xb + (size_t)m * C + c);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              __nv_bfloat162 pr = __floats2bfloat162_rn(v[8 * k + 2 * q], v[8 * k + 2 * q + 1]);
+              w[q] = *reinterpret_cast<uint32_t*>(&pr);
+            }
+            bd[k] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+      }
+      if (row0 < M && m < M && wn > 0.f) {
+        float* st = e.stats_out + ((size_t)m * 2 + half) * 2;
+        st[0] = wmean;
+        st[1] = wm2;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+  }
+}
+
+static wm_status launch_mlp(const MlpArgs& a, cudaStream_t s) {
+  MlpEpi e;
+  e.colsum1 = a.colsum1;
+  e.bias1 = a.bias1;
+  e.bias2 = a.bias2;
+  e.stats_in = a.stats_in;
+  e.stats_out = a.stats_out;
+  e.x = a.x;
+  e.xb = a.xb;
+  e.np_in = a.np_in;
+  e.eps = a.eps;
+  const int tiles = (a.M + BM - 1) / BM;
+  const int grid = tiles < num_sms() ? tiles : num_sms();
+  WM_CUDA(launch_pdl(mlp_small_kernel, dim3(grid), dim3(THREADS), mlp::SMEM, s, a.pdl, a.tmA, a.tmW1, a.tmW2, a.M, e,
+                     device_status_word()));
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
 }  // namespace tc
 
 wm_status prepare_gemm_tc() {
   wm_status st = tc::set_attrs_bn<128>();
   if (st == WM_OK) st = tc::set_attrs_bn<256>();
+  if (st == WM_OK && cudaFuncSetAttribute(tc::mlp_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tc::mlp::SMEM) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "fused MLP shared-memory limit");
   return st;
+}
+
+wm_status launch_mlp_small(const MlpArgs& a, cudaStream_t s) {
+  if (a.M <= 0) return WM_OK;
+  if (!a.colsum1 || !a.bias1 || !a.bias2 || !a.stats_in || !a.stats_out || !a.x || !a.xb || a.np_in < 1)
+    return fail(WM_ERR_INVALID_ARG, "fused MLP needs the LayerNorm statistics, biases, residual and its bf16 copy");
+  if ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.xb)) & 15)
+    return fail(WM_ERR_INVALID_ARG, "fused MLP needs 16-byte aligned residual buffers");
+  return tc::launch_mlp(a, s);
 }
 
 wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s) {

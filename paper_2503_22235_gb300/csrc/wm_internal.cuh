@@ -258,6 +258,29 @@ struct GemmArgs {
 wm_status launch_rope_f32(float* qkv, long M, const RopeArgs* rope_dev, const RopeArgs& rope_host, cudaStream_t s);
 wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
 
+// The small latent's MLP (C = 128, hidden 512) fused into one kernel: FC1 with
+// LayerNorm 2 folded (stats_in: the output projection's np_in partials per
+// row, colsum1 / bias1: the folded W1's column sums and bias), GELU, FC2,
+// x += (.) + bias2, the bf16 copy xb and LayerNorm-1 partials (2 per row) of
+// the new x. Bit-identical to FC1 and FC2 as two GEMMs with 128-column tiles.
+struct MlpArgs {
+  CUtensorMap tmA;    // bf16 x [M, C] (make_tmap_bf16, box 128 rows)
+  CUtensorMap tmW1;   // folded bf16 W1 [4C, C] (box 128 rows)
+  CUtensorMap tmW2;   // bf16 W2 [C, 4C] (box 128 rows)
+  int M = 0;
+  const float* colsum1 = nullptr;
+  const float* bias1 = nullptr;
+  const float* bias2 = nullptr;
+  const float* stats_in = nullptr;
+  float* stats_out = nullptr;
+  float* x = nullptr;
+  __nv_bfloat16* xb = nullptr;
+  int np_in = 0;
+  float eps = 0.f;
+  bool pdl = false;
+};
+wm_status launch_mlp_small(const MlpArgs& a, cudaStream_t s);
+
 // variant: WM_NA_* of wm.h (0 = tuned plan / the shape's fixed family).
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
                          int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s, int variant = 0,
