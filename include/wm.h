@@ -346,12 +346,13 @@ wm_status wm_fp8_scales(wm_ctx* ctx, int which, int block, float* out);
 /* Test hook for the tcgen05 GEMM tiles (process-wide, not thread-safe with
  * respect to launches in flight): mode 0 = the autotuner's plans (default),
  * 1 = 128-column tiles, 2 = 256-column tiles, 3 = 256 x 256 tiles on CTA pairs
- * (cta_group::2; shapes with N % 256 != 0 keep single-CTA tiles). Applies to
- * every BF16 / FP8-MLP block GEMM launched or captured afterwards and to
- * wm_op_linear (BF16; pairs for epilogue 0 only). Results are the same
- * function of the inputs in every mode up to accumulation rounding; modes
- * 1 and 2 also change how the LayerNorm statistics partials are split.
- * WM_ERR_INVALID_ARG for a mode outside 0..3. */
+ * (cta_group::2; shapes with N % 256 != 0 keep single-CTA tiles), 4 = 64-column
+ * tiles (N % 64 == 0). Applies to every BF16 / FP8-MLP block GEMM launched or
+ * captured afterwards and to wm_op_linear (BF16; pairs for epilogue 0 only).
+ * Results are the same function of the inputs in every mode up to
+ * accumulation rounding; the tile width also sets how the LayerNorm
+ * statistics partials are split (two per tile). WM_ERR_INVALID_ARG for a
+ * mode outside 0..4. */
 wm_status wm_gemm_tile_override(int mode);
 
 /* Process-wide switch: enable = 1 runs a BF16 block's MLP at C = 128 as one

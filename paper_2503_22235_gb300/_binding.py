@@ -397,7 +397,7 @@ def wm_fp8_scales(ctx, which, block) -> tuple:
     return tuple(out)
 
 
-GEMM_TILES_TUNED, GEMM_TILES_128, GEMM_TILES_256, GEMM_TILES_PAIR = 0, 1, 2, 3
+GEMM_TILES_TUNED, GEMM_TILES_128, GEMM_TILES_256, GEMM_TILES_PAIR, GEMM_TILES_64 = 0, 1, 2, 3, 4
 
 
 def wm_set_fused_mlp(enable) -> None:

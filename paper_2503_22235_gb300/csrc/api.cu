@@ -32,15 +32,15 @@ namespace {
 struct BlockW {
   const float *ln1_g, *ln1_b, *wqkv, *bqkv, *wo, *bo, *ln2_g, *ln2_b, *w1, *b1, *w2, *b2;
   bf16 *ho, *h2;       // bf16 Wo and W2 (Wqkv and W1 are used LayerNorm-folded, below)
-  CUtensorMap tm_o[2], tm_2[2];  // [0]: box 128 rows, [1]: box 256 rows
+  CUtensorMap tm_o[3], tm_2[3];  // [0]: box 128 rows, [1]: box 256 rows, [2]: box 64 rows
   // LayerNorm folded into QKV and FC1: bf16 W diag(gamma), its column sums,
   // and the folded bias b + W beta
   bf16 *fqkv, *f1;
   const float *cs_qkv, *bb_qkv, *cs_1, *bb_1;
-  CUtensorMap tm_fqkv[2], tm_f1[2];
+  CUtensorMap tm_fqkv[3], tm_f1[3];
   // FP8 MLP: e4m3 copies of W1, W2 and the static per-tensor scales
   uint8_t *q1, *q2;
-  CUtensorMap tm_q1[2], tm_q2[2];
+  CUtensorMap tm_q1[3], tm_q2[3];
   float s_u, s_w1, s_h, s_w2;   // LN2 output, W1, GELU output, W2
 };
 
@@ -184,7 +184,7 @@ wm_status ensure_workspace(wm_ctx* ctx, int batch, bool fp32) {
     ctx->q_u = ctx->q_h = nullptr;
     ctx->xb = nullptr;
     ctx->stats = nullptr;
-    const size_t np_max = 2 * ((C + 127) / 128);
+    const size_t np_max = 2 * ((C + 63) / 64);   // LayerNorm partials: two per 64-column tile at most
     if (cudaMalloc(&ctx->xb, M * C * 2) != cudaSuccess || cudaMalloc(&ctx->stats, M * np_max * 2 * 4) != cudaSuccess) {
       cudaGetLastError();
       return fail(WM_ERR_OOM, "LayerNorm statistics workspace allocation failed");
@@ -245,7 +245,7 @@ int pick_bn(long M, int N) {
 }
 
 // ---- GEMM tile autotuner
-// Tile width BN (128 or 256 output columns; 256 also as 256 x 256 tiles on
+// Tile width BN (64, 128 or 256 output columns; 256 also as 256 x 256 tiles on
 // CTA pairs) and, for the residual epilogue, one or two staging tiles,
 // chosen per GEMM of the block by timing every candidate when a context's
 // BF16 workspace is allocated. BN changes no
@@ -260,7 +260,8 @@ struct GemmPick {
   bool pair = false;
   double ms = 0.0;
 };
-// Test hook (wm_gemm_tile_override): 0 = tuned plans, 1 = BN 128, 2 = BN 256, 3 = BN 256 on CTA pairs.
+// Test hook (wm_gemm_tile_override): 0 = tuned plans, 1 = BN 128, 2 = BN 256, 3 = BN 256 on CTA pairs,
+// 4 = BN 64.
 std::atomic<int> g_gemm_override{0};
 // wm_set_fused_mlp: 1 runs the C = 128 MLP as the fused kernel, 0 (default) as two GEMMs.
 std::atomic<int> g_mlp_fused{0};
@@ -277,7 +278,7 @@ GemmPick pick_gemm(long M, int N, int K, int epi, bool f8) {
   const int ov = g_gemm_override.load();
   if (ov != 0) {
     GemmPick g;
-    g.bn = (ov == 1 || N % 256 != 0) ? 128 : 256;
+    g.bn = ov == 4 ? (N % 64 == 0 ? 64 : 128) : (ov == 1 || N % 256 != 0) ? 128 : 256;
     // the pair kernel carries the block's epilogues (not the FP8-MLP path's plain residual add)
     g.pair = ov == 3 && g.bn == 256 && epi != wm::EPI_RESID_F32;
     return g;
@@ -294,7 +295,7 @@ GemmPick pick_gemm(long M, int N, int K, int epi, bool f8) {
 
 // Times the candidates of one GEMM (a: every field but bn / dual / tmB set;
 // tmB[0], tmB[1]: the W map for BN = 128 and 256) and records the fastest.
-wm_status tune_gemm(wm::GemmArgs a, const CUtensorMap (&tmB)[2], const char* name, cudaStream_t s) {
+wm_status tune_gemm(wm::GemmArgs a, const CUtensorMap (&tmB)[3], const char* name, cudaStream_t s) {
   const GemmKey key = gemm_key(a.M, a.N, a.K, a.epi, a.f8);
   {
     std::lock_guard<std::mutex> lk(g_gemm_mu);
@@ -306,7 +307,7 @@ wm_status tune_gemm(wm::GemmArgs a, const CUtensorMap (&tmB)[2], const char* nam
   GemmPick best;
   best.ms = 1e30;
   wm_status st = WM_OK;
-  for (int cand : {128, 256, 512}) {   // 512: BN = 256 on CTA pairs
+  for (int cand : {64, 128, 256, 512}) {   // 512: BN = 256 on CTA pairs
     const int bn = cand == 512 ? 256 : cand;
     const bool pair = cand == 512;
     if (a.epi == wm::EPI_RESID_LN && a.N % bn != 0) continue;
@@ -316,7 +317,7 @@ wm_status tune_gemm(wm::GemmArgs a, const CUtensorMap (&tmB)[2], const char* nam
       a.bn = bn;
       a.pair = pair;
       a.dual = a.epi == wm::EPI_RESID_LN ? dual : -1;
-      a.tmB = tmB[bn == 256 && !pair];
+      a.tmB = tmB[bn == 64 ? 2 : (bn == 256 && !pair ? 1 : 0)];
       st = wm::launch_gemm_tc(a, s);
       if (st != WM_OK) break;
       cudaEventRecord(e0, s);
@@ -388,7 +389,7 @@ wm_status tune_block_gemms(wm_ctx* ctx, int batch) {
   }
   wm_status st = WM_OK;
   auto chk = [&](wm_status x) { if (st == WM_OK) st = x; };
-  const size_t np_max = 2 * ((C + 127) / 128);
+  const size_t np_max = 2 * ((C + 63) / 64);
   if (cudaMemset(xt, 0, (size_t)M * C * 4) != cudaSuccess ||
       cudaMemset(ctx->stats, 0, (size_t)M * np_max * 2 * 4) != cudaSuccess)
     st = fail(WM_ERR_CUDA, "GEMM autotune scratch clear failed");
@@ -448,9 +449,10 @@ void set_tile(wm::GemmArgs& a, long M, int epi, bool f8) {
   a.dual = g.dual;
 }
 
-// Which of a weight's two W maps the tile reads: boxes of 256 rows for
-// single-CTA BN = 256 tiles, of 128 rows for BN = 128 and for each CTA of a pair.
-int wmap(const wm::GemmArgs& a) { return a.bn == 256 && !a.pair ? 1 : 0; }
+// Which of a weight's W maps the tile reads: boxes of 256 rows for single-CTA
+// BN = 256 tiles, of 128 rows for BN = 128 and for each CTA of a pair, of 64
+// rows for BN = 64.
+int wmap(const wm::GemmArgs& a) { return a.bn == 64 ? 2 : (a.bn == 256 && !a.pair ? 1 : 0); }
 
 // ---- optional per-launch timing: an event pair around each hot-path kernel
 const char* const kKernelNames[WM_KERNEL_KINDS] = {"ln1", "qkv", "attention", "proj", "ln2", "fc1", "fc2"};
@@ -570,10 +572,12 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
     m.tmA = ctx->tm_xb; m.tmW1 = w.tm_f1[0]; m.tmW2 = w.tm_2[0];
     m.M = (int)M;
     m.colsum1 = w.cs_1; m.bias1 = w.bb_1; m.bias2 = w.b2;
-    m.stats_in = ctx->stats; m.stats_out = ctx->stats; m.np_in = np2; m.eps = c.ln_eps;
+    // the same LayerNorm partials as FC2 on the tiles the tuner keeps for it
+    const int bn2 = pick_gemm(M, C, 4 * C, wm::EPI_RESID_LN, false).bn;
+    m.stats_in = ctx->stats; m.stats_out = ctx->stats; m.np_in = np2; m.np_out = 2 * C / bn2; m.eps = c.ln_eps;
     m.x = x; m.xb = ctx->xb; m.pdl = pdl;
     { TimedLaunch t(ctx, WM_K_FC1, s); WM_TRY(wm::launch_mlp_small(m, s)); }
-    ctx->np_next = 2;
+    ctx->np_next = m.np_out;
     return WM_OK;
   }
   // LayerNorm 2 folded into FC1 (+ GELU)
@@ -822,8 +826,8 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
       WM_CUDA(cudaMemcpy(v, hv.data(), 14 * C * 4, cudaMemcpyHostToDevice));
       if (C % 8 == 0) {
         bool ok = true;
-        for (int k = 0; k < 2; ++k) {
-          const uint32_t box = k ? 256 : 128;
+        for (int k = 0; k < 3; ++k) {
+          const uint32_t box = k == 0 ? 128 : (k == 1 ? 256 : 64);
           ok = ok && wm::make_tmap_bf16(&w.tm_fqkv[k], w.fqkv, 3 * C, C, box);
           ok = ok && wm::make_tmap_bf16(&w.tm_f1[k], w.f1, 4 * C, C, box);
         }
@@ -836,8 +840,8 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
     WM_TRY(wm::launch_f32_to_e4m3(w.w2, w.q2, 4 * C * C, 1.f / w.s_w2, 0));
     if (C % 16 == 0) {
       bool ok = true;
-      for (int k = 0; k < 2; ++k) {
-        const uint32_t box = k ? 256 : 128;
+      for (int k = 0; k < 3; ++k) {
+        const uint32_t box = k == 0 ? 128 : (k == 1 ? 256 : 64);
         ok = ok && wm::make_tmap_e4m3(&w.tm_q1[k], w.q1, 4 * C, C, box);
         ok = ok && wm::make_tmap_e4m3(&w.tm_q2[k], w.q2, C, 4 * C, box);
       }
@@ -845,8 +849,8 @@ wm_status upload_weights(wm_ctx* ctx, const float* host, size_t n) {
     }
     if (C % 8 == 0) {
       bool ok = true;
-      for (int k = 0; k < 2; ++k) {
-        const uint32_t box = k ? 256 : 128;
+      for (int k = 0; k < 3; ++k) {
+        const uint32_t box = k == 0 ? 128 : (k == 1 ? 256 : 64);
         ok = ok && wm::make_tmap_bf16(&w.tm_o[k], w.ho, C, C, box);
         ok = ok && wm::make_tmap_bf16(&w.tm_2[k], w.h2, C, 4 * C, box);
       }
@@ -1297,7 +1301,7 @@ wm_status wm_op_linear(const void* A, const void* W, const float* bias, void* ou
   if (K % 8 != 0 || N % 8 != 0) return fail(WM_ERR_INVALID_ARG, "BF16 linear needs K % 8 == 0 and N % 8 == 0");
   wm::GemmArgs a;
   const int ov = g_gemm_override.load();
-  a.bn = ov == 1 ? 128 : (ov >= 2 && N % 256 == 0) ? 256 : pick_bn(M, N);
+  a.bn = ov == 1 ? 128 : ov == 4 ? 64 : (ov >= 2 && N % 256 == 0) ? 256 : pick_bn(M, N);
   a.pair = ov == 3 && a.bn == 256 && epilogue == wm::EPI_STORE;
   const bool out_f32 = epilogue == wm::EPI_RESID_F32 || epilogue == wm::EPI_STORE_F32;
   if (!wm::make_tmap_bf16(&a.tmA, A, (uint64_t)M, (uint64_t)K, 128) ||
@@ -1316,7 +1320,7 @@ wm_status wm_set_fused_mlp(int enable) {
 }
 
 wm_status wm_gemm_tile_override(int mode) {
-  if (mode < 0 || mode > 3) return fail(WM_ERR_INVALID_ARG, "GEMM tile override must be 0..3");
+  if (mode < 0 || mode > 4) return fail(WM_ERR_INVALID_ARG, "GEMM tile override must be 0..4");
   g_gemm_override.store(mode);
   return WM_OK;
 }

@@ -825,10 +825,11 @@ struct MlpEpi {
   const float* bias1;     // folded FC1 bias
   const float* bias2;     // FC2 bias
   const float* stats_in;  // [M, np_in, 2] LayerNorm-2 partials (from the output projection)
-  float* stats_out;       // [M, 2, 2] LayerNorm-1 partials of the new residual
+  float* stats_out;       // [M, np_out, 2] LayerNorm-1 partials of the new residual
   float* x;               // fp32 residual [M, C], read and rewritten
   __nv_bfloat16* xb;      // bf16 copy of the new residual [M, C]
   int np_in;
+  int np_out;             // 2: one partial per 64 columns; 4: one per 32 (as FC2 on 128- or 64-column tiles)
   float eps;
 };
 
@@ -1139,6 +1140,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         wmean += d * (32.f / nt);
         wm2 += cq + d * d * (wn * 32.f / nt);
         wn = nt;
+        if (e.np_out == 4 && m < M) {
+          // one partial per 32 columns: this chunk's own (mean, M2), as a
+          // residual epilogue on 64-column tiles writes it
+          float* st = e.stats_out + ((size_t)m * 4 + half * 2 + sub) * 2;
+          st[0] = wmean;
+          st[1] = wm2;
+          wn = 0.f;
+          wmean = 0.f;
+          wm2 = 0.f;
+        }
         if (m < M) {
           float4* xd = reinterpret_cast<float4*>(e.x + (size_t)m * C + c);
 #pragma unroll
@@ -1156,7 +1167,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
-      if (row0 < M && m < M && wn > 0.f) {
+      if (e.np_out == 2 && row0 < M && m < M && wn > 0.f) {
         float* st = e.stats_out + ((size_t)m * 2 + half) * 2;
         st[0] = wmean;
         st[1] = wm2;
@@ -1182,6 +1193,7 @@ static wm_status launch_mlp(const MlpArgs& a, cudaStream_t s) {
   e.x = a.x;
   e.xb = a.xb;
   e.np_in = a.np_in;
+  e.np_out = a.np_out;
   e.eps = a.eps;
   const int tiles = (a.M + BM - 1) / BM;
   const int grid = tiles < num_sms() ? tiles : num_sms();
@@ -1195,6 +1207,7 @@ static wm_status launch_mlp(const MlpArgs& a, cudaStream_t s) {
 wm_status prepare_gemm_tc() {
   wm_status st = tc::set_attrs_bn<128>();
   if (st == WM_OK) st = tc::set_attrs_bn<256>();
+  if (st == WM_OK) st = tc::set_attrs_bn<64>();
   if (st == WM_OK && cudaFuncSetAttribute(tc::mlp_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           tc::mlp::SMEM) != cudaSuccess)
     st = cuda_fail(cudaGetLastError(), "fused MLP shared-memory limit");
@@ -1203,7 +1216,8 @@ wm_status prepare_gemm_tc() {
 
 wm_status launch_mlp_small(const MlpArgs& a, cudaStream_t s) {
   if (a.M <= 0) return WM_OK;
-  if (!a.colsum1 || !a.bias1 || !a.bias2 || !a.stats_in || !a.stats_out || !a.x || !a.xb || a.np_in < 1)
+  if (!a.colsum1 || !a.bias1 || !a.bias2 || !a.stats_in || !a.stats_out || !a.x || !a.xb || a.np_in < 1 ||
+      (a.np_out != 2 && a.np_out != 4))
     return fail(WM_ERR_INVALID_ARG, "fused MLP needs the LayerNorm statistics, biases, residual and its bf16 copy");
   if ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.xb)) & 15)
     return fail(WM_ERR_INVALID_ARG, "fused MLP needs 16-byte aligned residual buffers");
@@ -1224,7 +1238,8 @@ wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s) {
   }
   if (a.bn == 256) return tc::launch_bn<256>(a, s);
   if (a.bn == 128) return tc::launch_bn<128>(a, s);
-  return fail(WM_ERR_INVALID_ARG, "GEMM tile width must be 128 or 256");
+  if (a.bn == 64) return tc::launch_bn<64>(a, s);
+  return fail(WM_ERR_INVALID_ARG, "GEMM tile width must be 64, 128 or 256");
 }
 
 // ------------------------------------------------------------ TMA maps ----

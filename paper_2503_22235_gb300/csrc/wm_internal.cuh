@@ -245,7 +245,7 @@ struct GemmArgs {
   int np = 0;
   float eps = 0.f;
   int epi;
-  int bn;              // 128 or 256 (tmB box rows must match)
+  int bn;              // 64, 128 or 256 (tmB box rows must match)
   bool f8 = false;     // A and W are e4m3 (kind::f8f6f4); otherwise bf16 (kind::f16)
   float alpha = 1.f;   // e4m3 only: accumulator scale (product of the operand scales)
   float out_scale = 1.f;  // EPI_GELU_F8: 1 / output scale
@@ -261,8 +261,9 @@ wm_status launch_gemm_tc(const GemmArgs& a, cudaStream_t s);
 // The small latent's MLP (C = 128, hidden 512) fused into one kernel: FC1 with
 // LayerNorm 2 folded (stats_in: the output projection's np_in partials per
 // row, colsum1 / bias1: the folded W1's column sums and bias), GELU, FC2,
-// x += (.) + bias2, the bf16 copy xb and LayerNorm-1 partials (2 per row) of
-// the new x. Bit-identical to FC1 and FC2 as two GEMMs with 128-column tiles.
+// x += (.) + bias2, the bf16 copy xb and LayerNorm-1 partials of the new x
+// (np_out per row: 2 or 4, as FC2 on 128- or 64-column tiles writes them).
+// Bit-identical to FC1 and FC2 as two GEMMs.
 struct MlpArgs {
   CUtensorMap tmA;    // bf16 x [M, C] (make_tmap_bf16, box 128 rows)
   CUtensorMap tmW1;   // folded bf16 W1 [4C, C] (box 128 rows)
@@ -276,6 +277,7 @@ struct MlpArgs {
   float* x = nullptr;
   __nv_bfloat16* xb = nullptr;
   int np_in = 0;
+  int np_out = 2;
   float eps = 0.f;
   bool pdl = false;
 };

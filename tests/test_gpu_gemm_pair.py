@@ -119,3 +119,55 @@ def test_pair_tiles_full_size_block_at_sampled_tokens():
     finally:
         wm.wm_gemm_tile_override(wm.GEMM_TILES_TUNED)
     assert_close(got, ref, 2e-2, s.C)
+
+
+@pytest.mark.parametrize("M,N,K", [(1000, 256, 128), (300, 512, 136), (1, 128, 64), (4685, 768, 768)])
+def test_64_column_tiles_equal_wide_tiles_and_reference(M, N, K):
+    """64-column tiles (more CTAs for narrow GEMMs) sum every element in the
+    same K order as the wider tiles."""
+    rng = np.random.default_rng(M + 5 * N + 11 * K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    W = (rng.standard_normal((N, K)) / np.sqrt(K)).astype(np.float32)
+    bias = (0.1 * rng.standard_normal(N)).astype(np.float32)
+    Ah = torch.from_numpy(A).to(CUDA, torch.bfloat16)
+    Wh = torch.from_numpy(W).to(CUDA, torch.bfloat16)
+    bd = torch.from_numpy(bias).to(CUDA)
+    outs = {}
+    try:
+        for mode in (wm.GEMM_TILES_128, wm.GEMM_TILES_64):
+            wm.wm_gemm_tile_override(mode)
+            o = torch.full((M, N), float("nan"), device=CUDA, dtype=torch.bfloat16)
+            wm.wm_op_linear(Ah, Wh, bd, o, wm.WM_PREC_BF16, wm.EPI_STORE)
+            outs[mode] = host(o)
+    finally:
+        wm.wm_gemm_tile_override(wm.GEMM_TILES_TUNED)
+    assert np.array_equal(outs[wm.GEMM_TILES_64], outs[wm.GEMM_TILES_128])
+    assert_close(outs[wm.GEMM_TILES_64], orc.linear(bf16_round(A), bf16_round(W), bias), 4e-3, N)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8mlp"])
+def test_64_column_tiles_processor_step_small_latent(precision):
+    """Every block GEMM of the small latent on 64-column tiles (four LayerNorm
+    partials per row from the residual epilogues) against the oracle."""
+    s = synth.SMALL
+    prec = wm.WM_PREC_BF16 if precision == "bf16" else wm.WM_PREC_BF16_FP8MLP
+    p6, p1 = synth.processor_weights(s, seed=0, stress=True)
+    x = synth.latent(s, 2, seed=1)
+    try:
+        wm.wm_gemm_tile_override(wm.GEMM_TILES_64)
+        ctx = wm.wm_create_from_host(wm.make_config(s, prec, 2), synth.pack_weights(p6, p1))
+        try:
+            xt = torch.from_numpy(x).to(CUDA)
+            wm.wm_processor_step(ctx, xt, wm.WM_P1)
+            got = host(xt)
+        finally:
+            wm.wm_destroy(ctx)
+    finally:
+        wm.wm_gemm_tile_override(wm.GEMM_TILES_TUNED)
+    if precision == "bf16":
+        ref = orc.processor(x, p1, s)
+    else:
+        ref = x
+        for blk in p1:
+            ref = orc.block_fp8mlp(ref, blk, s)
+    assert_close(got, ref, 2e-2 * len(p1), s.C)
