@@ -364,6 +364,22 @@ wm_status wm_gemm_tile_override(int mode);
  * captured afterwards. WM_ERR_INVALID_ARG for another value. */
 wm_status wm_set_fused_mlp(int enable);
 
+/* Whole-rollout launches for narrow latents (Section 2.1 latent rollout,
+ * Appendix A.2 blocks): 1 (the default) lets wm_latent_rollout and
+ * wm_rollout_batch run BF16 contexts with C = 128, 4 heads, periodic
+ * longitude, no rotary embedding, H % 8 == 0, W % 16 == 0, W >= 32 and
+ * latitude / longitude windows of at most 5 as ONE kernel launch per group of
+ * latents (as many as the device holds at once: 4 for the 4 x 24 x 48 latent).
+ * Each CTA keeps an 8 x 16-token patch of its latent's residual stream in
+ * shared memory for the whole rollout and runs every block's attention,
+ * projection, MLP, LayerNorms and residual adds; the latent's CTAs meet once
+ * per block at a counter in global memory. The result equals the per-kernel
+ * path within the BF16 tolerance (LayerNorm is applied explicitly, not folded
+ * into the GEMMs, so the two are not bit-identical). Latents of
+ * wm_rollout_batch are read and written in place. 0: every rollout uses one
+ * launch per GEMM / attention. WM_ERR_INVALID_ARG for another value. */
+wm_status wm_set_fused_rollout(int enable);
+
 /* ------------------------------------------------------------------------
  * Encoder and decoder (Section 2.1 "Encoder-processor-decoder architecture";
  * Appendix A.1 variables, A.2 architecture). The paper gives the grid (0.25

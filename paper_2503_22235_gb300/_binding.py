@@ -85,6 +85,7 @@ _SIGS = {
     "wm_fp8_scales": (_c_int, [_vp, _c_int, _c_int, ctypes.POINTER(_c_float)]),
     "wm_gemm_tile_override": (_c_int, [_c_int]),
     "wm_set_fused_mlp": (_c_int, [_c_int]),
+    "wm_set_fused_rollout": (_c_int, [_c_int]),
     "wm_codec_create": (_c_int, [ctypes.POINTER(wm_codec_config), _vp, _sz, ctypes.POINTER(_vp)]),
     "wm_codec_destroy": (_c_int, [_vp]),
     "wm_encode": (_c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -398,6 +399,11 @@ def wm_fp8_scales(ctx, which, block) -> tuple:
 
 
 GEMM_TILES_TUNED, GEMM_TILES_128, GEMM_TILES_256, GEMM_TILES_PAIR, GEMM_TILES_64 = 0, 1, 2, 3, 4
+
+
+def wm_set_fused_rollout(enable) -> None:
+    """1 (default): narrow-latent rollouts as one whole-rollout launch; 0: one launch per kernel."""
+    _check(lib().wm_set_fused_rollout(int(enable)))
 
 
 def wm_set_fused_mlp(enable) -> None:

@@ -87,6 +87,12 @@ struct wm_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_marks;  // (kernel kind, index of the start event)
   cudaStream_t cap_stream = nullptr;
+  // whole-rollout kernel for narrow latents (k_rollout_small.cu)
+  bf16* d_rs_w = nullptr;                 // swizzled bf16 weight chunks, 12 per block
+  wm::RolloutBlock* d_rs_blk = nullptr;   // per-block table: six-hour blocks, then one-hour blocks
+  float* d_rs_qkv = nullptr;              // its double-buffered bf16 q, k, v (capacity in floats)
+  size_t rs_qkv_cap = 0;
+  unsigned int* d_rs_bar = nullptr;       // one barrier counter per latent
   std::recursive_mutex mu;
 };
 
@@ -265,6 +271,9 @@ struct GemmPick {
 std::atomic<int> g_gemm_override{0};
 // wm_set_fused_mlp: 1 runs the C = 128 MLP as the fused kernel, 0 (default) as two GEMMs.
 std::atomic<int> g_mlp_fused{0};
+// 1: rollouts of eligible narrow latents run as one whole-rollout launch
+// (k_rollout_small.cu); 0: one launch per GEMM / attention as for any shape.
+std::atomic<int> g_fused_rollout{1};
 using GemmKey = std::array<long, 5>;   // rows (-1 for the residual epilogue), N, K, epilogue, e4m3
 std::mutex g_gemm_mu;
 std::map<GemmKey, GemmPick> g_gemm_picks;
@@ -599,8 +608,24 @@ wm_status block_forward(wm_ctx* ctx, float* x, int batch, int which, int b, bool
   return WM_OK;
 }
 
+int rollout_small_group(const wm_ctx* ctx, int batch);
+wm_status rollout_small(wm_ctx* ctx, float* const* x, const int* n6, const int* n1, int G, cudaStream_t s);
+
 wm_status processor_step(wm_ctx* ctx, float* x, int batch, int which, cudaStream_t s) {
   wm::NvtxRange range(which == WM_P6 ? "six-hour step" : "one-hour step");
+  const int G = rollout_small_group(ctx, batch);
+  if (G > 0) {
+    // narrow latent: the step's blocks as one whole-rollout launch per G latents
+    const size_t lat = (size_t)ctx->N * ctx->cfg.C;
+    for (int i0 = 0; i0 < batch; i0 += G) {
+      const int g = std::min(G, batch - i0);
+      std::vector<float*> xs(g);
+      std::vector<int> a6(g, which == WM_P6 ? 1 : 0), a1(g, which == WM_P1 ? 1 : 0);
+      for (int i = 0; i < g; ++i) xs[i] = x + (i0 + i) * lat;
+      WM_TRY(rollout_small(ctx, xs.data(), a6.data(), a1.data(), g, s));
+    }
+    return WM_OK;
+  }
   const int L = which == WM_P6 ? ctx->cfg.blocks_p6 : ctx->cfg.blocks_p1;
   for (int b = 0; b < L; ++b) WM_TRY(block_forward(ctx, x, batch, which, b, b == 0, s));
   return WM_OK;
@@ -646,6 +671,110 @@ wm_status run_graph(wm_ctx* ctx, const std::vector<uintptr_t>& key, cudaStream_t
   return WM_OK;
 }
 
+// ---- whole-rollout kernel for narrow latents
+
+// Patches of 8 x 16 tokens tile every level; the latitude halo of every patch
+// row spans 8 to 12 rows (a warp's 8-row key rectangle fits in it).
+bool rollout_small_shape(const wm_config& c) {
+  if (c.precision != WM_PREC_BF16 || c.C != 128 || c.heads != 4 || !c.lon_periodic || c.rope) return false;
+  if (c.H % 8 || c.W % 16 || c.W < 32 || c.kh > 5 || c.kw > 5 || c.kd > c.D) return false;
+  const int rh = c.kh / 2;
+  auto start = [&](int h) { return std::min(std::max(h - rh, 0), c.H - c.kh); };
+  for (int h0 = 0; h0 < c.H; h0 += 8) {
+    const int rows = start(h0 + 7) + c.kh - start(h0);
+    if (rows < 8 || rows > 12) return false;
+  }
+  return true;
+}
+
+// G latents of this context in one launch: the shape above, room on the
+// device for all their patches at once, and no per-launch timing requested.
+bool rollout_small_fits(const wm_ctx* ctx, int G) {
+  if (g_fused_rollout.load() == 0 || ctx->timing || !rollout_small_shape(ctx->cfg)) return false;
+  if (G < 1 || G > wm::kRolloutSmallMaxLatents) return false;
+  const int T = ctx->cfg.D * (ctx->cfg.H / 8) * (ctx->cfg.W / 16);
+  return G * T <= wm::rollout_small_capacity();
+}
+
+// Latents per whole-rollout launch for `batch` latents of this context: the
+// most that fit on the device at once (at most `batch`), 0 when the kernel
+// does not apply.
+int rollout_small_group(const wm_ctx* ctx, int batch) {
+  if (batch < 1 || !rollout_small_fits(ctx, 1)) return 0;
+  const int T = ctx->cfg.D * (ctx->cfg.H / 8) * (ctx->cfg.W / 16);
+  return std::min({batch, wm::kRolloutSmallMaxLatents, wm::rollout_small_capacity() / T});
+}
+
+// Once per context: every block's weights as 12 swizzled bf16 chunks and the
+// per-block table the kernel reads.
+wm_status prepare_rollout_small(wm_ctx* ctx) {
+  if (ctx->d_rs_blk) return WM_OK;
+  const size_t C = 128, chunk = 128 * 128;
+  const size_t nb = ctx->blk[0].size() + ctx->blk[1].size();
+  WM_CUDA(cudaMalloc(&ctx->d_rs_w, nb * 12 * chunk * sizeof(bf16)));
+  std::vector<wm::RolloutBlock> tab;
+  for (int which = 0; which < 2; ++which)
+    for (const BlockW& w : ctx->blk[which]) {
+      bf16* out = ctx->d_rs_w + tab.size() * 12 * chunk;
+      for (size_t c = 0; c < 3; ++c) WM_TRY(wm::launch_swizzle_chunk(w.wqkv + 128 * c * C, (int)C, out + c * chunk, 0));
+      WM_TRY(wm::launch_swizzle_chunk(w.wo, (int)C, out + 3 * chunk, 0));
+      for (size_t j = 0; j < 4; ++j) WM_TRY(wm::launch_swizzle_chunk(w.w1 + 128 * j * C, (int)C, out + (4 + j) * chunk, 0));
+      for (size_t j = 0; j < 4; ++j) WM_TRY(wm::launch_swizzle_chunk(w.w2 + 128 * j, (int)(4 * C), out + (8 + j) * chunk, 0));
+      tab.push_back({out, w.ln1_g, w.ln1_b, w.bqkv, w.bo, w.ln2_g, w.ln2_b, w.b1, w.b2});
+    }
+  WM_CUDA(cudaMalloc(&ctx->d_rs_blk, tab.size() * sizeof(wm::RolloutBlock)));
+  WM_CUDA(cudaMemcpy(ctx->d_rs_blk, tab.data(), tab.size() * sizeof(wm::RolloutBlock), cudaMemcpyHostToDevice));
+  WM_CUDA(cudaMalloc(&ctx->d_rs_bar, wm::kRolloutSmallMaxLatents * sizeof(unsigned int)));
+  WM_CUDA(cudaDeviceSynchronize());
+  return WM_OK;
+}
+
+// Weights and workspace for launches of up to the group size of `batch`
+// latents, before a graph capture that may contain such launches.
+wm_status rollout_small_reserve(wm_ctx* ctx, int batch) {
+  const int G = rollout_small_group(ctx, batch);
+  if (G == 0) return WM_OK;
+  WM_TRY(prepare_rollout_small(ctx));
+  return ensure_buffer(&ctx->d_rs_qkv, &ctx->rs_qkv_cap, (size_t)G * ctx->N * 384);
+}
+
+// Latents x[0..G) advance n6[i] six-hour then n1[i] one-hour steps (each at
+// least one block) in one launch; rollout_small_fits(ctx, G) must hold.
+wm_status rollout_small(wm_ctx* ctx, float* const* x, const int* n6, const int* n1, int G, cudaStream_t s) {
+  const wm_config& c = ctx->cfg;
+  const size_t qkv_floats = (size_t)G * ctx->N * 384;   // 2 x G x N x 384 bf16
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  WM_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) {
+    // inside a graph capture nothing may be allocated: rollout_small_reserve ran before
+    if (!ctx->d_rs_blk || qkv_floats > ctx->rs_qkv_cap)
+      return fail(WM_ERR_INVALID_ARG, "whole-rollout kernel captured without its workspace reserved");
+  } else {
+    WM_TRY(prepare_rollout_small(ctx));
+    WM_TRY(ensure_buffer(&ctx->d_rs_qkv, &ctx->rs_qkv_cap, qkv_floats));
+  }
+  wm::RolloutSmallArgs a{};
+  a.blk = ctx->d_rs_blk;
+  a.L6 = c.blocks_p6;
+  a.L1 = c.blocks_p1;
+  a.G = G;
+  a.T = c.D * (c.H / 8) * (c.W / 16);
+  a.D = c.D; a.H = c.H; a.W = c.W; a.kd = c.kd; a.kh = c.kh; a.kw = c.kw;
+  for (int i = 0; i < G; ++i) {
+    a.x[i] = x[i];
+    a.n6[i] = n6[i];
+    a.n1[i] = n1[i];
+  }
+  a.qkv = reinterpret_cast<bf16*>(ctx->d_rs_qkv);
+  a.bar = ctx->d_rs_bar;
+  a.status = wm::device_status_word();
+  a.eps = c.ln_eps;
+  a.scale_log2 = (float)(1.4426950408889634 / std::sqrt(32.0));
+  WM_CUDA(cudaMemsetAsync(ctx->d_rs_bar, 0, G * sizeof(unsigned int), s));
+  wm::NvtxRange range("whole rollout (narrow latent)");
+  return wm::launch_rollout_small(a, s);
+}
+
 }  // namespace
 
 namespace wm {
@@ -657,6 +786,7 @@ wm_status processor_step_graphed(wm_ctx* ctx, float* x, int batch, int which, cu
   if (which != WM_P6 && which != WM_P1) return fail(WM_ERR_INVALID_ARG, "which must be WM_P6 or WM_P1");
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   WM_TRY(ensure_workspace(ctx, batch));
+  WM_TRY(rollout_small_reserve(ctx, batch));
   const std::vector<uintptr_t> key = {4, (uintptr_t)x, (uintptr_t)batch, (uintptr_t)which,
                                       (uintptr_t)ctx->cfg.precision};
   return run_graph(ctx, key, s, [&](cudaStream_t st) -> wm_status { return processor_step(ctx, x, batch, which, st); });
@@ -941,6 +1071,10 @@ wm_status wm_destroy(wm_ctx* ctx) {
   cudaFree(ctx->d_vf);
   cudaFree(ctx->d_rope_tab);
   cudaFree(ctx->d_rope);
+  cudaFree(ctx->d_rs_w);
+  cudaFree(ctx->d_rs_blk);
+  cudaFree(ctx->d_rs_qkv);
+  cudaFree(ctx->d_rs_bar);
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_io);
   for (float* p : ctx->d_ring) cudaFree(p);
@@ -986,6 +1120,19 @@ wm_status wm_latent_rollout(wm_ctx* ctx, float* latent, int batch, int lead_hour
   int n6 = 0, n1 = 0;
   wm_schedule(lead_hours, &n6, &n1);
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  const int G = rollout_small_group(ctx, batch);
+  if (G > 0) {
+    // narrow latent: whole rollouts in launches of G latents each
+    const size_t lat = (size_t)ctx->N * ctx->cfg.C;
+    for (int i0 = 0; i0 < batch; i0 += G) {
+      const int g = std::min(G, batch - i0);
+      std::vector<float*> xs(g);
+      std::vector<int> a6(g, n6), a1(g, n1);
+      for (int i = 0; i < g; ++i) xs[i] = latent + (i0 + i) * lat;
+      WM_TRY(rollout_small(ctx, xs.data(), a6.data(), a1.data(), g, (cudaStream_t)stream));
+    }
+    return WM_OK;
+  }
   WM_TRY(ensure_workspace(ctx, batch));
   std::vector<uintptr_t> key = {1, (uintptr_t)latent, (uintptr_t)batch, (uintptr_t)n6, (uintptr_t)n1,
                                 (uintptr_t)ctx->cfg.precision};
@@ -1092,6 +1239,29 @@ wm_status wm_rollout_batch(wm_ctx* ctx, float* const* latents, const int* lead_h
     ticks = std::max(ticks, n6[i] + n1[i]);
   }
   if (ticks == 0) return WM_OK;
+  const int G = rollout_small_group(ctx, n);
+  if (G > 0) {
+    // narrow latent: launches of up to G latents with their own schedules,
+    // longest rollouts together, read and written in place (no gather)
+    std::vector<int> order;
+    for (int i = 0; i < n; ++i)
+      if (n6[i] + n1[i] > 0) order.push_back(i);
+    const int L6 = ctx->cfg.blocks_p6, L1 = ctx->cfg.blocks_p1;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int p, int q) { return n6[p] * L6 + n1[p] * L1 > n6[q] * L6 + n1[q] * L1; });
+    for (size_t i0 = 0; i0 < order.size(); i0 += G) {
+      const int g = (int)std::min(order.size() - i0, (size_t)G);
+      std::vector<float*> xs(g);
+      std::vector<int> a6(g), a1(g);
+      for (int i = 0; i < g; ++i) {
+        xs[i] = latents[order[i0 + i]];
+        a6[i] = n6[order[i0 + i]];
+        a1[i] = n1[order[i0 + i]];
+      }
+      WM_TRY(rollout_small(ctx, xs.data(), a6.data(), a1.data(), g, (cudaStream_t)stream));
+    }
+    return WM_OK;
+  }
   WM_TRY(ensure_workspace(ctx, n));
   const size_t lat = (size_t)ctx->N * ctx->cfg.C;
   WM_TRY(ensure_buffer(&ctx->d_stage, &ctx->stage_cap, lat * n));
@@ -1190,6 +1360,7 @@ wm_status wm_rollout_hourly(wm_ctx* ctx, const float* x, int max_lead, float* ou
   const int K = max_lead / 6;
   WM_TRY(ensure_workspace(ctx, std::max(1, std::min(max_batch, K + 1))));
   WM_TRY(ensure_buffer(&ctx->d_stage, &ctx->stage_cap, lat * std::min(max_batch, K + 1)));
+  WM_TRY(rollout_small_reserve(ctx, std::max(1, std::min(max_batch, K + 1))));
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<uintptr_t> key = {3, (uintptr_t)x, (uintptr_t)out, (uintptr_t)max_lead, (uintptr_t)max_batch,
                                 (uintptr_t)ctx->cfg.precision};
@@ -1311,6 +1482,12 @@ wm_status wm_op_linear(const void* A, const void* W, const float* bias, void* ou
   a.M = M; a.N = N; a.K = K;
   a.bias = bias; a.epi = epilogue;
   return wm::launch_gemm_tc(a, s);
+}
+
+wm_status wm_set_fused_rollout(int enable) {
+  if (enable < 0 || enable > 1) return fail(WM_ERR_INVALID_ARG, "fused rollout switch must be 0 or 1");
+  g_fused_rollout.store(enable);
+  return WM_OK;
 }
 
 wm_status wm_set_fused_mlp(int enable) {

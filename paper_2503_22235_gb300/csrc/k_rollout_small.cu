@@ -1,0 +1,786 @@
+// Whole-rollout persistent kernel for narrow latents (C = 128, 4 heads of 32
+// channels): every block of the greedy schedule of every latent in ONE launch.
+//
+// Why: at C = 128 a block's five GEMM / attention launches are each a few
+// microseconds of latency on a few dozen SMs, so a 14-day rollout (448 blocks)
+// is bound by launch and memory round trips, not by arithmetic. Here each CTA
+// owns one 8 x 16 (latitude x longitude) patch of 128 tokens of one level of
+// one latent for the whole rollout; its residual rows stay in shared memory,
+// and per block (pre-LN transformer block, paper Sec. 2.1 and App. A.2):
+//
+//   attention   8 warps, mma.sync m16n8k16: each warp takes a 4 x 4 query
+//               group and one head at a time and walks its 8 x 8 key
+//               rectangle per key level (K/V slabs of the patch's halo staged
+//               in shared memory by cp.async, double buffered), FP32 online
+//               softmax; O goes to shared memory as the next GEMM's A operand
+//   proj        tcgen05.mma (M = N = 128, K = 128) into TMEM; x += acc + b_o;
+//               LayerNorm 2 of the new rows (two-pass, FP32) -> bf16 A operand
+//   MLP         four 128-column hidden chunks: FC1 into two TMEM buffers,
+//               bias + erf GELU -> bf16 chunk in shared memory, FC2 K slice
+//               accumulated in TMEM; x += acc + b_2
+//   LN1 + QKV   LayerNorm 1 of the next block -> A operand; Q, K, V (+ bias) to
+//               a double-buffered bf16 [3C] array in global memory (L2)
+//   barrier     the latent's CTAs meet at a counter in global memory (bounded
+//               spin), then read their neighbours' K/V for the next block
+//
+// Roles (320 threads): warps 0-7 compute (attention, epilogues, LayerNorm),
+// warp 8 one thread issuing the tcgen05 MMAs, warp 9 one thread streaming the
+// block's weights (12 pre-swizzled 32 KB chunks per block, one bulk copy
+// each) through a two-slot ring. Latents are independent: each has its own
+// schedule (six-hour blocks, then one-hour blocks) and its own barrier, so
+// latents with different lead times share the launch.
+//
+// Every mbarrier wait and the latent barrier are bounded in time; on a
+// timeout the CTA records WM_ERR_TIMEOUT, the compute warps leave together
+// (barrier with OR-reduction), copies and MMAs in flight are drained, TMEM
+// is freed and the CTA returns.
+#include "tc_gemm.cuh"
+
+namespace wm {
+namespace rs {
+
+using namespace ptx;
+using namespace tc;
+using bf16 = __nv_bfloat16;
+using Blk = RolloutBlock;
+
+constexpr int C = 128, DH = 32, QKV = 3 * C;
+constexpr int TH = 8, TW = 16;                 // query patch of one CTA
+constexpr int SW = TW + 4;                     // slab columns: the patch's longitudes + 2 on each side
+constexpr int SR_MAX = TH + 4;                 // slab rows (latitude windows of at most 5)
+constexpr int THREADS = 320, MMA_WARP = 8, LOAD_WARP = 9;
+constexpr int CHUNK = 128 * 128 * 2;           // 128 x 128 bf16 operand: two 64-column 128B-swizzled slices
+constexpr int SLICE = CHUNK / 2;
+constexpr int OFF_X = 0;                       // fp32 residual rows [128][128], 16-byte units swizzled
+constexpr int OFF_A = 128 * C * 4;             // A operand: LN1(x), O or LN2(x)
+constexpr int OFF_W = OFF_A + CHUNK;           // weight ring, 2 slots
+constexpr int OFF_H = OFF_W + 2 * CHUNK;       // GELU chunks, 2 slots; the attention's K/V stages alias it
+constexpr int SMEM_USED = OFF_H + 2 * CHUNK;
+constexpr int SMEM = SMEM_USED + 1024;         // + alignment slack
+constexpr int KV_SLAB = SR_MAX * SW * DH * 2;  // one head's K (or V) rows of a key level
+constexpr int KV_STAGE = 2 * KV_SLAB;
+constexpr int OFF_RED = OFF_H + 2 * KV_STAGE;  // LayerNorm row partials [2 passes][2 halves][128]
+static_assert(OFF_RED + 4 * 128 * 4 <= SMEM_USED, "LayerNorm exchange must fit in the GELU region");
+constexpr uint32_t T_ACC1 = 0;                 // FC1 accumulators at 0 and 128; QKV chunks at 0, 128, 256
+constexpr uint32_t T_ACC2 = 256, T_PROJ = 384;
+// weight chunks of a block, in this order in memory
+constexpr int W_QKV = 0, W_O = 3, W_1 = 4, W_2 = 8;
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// ---- compute-warp barriers (named barrier 1, the 256 compute threads)
+__device__ __forceinline__ void bar_compute() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// The same barrier, returning the OR of `p` over the compute threads: every
+// compute warp takes the same decision from it.
+__device__ __forceinline__ bool bar_compute_or(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&p);
+}
+// global -> shared bulk copy completing on an mbarrier (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// byte offset of bf16 element (r, c) of a 128 x 128 operand (two 128B-swizzled 64-column slices)
+__device__ __forceinline__ uint32_t op_off(int r, int c) {
+  return (uint32_t)((c >> 6) * SLICE + r * 128 + ((((c & 63) >> 3) ^ (r & 7)) << 4) + (c & 7) * 2);
+}
+// byte offset of fp32 16-byte unit u (columns 4u .. 4u + 3) of residual row r
+__device__ __forceinline__ uint32_t x_off(int r, int u) { return (uint32_t)(OFF_X + r * 512 + ((u ^ (r & 7)) << 4)); }
+
+// Block i of latent g: six-hour blocks first, then one-hour blocks.
+__device__ __forceinline__ const Blk* block_of(const RolloutSmallArgs& a, int g, int i) {
+  const int p6 = a.n6[g] * a.L6;
+  return i < p6 ? a.blk + (i % a.L6) : a.blk + a.L6 + (i - p6) % a.L1;
+}
+
+// A block's vector as float4s. Each phase reads the pointers it needs into
+// registers before its first global store (the stores would otherwise make
+// the compiler re-read the table after each one).
+__device__ __forceinline__ const float4* f4(const float* p) { return reinterpret_cast<const float4*>(p); }
+
+// LayerNorm of the thread's 64 columns (half hf of row r) with the partner
+// half's partial sums exchanged through shared memory (two passes: mean, then
+// the mean squared deviation), affine, rounded to bf16 into the A operand.
+__device__ __forceinline__ void layernorm_to_a(uint8_t* smem, const float (&v)[64], int r, int hf,
+                                               const float4* __restrict__ gamma, const float4* __restrict__ beta,
+                                               float eps) {
+  float* red = reinterpret_cast<float*>(smem + OFF_RED);
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < 64; ++j) s += v[j];
+  red[hf * 128 + r] = s;
+  bar_compute();
+  const float mean = (red[r] + red[128 + r]) * (1.f / C);
+  float q = 0.f;
+#pragma unroll
+  for (int j = 0; j < 64; ++j) {
+    const float dv = v[j] - mean;
+    q += dv * dv;
+  }
+  red[256 + hf * 128 + r] = q;
+  bar_compute();
+  const float rstd = rsqrtf((red[256 + r] + red[384 + r]) * (1.f / C) + eps);
+  uint8_t* A = smem + OFF_A;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = 8 * k, c4 = (64 * hf + j) >> 2;
+    const float4 g0 = __ldg(gamma + c4), g1 = __ldg(gamma + c4 + 1);
+    const float4 b0 = __ldg(beta + c4), b1 = __ldg(beta + c4 + 1);
+    const uint32_t w0 = pack_bf16((v[j] - mean) * rstd * g0.x + b0.x, (v[j + 1] - mean) * rstd * g0.y + b0.y);
+    const uint32_t w1 = pack_bf16((v[j + 2] - mean) * rstd * g0.z + b0.z, (v[j + 3] - mean) * rstd * g0.w + b0.w);
+    const uint32_t w2 = pack_bf16((v[j + 4] - mean) * rstd * g1.x + b1.x, (v[j + 5] - mean) * rstd * g1.y + b1.y);
+    const uint32_t w3 = pack_bf16((v[j + 6] - mean) * rstd * g1.z + b1.z, (v[j + 7] - mean) * rstd * g1.w + b1.w);
+    *reinterpret_cast<uint4*>(A + hf * SLICE + r * 128 + ((k ^ (r & 7)) << 4)) = make_uint4(w0, w1, w2, w3);
+  }
+}
+
+// x[r, 64 hf + 32 sub ..] += acc + bias for 32 columns; the new values into v[32 sub ..]
+__device__ __forceinline__ void residual_add32(uint8_t* smem, int r, int hf, int sub, const float (&acc)[32],
+                                               const float4* __restrict__ bias, float (&v)[64]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int u = 16 * hf + 8 * sub + q;
+    float4* p = reinterpret_cast<float4*>(smem + x_off(r, u));
+    float4 x = *p;
+    const float4 b = __ldg(bias + u);
+    x.x += acc[4 * q] + b.x;
+    x.y += acc[4 * q + 1] + b.y;
+    x.z += acc[4 * q + 2] + b.z;
+    x.w += acc[4 * q + 3] + b.w;
+    *p = x;
+    v[32 * sub + 4 * q] = x.x;
+    v[32 * sub + 4 * q + 1] = x.y;
+    v[32 * sub + 4 * q + 2] = x.z;
+    v[32 * sub + 4 * q + 3] = x.w;
+  }
+}
+
+// Bounded wait (all lanes of the warp take the result of lane 0's view).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag));
+}
+
+// Arrive on the latent's counter and wait until `target` CTAs have arrived,
+// bounded in time. Every compute thread returns the same verdict.
+__device__ __forceinline__ bool latent_barrier(unsigned int* counter, unsigned int target, int warp, int lane,
+                                               volatile int* abort_flag) {
+  bar_compute();   // every compute thread's global stores of this phase are issued
+  int ok = 1;
+  if (warp == 0) {
+    if (lane == 0) {
+      __threadfence();
+      atomicAdd(counter, 1u);
+      const unsigned long long t0 = globaltimer();
+      while (true) {
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+        if (v >= target) break;
+        if (*abort_flag || globaltimer() - t0 > kWaitLimitNs) {
+          ok = 0;
+          break;
+        }
+      }
+      __threadfence();
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+  }
+  return !bar_compute_or(!ok);
+}
+
+__global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_constant__ RolloutSmallArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t w_full[2], w_empty[2], a_full, mma_done, drain_bar;
+  __shared__ __align__(8) uint64_t acc1_full[2], acc1_empty[2], h_full[2], h_empty[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x / a.T, tile = blockIdx.x % a.T;
+  const int nb = a.n6[g] * a.L6 + a.n1[g] * a.L1;   // blocks of this latent's rollout (>= 1)
+
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&w_full[b], 1);
+      mbar_init(&w_empty[b], 1);
+      mbar_init(&acc1_full[b], 1);
+      mbar_init(&acc1_empty[b], 8);
+      mbar_init(&h_full[b], 8);
+      mbar_init(&h_empty[b], 1);
+    }
+    mbar_init(&a_full, 8);
+    mbar_init(&mma_done, 1);
+    mbar_init(&drain_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == LOAD_WARP) {
+    if (lane == 0) {
+      // ------------------------------------------------------ weight stream
+      int seq = 0;
+      int last[2] = {-1, -1};   // parity of each slot's last copy (for the drain after a timeout)
+      bool ok = true;
+      auto load = [&](const bf16* src) -> bool {
+        const int slot = seq & 1;
+        const uint32_t use = (uint32_t)(seq >> 1);
+        if (!mbar_wait(&w_empty[slot], (use & 1u) ^ 1u, &abort_flag)) return false;
+        mbar_expect_tx(&w_full[slot], CHUNK);
+        bulk_g2s(sbase + OFF_W + slot * CHUNK, src, CHUNK, &w_full[slot]);
+        last[slot] = (int)(use & 1u);
+        ++seq;
+        return true;
+      };
+      constexpr int kOrder[9] = {W_O, W_1 + 0, W_1 + 1, W_2 + 0, W_1 + 2, W_2 + 1, W_1 + 3, W_2 + 2, W_2 + 3};
+      const bf16* w0 = block_of(a, g, 0)->w;
+      for (int c = 0; c < 3 && ok; ++c) ok = load(w0 + (size_t)(W_QKV + c) * (CHUNK / 2));
+      for (int i = 0; i < nb && ok; ++i) {
+        const bf16* w = block_of(a, g, i)->w;
+        for (int q = 0; q < 9 && ok; ++q) ok = load(w + (size_t)kOrder[q] * (CHUNK / 2));
+        if (i + 1 < nb) {
+          const bf16* wn = block_of(a, g, i + 1)->w;
+          for (int c = 0; c < 3 && ok; ++c) ok = load(wn + (size_t)(W_QKV + c) * (CHUNK / 2));
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(a.status, (int)WM_ERR_TIMEOUT);
+        volatile int never = 0;
+        for (int b = 0; b < 2; ++b)
+          if (last[b] >= 0) mbar_wait(&w_full[b], (uint32_t)last[b], &never);
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      // ------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(128, 128);
+      int seq = 0, a_cnt = 0;
+      bool ok = true;
+      // one 128 x 128 x 128 product: A operand at a_addr, the next weight chunk of the ring
+      auto gemm = [&](uint32_t col, uint32_t a_addr, bool acc_in) -> bool {
+        const int slot = seq & 1;
+        if (!mbar_wait(&w_full[slot], (uint32_t)(seq >> 1) & 1u, &abort_flag)) return false;
+        tc_fence_after();
+        const uint32_t b_addr = sbase + OFF_W + slot * CHUNK;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const uint64_t ad = sw128_desc(a_addr + s * SLICE), bd = sw128_desc(b_addr + s * SLICE);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            umma_bf16<false>(tmem + col, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc,
+                             (acc_in || s || k) ? 1u : 0u);
+        }
+        umma_commit(&w_empty[slot]);
+        ++seq;
+        return true;
+      };
+      auto wait_a = [&]() -> bool {
+        const bool r = mbar_wait(&a_full, (uint32_t)(a_cnt++) & 1u, &abort_flag);
+        tc_fence_after();
+        return r;
+      };
+      const uint32_t A = sbase + OFF_A;
+      auto qkv = [&]() -> bool {
+        if (!wait_a()) return false;
+        for (int c = 0; c < 3; ++c)
+          if (!gemm(T_ACC1 + 128 * c, A, false)) return false;
+        umma_commit(&mma_done);
+        return true;
+      };
+      auto fc1 = [&](int j) -> bool {
+        const int b = j & 1;
+        if (j >= 2 && !mbar_wait(&acc1_empty[b], 0u, &abort_flag)) return false;
+        tc_fence_after();
+        if (!gemm(T_ACC1 + 128 * b, A, false)) return false;
+        umma_commit(&acc1_full[b]);
+        return true;
+      };
+      auto fc2 = [&](int j) -> bool {
+        const int b = j & 1;
+        if (!mbar_wait(&h_full[b], (uint32_t)(j >> 1), &abort_flag)) return false;
+        tc_fence_after();
+        if (!gemm(T_ACC2, sbase + OFF_H + b * CHUNK, j > 0)) return false;
+        umma_commit(&h_empty[b]);
+        return true;
+      };
+      ok = qkv();
+      for (int i = 0; i < nb && ok; ++i) {
+        ok = wait_a() && gemm(T_PROJ, A, false);
+        if (!ok) break;
+        umma_commit(&mma_done);
+        ok = wait_a() && fc1(0) && fc1(1) && fc2(0) && fc1(2) && fc2(1) && fc1(3) && fc2(2) && fc2(3);
+        if (!ok) break;
+        umma_commit(&mma_done);
+        if (i + 1 < nb) ok = qkv();
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(a.status, (int)WM_ERR_TIMEOUT);
+      }
+      // every MMA issued so far completes before TMEM and shared memory are released
+      umma_commit(&drain_bar);
+      volatile int never = 0;
+      mbar_wait(&drain_bar, 0u, &never);
+    }
+  } else {
+    // ------------------------------------------------------ compute warps
+    const int r = 32 * (warp & 3) + lane, hf = warp >> 2;   // epilogue row and column half
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    const int tpr = a.W / TW, tpl = (a.H / TH) * tpr;
+    const int d = tile / tpl, h0 = ((tile % tpl) / tpr) * TH, w0 = (tile % tpr) * TW;
+    const long N = (long)a.D * a.H * a.W;
+    const long tok_r = ((long)d * a.H + h0 + (r >> 4)) * a.W + w0 + (r & 15);
+    float* xg = a.x[g] + tok_r * C + 64 * hf;
+    int md = 0;          // mma_done completions waited for
+    bool ok = true;
+    float v[64];
+
+    // attention geometry of this warp: a 4 x 4 query group (rows g8, g8 + 8 of the m16 tile)
+    const int gr = warp >> 2, gc = warp & 3, g8 = lane >> 2, t4 = lane & 3;
+    const int rh = a.kh / 2, rw = a.kw / 2;
+    const int S0 = clampi(h0 - rh, 0, a.H - a.kh);
+    const int SR = clampi(h0 + TH - 1 - rh, 0, a.H - a.kh) + a.kh - S0;
+    const int R0 = min(clampi(h0 + 4 * gr - rh, 0, a.H - a.kh) - S0, SR - 8);
+    const int qh0 = h0 + 4 * gr + (g8 >> 2), qh1 = qh0 + 2, qcl = g8 & 3;
+    const uint32_t kmask = (1u << a.kh) - 1u;
+    const uint32_t lat0 = kmask << (clampi(qh0 - rh, 0, a.H - a.kh) - S0 - R0);
+    const uint32_t lat1 = kmask << (clampi(qh1 - rh, 0, a.H - a.kh) - S0 - R0);
+    const bool lon0 = abs(2 * t4 - 2 - qcl) <= rw, lon1 = abs(2 * t4 + 1 - 2 - qcl) <= rw;
+    const int kd0 = clampi(d - a.kd / 2, 0, a.D - a.kd);
+    const int tq0 = (d * a.H + qh0) * a.W + w0 + 4 * gc + qcl, tq1 = tq0 + 2 * a.W;
+    const int ri0 = (4 * gr + (g8 >> 2)) * TW + 4 * gc + qcl, ri1 = ri0 + 2 * TW;
+    // ldmatrix row offsets within a stage (bytes): K rows per n8 block, V rows per (k16 step, matrix)
+    uint32_t koff[8], voff[4][2];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int key = (R0 + b) * SW + 4 * gc + (lane & 7), u = lane >> 3;
+      koff[b] = (uint32_t)(key * 64 + ((u ^ ((key >> 1) & 3)) << 4));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        const int mi = lane >> 3;
+        const int key = (R0 + 2 * q + (mi & 1)) * SW + 4 * gc + (lane & 7), u = 2 * np + (mi >> 1);
+        voff[q][np] = (uint32_t)(KV_SLAB + key * 64 + ((u ^ ((key >> 1) & 3)) << 4));
+      }
+
+    // K/V staging: this thread's fixed items (slab key k, K or V, 16-byte unit
+    // u); per step only the key level and the head move the source
+    // (item it = thread + 256 m: key k0 + 32 m, the same K/V and unit; the
+    // swizzle term (k >> 1) & 3 does not change with m)
+    const int items = SR * SW * 8;
+    int soff[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int it = threadIdx.x + 256 * m;
+      const int k = it >> 3, kv = (it >> 2) & 1, u = it & 3;
+      int lon = w0 - 2 + k % SW;
+      lon += lon < 0 ? a.W : 0;
+      lon -= lon >= a.W ? a.W : 0;
+      soff[m] = it < items ? ((S0 + k / SW) * a.W + lon) * QKV + C + kv * C + 8 * u : 0;
+    }
+    const int k0 = threadIdx.x >> 3, u0 = threadIdx.x & 3;
+    const uint32_t doff0 =
+        (uint32_t)(((threadIdx.x >> 2) & 1) * KV_SLAB + k0 * 64 + ((u0 ^ ((k0 >> 1) & 3)) << 4));
+    const long level_elems = (long)a.H * a.W * QKV;
+
+    // QKV epilogue: + bias, bf16 rows to the global qkv array of block buffer `buf`
+    auto qkv_epilogue = [&](const float4* __restrict__ bqkv, int buf) {
+      ok = warp_wait(&mma_done, (uint32_t)(md++) & 1u, &abort_flag) && ok;
+      if (!ok) abort_flag = 1;
+      tc_fence_after();
+      bf16* dst = a.qkv + (((long)buf * a.G + g) * N + tok_r) * QKV;
+#pragma unroll 1
+      for (int c = 0; c < 3; ++c)
+#pragma unroll 1
+        for (int sub = 0; sub < 2; ++sub) {
+          const int col = 128 * c + 64 * hf + 32 * sub;
+          float acc[32];
+          tmem_ld32(tmem + T_ACC1 + (uint32_t)col + lane_off, acc);
+          uint4* o = reinterpret_cast<uint4*>(dst + col);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 b0 = __ldg(bqkv + (col >> 2) + 2 * k), b1 = __ldg(bqkv + (col >> 2) + 2 * k + 1);
+            const int j = 8 * k;
+            o[k] = make_uint4(pack_bf16(acc[j] + b0.x, acc[j + 1] + b0.y), pack_bf16(acc[j + 2] + b0.z, acc[j + 3] + b0.w),
+                              pack_bf16(acc[j + 4] + b1.x, acc[j + 5] + b1.y), pack_bf16(acc[j + 6] + b1.z, acc[j + 7] + b1.w));
+          }
+        }
+      tc_fence_before();
+    };
+    auto a_ready = [&]() {
+      fence_async_smem();   // generic-proxy stores, read by the tensor core next
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&a_full);
+    };
+
+    // ---- prologue: residual rows in, LayerNorm 1 of block 0, QKV, latent barrier
+    {
+      const float4* src = reinterpret_cast<const float4*>(xg);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float4 x = src[q];
+        *reinterpret_cast<float4*>(smem + x_off(r, 16 * hf + q)) = x;
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+      }
+      const Blk* b0 = block_of(a, g, 0);
+      layernorm_to_a(smem, v, r, hf, f4(b0->ln1_g), f4(b0->ln1_b), a.eps);
+      a_ready();
+      qkv_epilogue(f4(b0->bqkv), 0);
+    }
+    unsigned int epoch = 0;
+    bool run = latent_barrier(a.bar + g, (++epoch) * (unsigned)a.T, warp, lane, &abort_flag) && !bar_compute_or(!ok);
+
+    for (int i = 0; i < nb && run; ++i) {
+      const Blk* bk = block_of(a, g, i);
+      const bf16* qkv_cur = a.qkv + ((long)(i & 1) * a.G + g) * N * QKV;
+      // ------------------------------------------------ neighborhood attention
+      {
+        const int steps = 4 * a.kd;
+        auto stage = [&](int s) {
+          const bf16* base = qkv_cur + (kd0 + s % a.kd) * level_elems + (s / a.kd) * DH;
+          const uint32_t dst0 = sbase + OFF_H + (s & 1) * KV_STAGE;
+#pragma unroll
+          for (int m = 0; m < 8; ++m)
+            if ((int)threadIdx.x + 256 * m < items) cp_async16(dst0 + doff0 + 2048u * m, base + soff[m]);
+          cp_async_commit();
+        };
+        // this lane's query rows of head h (A fragments of the two k16 steps)
+        auto load_q = [&](int h, uint32_t (&q)[2][4]) {
+          const bf16* q0 = qkv_cur + tq0 * QKV + h * DH + 2 * t4;
+          const bf16* q1 = qkv_cur + tq1 * QKV + h * DH + 2 * t4;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            q[kk][0] = __ldcg(reinterpret_cast<const unsigned int*>(q0 + 16 * kk));
+            q[kk][1] = __ldcg(reinterpret_cast<const unsigned int*>(q1 + 16 * kk));
+            q[kk][2] = __ldcg(reinterpret_cast<const unsigned int*>(q0 + 16 * kk + 8));
+            q[kk][3] = __ldcg(reinterpret_cast<const unsigned int*>(q1 + 16 * kk + 8));
+          }
+        };
+        stage(0);
+        float o[4][4], l0 = 0.f, l1 = 0.f, m0 = -INFINITY, m1 = -INFINITY;
+        uint32_t qa[2][4], qn[2][4];
+        load_q(0, qn);
+#pragma unroll 1
+        for (int s = 0; s < steps; ++s) {
+          const int h = s / a.kd, lv = s % a.kd;
+          if (s + 1 < steps) stage(s + 1);
+          else cp_async_commit();
+          cp_async_wait1();
+          bar_compute();
+          if (lv == 0) {
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+              for (int e = 0; e < 4; ++e) qa[kk][e] = qn[kk][e];
+            if (h + 1 < 4) load_q(h + 1, qn);   // the next head's queries, in flight during this head
+#pragma unroll
+            for (int nb8 = 0; nb8 < 4; ++nb8) o[nb8][0] = o[nb8][1] = o[nb8][2] = o[nb8][3] = 0.f;
+            l0 = l1 = 0.f;
+            m0 = m1 = -INFINITY;
+          }
+          const uint32_t kb = sbase + OFF_H + (s & 1) * KV_STAGE;
+          // S = Q K^T over the 8 x 8 key rectangle (8 n8 blocks, one per rectangle row)
+          float sc[8][4];
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            uint32_t k0, k1, k2, k3;
+            ldsm_x4(kb + koff[b], k0, k1, k2, k3);
+            sc[b][0] = sc[b][1] = sc[b][2] = sc[b][3] = 0.f;
+            mma16816(sc[b], qa[0], k0, k1);
+            mma16816(sc[b], qa[1], k2, k3);
+          }
+          // mask (latitude row of the rectangle, longitude column) and scale to log2 units
+          float mx0 = -INFINITY, mx1 = -INFINITY;
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            const bool r0v = (lat0 >> b) & 1u, r1v = (lat1 >> b) & 1u;
+            sc[b][0] = (r0v && lon0) ? sc[b][0] * a.scale_log2 : -INFINITY;
+            sc[b][1] = (r0v && lon1) ? sc[b][1] * a.scale_log2 : -INFINITY;
+            sc[b][2] = (r1v && lon0) ? sc[b][2] * a.scale_log2 : -INFINITY;
+            sc[b][3] = (r1v && lon1) ? sc[b][3] * a.scale_log2 : -INFINITY;
+            mx0 = fmaxf(mx0, fmaxf(sc[b][0], sc[b][1]));
+            mx1 = fmaxf(mx1, fmaxf(sc[b][2], sc[b][3]));
+          }
+          mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, 1));
+          mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, 2));
+          mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 1));
+          mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 2));
+          const float mn0 = fmaxf(m0, mx0), mn1 = fmaxf(m1, mx1);   // finite: every level holds window keys
+          const float al0 = ex2(m0 - mn0), al1 = ex2(m1 - mn1);
+          m0 = mn0;
+          m1 = mn1;
+          l0 *= al0;
+          l1 *= al1;
+#pragma unroll
+          for (int nb8 = 0; nb8 < 4; ++nb8) {
+            o[nb8][0] *= al0;
+            o[nb8][1] *= al0;
+            o[nb8][2] *= al1;
+            o[nb8][3] *= al1;
+          }
+          uint32_t pa[4][4];   // P as the A operand of the four k16 steps
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            const float p0 = ex2(sc[b][0] - mn0), p1 = ex2(sc[b][1] - mn0);
+            const float p2 = ex2(sc[b][2] - mn1), p3 = ex2(sc[b][3] - mn1);
+            l0 += p0 + p1;
+            l1 += p2 + p3;
+            pa[b >> 1][(b & 1) * 2 + 0] = pack_bf16(p0, p1);
+            pa[b >> 1][(b & 1) * 2 + 1] = pack_bf16(p2, p3);
+          }
+          // O += P V
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int np = 0; np < 2; ++np) {
+              uint32_t v0, v1, v2, v3;
+              ldsm_x4_t(kb + voff[q][np], v0, v1, v2, v3);
+              mma16816(o[2 * np], pa[q], v0, v1);
+              mma16816(o[2 * np + 1], pa[q], v2, v3);
+            }
+          if (lv == a.kd - 1) {
+            // head done: normalise, bf16 into the A operand (columns 32 h ..)
+            float s0 = l0, s1 = l1;
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+            const float i0 = 1.f / s0, i1 = 1.f / s1;
+#pragma unroll
+            for (int nb8 = 0; nb8 < 4; ++nb8) {
+              const int ch = h * DH + 8 * nb8 + 2 * t4;
+              *reinterpret_cast<uint32_t*>(smem + OFF_A + op_off(ri0, ch)) = pack_bf16(o[nb8][0] * i0, o[nb8][1] * i0);
+              *reinterpret_cast<uint32_t*>(smem + OFF_A + op_off(ri1, ch)) = pack_bf16(o[nb8][2] * i1, o[nb8][3] * i1);
+            }
+          }
+          bar_compute();   // the stage may be refilled
+        }
+        cp_async_wait0();
+      }
+      a_ready();
+      // ------------------------------------------------ output projection + residual, LayerNorm 2
+      ok = warp_wait(&mma_done, (uint32_t)(md++) & 1u, &abort_flag) && ok;
+      if (!ok) abort_flag = 1;
+      tc_fence_after();
+      {
+        const float4* bo = f4(bk->bo);
+        const float4* g2 = f4(bk->ln2_g);
+        const float4* be2 = f4(bk->ln2_b);
+#pragma unroll
+        for (int sub = 0; sub < 2; ++sub) {
+          float acc[32];
+          tmem_ld32(tmem + T_PROJ + (uint32_t)(64 * hf + 32 * sub) + lane_off, acc);
+          residual_add32(smem, r, hf, sub, acc, bo, v);
+        }
+        tc_fence_before();
+        layernorm_to_a(smem, v, r, hf, g2, be2, a.eps);
+      }
+      a_ready();
+      // ------------------------------------------------ MLP: FC1 chunks -> GELU -> shared memory
+      const float4* b1v = f4(bk->b1);
+#pragma unroll 1
+      for (int j = 0; j < 4; ++j) {
+        const int b = j & 1;
+        ok = warp_wait(&acc1_full[b], (uint32_t)(j >> 1), &abort_flag) && ok;
+        if (!ok) abort_flag = 1;
+        tc_fence_after();
+        uint8_t* H = smem + OFF_H + b * CHUNK + hf * SLICE;
+#pragma unroll 1
+        for (int sub = 0; sub < 2; ++sub) {
+          const int c = 64 * hf + 32 * sub;
+          float acc[32];
+          tmem_ld32(tmem + T_ACC1 + (uint32_t)(128 * b + c) + lane_off, acc);
+          if (sub == 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc1_empty[b]);
+          }
+          const float4* b1 = b1v + ((128 * j + c) >> 2);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 b = __ldg(b1 + q);
+            acc[4 * q] += b.x;
+            acc[4 * q + 1] += b.y;
+            acc[4 * q + 2] += b.z;
+            acc[4 * q + 3] += b.w;
+          }
+#pragma unroll
+          for (int jj = 0; jj < 32; jj += 2) gelu_erf2(acc[jj], acc[jj + 1]);
+          if (sub == 0 && j >= 2) {
+            // this slot's previous chunk has been read by FC2
+            ok = warp_wait(&h_empty[b], 0u, &abort_flag) && ok;
+            if (!ok) abort_flag = 1;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) w[e] = pack_bf16(acc[8 * k + 2 * e], acc[8 * k + 2 * e + 1]);
+            *reinterpret_cast<uint4*>(H + r * 128 + (((4 * sub + k) ^ (r & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&h_full[b]);
+      }
+      // ------------------------------------------------ FC2 + residual
+      ok = warp_wait(&mma_done, (uint32_t)(md++) & 1u, &abort_flag) && ok;
+      if (!ok) abort_flag = 1;
+      tc_fence_after();
+      {
+        const float4* b2 = f4(bk->b2);
+#pragma unroll
+        for (int sub = 0; sub < 2; ++sub) {
+          float acc[32];
+          tmem_ld32(tmem + T_ACC2 + (uint32_t)(64 * hf + 32 * sub) + lane_off, acc);
+          residual_add32(smem, r, hf, sub, acc, b2, v);
+        }
+      }
+      tc_fence_before();
+      if (i + 1 < nb) {
+        // ------------------------------------------------ next block: LayerNorm 1, QKV, latent barrier
+        const Blk* bn = block_of(a, g, i + 1);
+        const float4* bq = f4(bn->bqkv);
+        layernorm_to_a(smem, v, r, hf, f4(bn->ln1_g), f4(bn->ln1_b), a.eps);
+        a_ready();
+        qkv_epilogue(bq, (i + 1) & 1);
+        run = latent_barrier(a.bar + g, (++epoch) * (unsigned)a.T, warp, lane, &abort_flag);
+        run = !bar_compute_or(!ok) && run;
+      } else {
+        run = !bar_compute_or(!ok);
+        if (run) {
+          float4* dst = reinterpret_cast<float4*>(xg);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+      }
+    }
+    if (!run) {
+      abort_flag = 1;
+      atomicCAS(a.status, 0, (int)WM_ERR_TIMEOUT);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// One 128 x 128 chunk W[r0 + n][c0 + k] (row stride ld floats) as bf16 in the
+// 128B-swizzled K-major layout the MMA reads: column k of row n in slice
+// k / 64, 16-byte unit (k % 64) / 8 stored at unit ^ (n % 8).
+__global__ void swizzle_chunk_kernel(const float* __restrict__ W, int ld, bf16* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 128 * 16) return;
+  const int n = idx >> 4, uk = idx & 15;
+  const float* s = W + (size_t)n * ld + 8 * uk;
+  uint32_t w[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) w[e] = pack_bf16(s[2 * e], s[2 * e + 1]);
+  uint8_t* o = reinterpret_cast<uint8_t*>(out) + (uk >> 3) * SLICE + n * 128 + (((uk & 7) ^ (n & 7)) << 4);
+  *reinterpret_cast<uint4*>(o) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+}  // namespace rs
+
+wm_status launch_swizzle_chunk(const float* W, int ld, __nv_bfloat16* out, cudaStream_t s) {
+  rs::swizzle_chunk_kernel<<<8, 256, 0, s>>>(W, ld, out);
+  WM_CUDA(cudaGetLastError());
+  return WM_OK;
+}
+
+int rollout_small_capacity() {
+  static int cap = -1;
+  if (cap >= 0) return cap;
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(rs::rollout_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rs::SMEM) !=
+      cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rs::rollout_small_kernel, rs::THREADS, rs::SMEM) !=
+      cudaSuccess)
+    return 0;
+  cap = per * sms;
+  return cap;
+}
+
+wm_status launch_rollout_small(const RolloutSmallArgs& a, cudaStream_t s) {
+  const int grid = a.G * a.T;
+  if (a.G < 1 || a.G > kRolloutSmallMaxLatents || grid > rollout_small_capacity())
+    return fail(WM_ERR_INVALID_ARG, "small-latent rollout kernel: too many tiles for one cooperative launch");
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(rs::THREADS);
+  cfg.dynamicSmemBytes = rs::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  WM_CUDA(cudaLaunchKernelEx(&cfg, rs::rollout_small_kernel, a));
+  return WM_OK;
+}
+
+}  // namespace wm

@@ -283,6 +283,34 @@ struct MlpArgs {
 };
 wm_status launch_mlp_small(const MlpArgs& a, cudaStream_t s);
 
+// Whole-rollout kernel for latents with C = 128 and 4 heads (k_rollout_small.cu):
+// one cooperative launch runs every block of every latent's greedy schedule.
+constexpr int kRolloutSmallMaxLatents = 8;
+struct RolloutBlock {
+  const __nv_bfloat16* w;   // 12 chunks of 128 x 128 bf16 in the 128B-swizzled K-major
+                            // layout: Wqkv rows 0-127, 128-255, 256-383; Wo; W1 rows
+                            // 0-127 .. 384-511; W2 columns 0-127 .. 384-511
+  const float *ln1_g, *ln1_b, *bqkv, *bo, *ln2_g, *ln2_b, *b1, *b2;
+};
+struct RolloutSmallArgs {
+  const RolloutBlock* blk;   // device array: the six-hour blocks, then the one-hour blocks
+  int L6, L1;                // blocks per processor
+  int G, T;                  // latents; CTAs (8 x 16-token patches) per latent
+  int D, H, W, kd, kh, kw;   // H % 8 == 0, W % 16 == 0, W >= 32, kh <= 5, kw <= 5, periodic longitude
+  float* x[kRolloutSmallMaxLatents];     // fp32 latents [D*H*W, 128], updated in place
+  int n6[kRolloutSmallMaxLatents];       // six-hour steps per latent (then n1 one-hour steps)
+  int n1[kRolloutSmallMaxLatents];
+  __nv_bfloat16* qkv;        // workspace [2][G][D*H*W][384]
+  unsigned int* bar;         // [G] counters, zero at launch
+  int* status;               // device status word
+  float eps, scale_log2;     // LayerNorm epsilon; log2(e) / sqrt(32)
+};
+// CTAs the device can hold at once for the rollout kernel (0 when unknown).
+int rollout_small_capacity();
+wm_status launch_rollout_small(const RolloutSmallArgs& a, cudaStream_t s);
+// W[n][k] (row stride ld floats), n, k < 128, to one bf16 chunk of the layout above.
+wm_status launch_swizzle_chunk(const float* W, int ld, __nv_bfloat16* out, cudaStream_t s);
+
 // variant: WM_NA_* of wm.h (0 = tuned plan / the shape's fixed family).
 wm_status launch_na_bf16(const __nv_bfloat16* qkv, __nv_bfloat16* out, int B, int D, int H, int W, int C,
                          int heads, int kd, int kh, int kw, bool periodic, cudaStream_t s, int variant = 0,

@@ -40,6 +40,7 @@ def host(t):
 def _run(shape, batch, fn, fused, stress=True):
     p6, p1 = synth.processor_weights(shape, seed=0, stress=stress)
     wm.wm_set_fused_mlp(fused)
+    wm.wm_set_fused_rollout(0)   # processor steps and rollouts through the per-kernel path
     try:
         ctx = wm.wm_create_from_host(wm.make_config(shape, wm.WM_PREC_BF16, batch), synth.pack_weights(p6, p1))
         try:
@@ -50,6 +51,7 @@ def _run(shape, batch, fn, fused, stress=True):
             wm.wm_destroy(ctx)
     finally:
         wm.wm_set_fused_mlp(0)
+        wm.wm_set_fused_rollout(1)
 
 
 @pytest.mark.parametrize("shape,batch", [(synth.SMALL, 1), (synth.SMALL, 3), (RAGGED, 1)])

@@ -155,6 +155,7 @@ def test_64_column_tiles_processor_step_small_latent(precision):
     x = synth.latent(s, 2, seed=1)
     try:
         wm.wm_gemm_tile_override(wm.GEMM_TILES_64)
+        wm.wm_set_fused_rollout(0)   # the step through the per-kernel GEMMs
         ctx = wm.wm_create_from_host(wm.make_config(s, prec, 2), synth.pack_weights(p6, p1))
         try:
             xt = torch.from_numpy(x).to(CUDA)
@@ -164,6 +165,7 @@ def test_64_column_tiles_processor_step_small_latent(precision):
             wm.wm_destroy(ctx)
     finally:
         wm.wm_gemm_tile_override(wm.GEMM_TILES_TUNED)
+        wm.wm_set_fused_rollout(1)
     if precision == "bf16":
         ref = orc.processor(x, p1, s)
     else:

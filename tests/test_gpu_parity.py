@@ -277,9 +277,13 @@ def test_block_bf16_small_latent(stress):
         wm.wm_destroy(ctx)
 
 
-def test_processor_steps_bf16_and_fp32_small_latent():
+@pytest.mark.parametrize("fused", [1, 0])
+def test_processor_steps_bf16_and_fp32_small_latent(fused):
+    """P6 then P1 on the small latent against the oracle; in BF16 through the
+    whole-rollout kernel (fused = 1) and through one launch per kernel (0)."""
     s = synth.SMALL
     ctx, p6, p1 = make_ctx(s, wm.WM_PREC_BF16, stress=True)
+    wm.wm_set_fused_rollout(fused)
     try:
         x = synth.latent(s, 1, seed=3)
         ref6 = orc.processor(x, p6, s)
@@ -292,6 +296,7 @@ def test_processor_steps_bf16_and_fp32_small_latent():
             wm.wm_processor_step(ctx, xt, wm.WM_P1)
             assert_close(host(xt), ref61, tol, s.C, (prec, "P6 then P1"))
     finally:
+        wm.wm_set_fused_rollout(1)
         wm.wm_destroy(ctx)
 
 

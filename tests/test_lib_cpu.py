@@ -79,6 +79,9 @@ def test_null_arguments_are_rejected():
     assert L.wm_processor_step(None, None, 1, 0, None) == wm.WM_ERR_INVALID_ARG
     assert L.wm_destroy(None) == wm.WM_OK
     assert L.wm_rollout_batch(None, None, None, 0, None) == wm.WM_ERR_INVALID_ARG
+    assert L.wm_set_fused_rollout(2) == wm.WM_ERR_INVALID_ARG
+    assert L.wm_set_fused_rollout(-1) == wm.WM_ERR_INVALID_ARG
+    assert L.wm_set_fused_rollout(1) == wm.WM_OK
 
 
 def _header_arity():
