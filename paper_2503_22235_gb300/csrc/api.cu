@@ -88,7 +88,7 @@ struct wm_ctx {
   std::vector<std::pair<int, int>> ev_marks;  // (kernel kind, index of the start event)
   cudaStream_t cap_stream = nullptr;
   // whole-rollout kernel for narrow latents (k_rollout_small.cu)
-  bf16* d_rs_w = nullptr;                 // swizzled bf16 weight chunks, 12 per block
+  bf16* d_rs_w = nullptr;                 // per block: 12 swizzled bf16 weight chunks and the fp32 vectors
   wm::RolloutBlock* d_rs_blk = nullptr;   // per-block table: six-hour blocks, then one-hour blocks
   float* d_rs_qkv = nullptr;              // its double-buffered bf16 q, k, v (capacity in floats)
   size_t rs_qkv_cap = 0;
@@ -711,16 +711,25 @@ wm_status prepare_rollout_small(wm_ctx* ctx) {
   if (ctx->d_rs_blk) return WM_OK;
   const size_t C = 128, chunk = 128 * 128;
   const size_t nb = ctx->blk[0].size() + ctx->blk[1].size();
-  WM_CUDA(cudaMalloc(&ctx->d_rs_w, nb * 12 * chunk * sizeof(bf16)));
+  const size_t per = wm::kRolloutBlockBytes / sizeof(bf16);
+  WM_CUDA(cudaMalloc(&ctx->d_rs_w, nb * wm::kRolloutBlockBytes));
   std::vector<wm::RolloutBlock> tab;
   for (int which = 0; which < 2; ++which)
     for (const BlockW& w : ctx->blk[which]) {
-      bf16* out = ctx->d_rs_w + tab.size() * 12 * chunk;
+      bf16* out = ctx->d_rs_w + tab.size() * per;
       for (size_t c = 0; c < 3; ++c) WM_TRY(wm::launch_swizzle_chunk(w.wqkv + 128 * c * C, (int)C, out + c * chunk, 0));
       WM_TRY(wm::launch_swizzle_chunk(w.wo, (int)C, out + 3 * chunk, 0));
       for (size_t j = 0; j < 4; ++j) WM_TRY(wm::launch_swizzle_chunk(w.w1 + 128 * j * C, (int)C, out + (4 + j) * chunk, 0));
       for (size_t j = 0; j < 4; ++j) WM_TRY(wm::launch_swizzle_chunk(w.w2 + 128 * j, (int)(4 * C), out + (8 + j) * chunk, 0));
-      tab.push_back({out, w.ln1_g, w.ln1_b, w.bqkv, w.bo, w.ln2_g, w.ln2_b, w.b1, w.b2});
+      // the vectors, fp32, after the chunks
+      float* vec = reinterpret_cast<float*>(out + 12 * chunk);
+      const std::pair<const float*, size_t> parts[8] = {{w.bqkv, 3 * C}, {w.bo, C},     {w.ln1_g, C}, {w.ln1_b, C},
+                                                        {w.ln2_g, C},    {w.ln2_b, C}, {w.b1, 4 * C}, {w.b2, C}};
+      for (const auto& pv : parts) {
+        WM_CUDA(cudaMemcpy(vec, pv.first, pv.second * sizeof(float), cudaMemcpyDeviceToDevice));
+        vec += pv.second;
+      }
+      tab.push_back({out});
     }
   WM_CUDA(cudaMalloc(&ctx->d_rs_blk, tab.size() * sizeof(wm::RolloutBlock)));
   WM_CUDA(cudaMemcpy(ctx->d_rs_blk, tab.data(), tab.size() * sizeof(wm::RolloutBlock), cudaMemcpyHostToDevice));
@@ -766,6 +775,10 @@ wm_status rollout_small(wm_ctx* ctx, float* const* x, const int* n6, const int* 
     a.n1[i] = n1[i];
   }
   a.qkv = reinterpret_cast<bf16*>(ctx->d_rs_qkv);
+  const uint32_t box_w[3] = {20, 18, 2};
+  for (int k = 0; k < 3; ++k)
+    if (!wm::make_tmap_kv_slab(&a.tm_kv[k], a.qkv, 384, (uint64_t)c.W, (uint64_t)c.H, 2ull * G * c.D, box_w[k], 12))
+      return fail(WM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the whole-rollout K/V rows");
   a.bar = ctx->d_rs_bar;
   a.status = wm::device_status_word();
   a.eps = c.ln_eps;

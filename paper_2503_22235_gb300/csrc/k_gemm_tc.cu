@@ -1196,6 +1196,21 @@ bool make_tmap_qkv_slab(CUtensorMap* map, const void* qkv, uint64_t C3, uint64_t
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool make_tmap_kv_slab(CUtensorMap* map, const void* qkv, uint64_t C3, uint64_t W, uint64_t H, uint64_t levels,
+                       uint32_t box_w, uint32_t box_h) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(qkv) & 15) || (C3 * 2) % 16 || box_w == 0 || box_w > W || box_h == 0 ||
+      box_h > 256 || levels == 0)
+    return false;
+  cuuint64_t dims[4] = {C3, W, H, levels};
+  cuuint64_t strides[3] = {C3 * 2, W * C3 * 2, H * W * C3 * 2};
+  cuuint32_t box[4] = {32, box_w, box_h, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(qkv), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || rows == 0 || cols == 0 || (cols * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15)) return false;

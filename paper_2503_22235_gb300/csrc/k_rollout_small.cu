@@ -5,14 +5,16 @@
 // microseconds of latency on a few dozen SMs, so a 14-day rollout (448 blocks)
 // is bound by launch and memory round trips, not by arithmetic. Here each CTA
 // owns one 8 x 16 (latitude x longitude) patch of 128 tokens of one level of
-// one latent for the whole rollout; its residual rows stay in shared memory,
+// one latent for the whole rollout; its residual rows stay in tensor memory,
 // and per block (pre-LN transformer block, paper Sec. 2.1 and App. A.2):
 //
 //   attention   8 warps, mma.sync m16n8k16: each warp takes a 4 x 4 query
 //               group and one head at a time and walks its 8 x 8 key
-//               rectangle per key level (K/V slabs of the patch's halo staged
-//               in shared memory by cp.async, double buffered), FP32 online
-//               softmax; O goes to shared memory as the next GEMM's A operand
+//               rectangle per key level (K/V slabs of the patch's halo brought
+//               to shared memory by tensor copies from a producer warp, one
+//               box per slab and two where the longitude wraps, double
+//               buffered), FP32 online softmax; O goes to shared memory as the
+//               next GEMM's A operand
 //   proj        tcgen05.mma (M = N = 128, K = 128) into TMEM; x += acc + b_o;
 //               LayerNorm 2 of the new rows (two-pass, FP32) -> bf16 A operand
 //   MLP         four 128-column hidden chunks: FC1 into two TMEM buffers,
@@ -23,12 +25,14 @@
 //   barrier     the latent's CTAs meet at a counter in global memory (bounded
 //               spin), then read their neighbours' K/V for the next block
 //
-// Roles (320 threads): warps 0-7 compute (attention, epilogues, LayerNorm),
+// Roles (352 threads): warps 0-7 compute (attention, epilogues, LayerNorm),
 // warp 8 one thread issuing the tcgen05 MMAs, warp 9 one thread streaming the
-// block's weights (12 pre-swizzled 32 KB chunks per block, one bulk copy
-// each) through a two-slot ring. Latents are independent: each has its own
-// schedule (six-hour blocks, then one-hour blocks) and its own barrier, so
-// latents with different lead times share the launch.
+// block's weights (12 pre-swizzled 32 KB chunks per block, one bulk copy each,
+// through a three-slot ring) and its biases and LayerNorm vectors (one bulk
+// copy into a two-slot buffer), warp 10 one thread issuing the K/V tensor
+// copies. Latents are independent: each has its own schedule (six-hour
+// blocks, then one-hour blocks) and its own barrier, so latents with
+// different lead times share the launch.
 //
 // Every mbarrier wait and the latent barrier are bounded in time; on a
 // timeout the CTA records WM_ERR_TIMEOUT, the compute warps leave together
@@ -48,23 +52,31 @@ constexpr int C = 128, DH = 32, QKV = 3 * C;
 constexpr int TH = 8, TW = 16;                 // query patch of one CTA
 constexpr int SW = TW + 4;                     // slab columns: the patch's longitudes + 2 on each side
 constexpr int SR_MAX = TH + 4;                 // slab rows (latitude windows of at most 5)
-constexpr int THREADS = 320, MMA_WARP = 8, LOAD_WARP = 9;
+constexpr int THREADS = 352, MMA_WARP = 8, LOAD_WARP = 9, KV_WARP = 10;
 constexpr int CHUNK = 128 * 128 * 2;           // 128 x 128 bf16 operand: two 64-column 128B-swizzled slices
 constexpr int SLICE = CHUNK / 2;
-constexpr int OFF_X = 0;                       // fp32 residual rows [128][128], 16-byte units swizzled
-constexpr int OFF_A = 128 * C * 4;             // A operand: LN1(x), O or LN2(x)
-constexpr int OFF_W = OFF_A + CHUNK;           // weight ring, 2 slots
-constexpr int OFF_H = OFF_W + 2 * CHUNK;       // GELU chunks, 2 slots; the attention's K/V stages alias it
-constexpr int SMEM_USED = OFF_H + 2 * CHUNK;
+constexpr int NSLOT = 3;                       // weight ring slots
+constexpr int VEC_FLOATS = 1664;               // a block's vectors (layout below)
+constexpr int VEC_BYTES = VEC_FLOATS * 4;
+constexpr int OFF_A = 0;                       // A operand: LN1(x), O or LN2(x)
+constexpr int OFF_W = OFF_A + CHUNK;           // weight ring
+constexpr int OFF_H = OFF_W + NSLOT * CHUNK;   // GELU chunks, 2 slots; the attention's K/V stages alias it
+constexpr int OFF_VEC = OFF_H + 2 * CHUNK;     // vectors of two blocks
+constexpr int SMEM_USED = OFF_VEC + 2 * VEC_BYTES;
 constexpr int SMEM = SMEM_USED + 1024;         // + alignment slack
 constexpr int KV_SLAB = SR_MAX * SW * DH * 2;  // one head's K (or V) rows of a key level
 constexpr int KV_STAGE = 2 * KV_SLAB;
 constexpr int OFF_RED = OFF_H + 2 * KV_STAGE;  // LayerNorm row partials [2 passes][2 halves][128]
-static_assert(OFF_RED + 4 * 128 * 4 <= SMEM_USED, "LayerNorm exchange must fit in the GELU region");
-constexpr uint32_t T_ACC1 = 0;                 // FC1 accumulators at 0 and 128; QKV chunks at 0, 128, 256
-constexpr uint32_t T_ACC2 = 256, T_PROJ = 384;
-// weight chunks of a block, in this order in memory
-constexpr int W_QKV = 0, W_O = 3, W_1 = 4, W_2 = 8;
+static_assert(OFF_RED + 4 * 128 * 4 <= OFF_H + 2 * CHUNK, "LayerNorm exchange must fit in the GELU region");
+static_assert(OFF_H % 1024 == 0 && KV_SLAB % 512 == 0, "swizzled operands need aligned bases");
+// TMEM columns: FC1 accumulators (and the projection's) at 0 and 128, FC2's at
+// 256; QKV chunks at 0, 128, 256; the fp32 residual rows at 384
+constexpr uint32_t T_ACC1 = 0, T_PROJ = 0, T_ACC2 = 256, T_X = 384;
+// weight chunks of a block, in this order in memory, then the vectors
+constexpr int W_QKV = 0, W_O = 3, W_1 = 4, W_2 = 8, W_VEC = 12;
+// offsets of the vectors in floats
+constexpr int V_BQKV = 0, V_BO = 384, V_LN1G = 512, V_LN1B = 640, V_LN2G = 768, V_LN2B = 896, V_B1 = 1024,
+              V_B2 = 1536;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -82,12 +94,15 @@ __device__ __forceinline__ bool bar_compute_or(bool p) {
   return r != 0;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// One box of a 4D tensor map (coordinates innermost first) into shared memory, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+      "%6}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
@@ -120,31 +135,35 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// 32 consecutive TMEM columns of this warp's 32 lanes (one row per thread); the caller waits (tmem_wait_st)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]),
+      "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]),
+      "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
+      : "memory");
+}
 
 // byte offset of bf16 element (r, c) of a 128 x 128 operand (two 128B-swizzled 64-column slices)
 __device__ __forceinline__ uint32_t op_off(int r, int c) {
   return (uint32_t)((c >> 6) * SLICE + r * 128 + ((((c & 63) >> 3) ^ (r & 7)) << 4) + (c & 7) * 2);
 }
-// byte offset of fp32 16-byte unit u (columns 4u .. 4u + 3) of residual row r
-__device__ __forceinline__ uint32_t x_off(int r, int u) { return (uint32_t)(OFF_X + r * 512 + ((u ^ (r & 7)) << 4)); }
 
 // Block i of latent g: six-hour blocks first, then one-hour blocks.
-__device__ __forceinline__ const Blk* block_of(const RolloutSmallArgs& a, int g, int i) {
+__device__ __forceinline__ const bf16* block_weights(const RolloutSmallArgs& a, int g, int i) {
   const int p6 = a.n6[g] * a.L6;
-  return i < p6 ? a.blk + (i % a.L6) : a.blk + a.L6 + (i - p6) % a.L1;
+  return (i < p6 ? a.blk[i % a.L6] : a.blk[a.L6 + (i - p6) % a.L1]).w;
 }
-
-// A block's vector as float4s. Each phase reads the pointers it needs into
-// registers before its first global store (the stores would otherwise make
-// the compiler re-read the table after each one).
-__device__ __forceinline__ const float4* f4(const float* p) { return reinterpret_cast<const float4*>(p); }
 
 // LayerNorm of the thread's 64 columns (half hf of row r) with the partner
 // half's partial sums exchanged through shared memory (two passes: mean, then
-// the mean squared deviation), affine, rounded to bf16 into the A operand.
+// the mean squared deviation), affine (gamma, beta: shared-memory vectors),
+// rounded to bf16 into the A operand.
 __device__ __forceinline__ void layernorm_to_a(uint8_t* smem, const float (&v)[64], int r, int hf,
-                                               const float4* __restrict__ gamma, const float4* __restrict__ beta,
-                                               float eps) {
+                                               const float4* gamma, const float4* beta, float eps) {
   float* red = reinterpret_cast<float*>(smem + OFF_RED);
   float s = 0.f;
 #pragma unroll
@@ -165,8 +184,8 @@ __device__ __forceinline__ void layernorm_to_a(uint8_t* smem, const float (&v)[6
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int j = 8 * k, c4 = (64 * hf + j) >> 2;
-    const float4 g0 = __ldg(gamma + c4), g1 = __ldg(gamma + c4 + 1);
-    const float4 b0 = __ldg(beta + c4), b1 = __ldg(beta + c4 + 1);
+    const float4 g0 = gamma[c4], g1 = gamma[c4 + 1];
+    const float4 b0 = beta[c4], b1 = beta[c4 + 1];
     const uint32_t w0 = pack_bf16((v[j] - mean) * rstd * g0.x + b0.x, (v[j + 1] - mean) * rstd * g0.y + b0.y);
     const uint32_t w1 = pack_bf16((v[j + 2] - mean) * rstd * g0.z + b0.z, (v[j + 3] - mean) * rstd * g0.w + b0.w);
     const uint32_t w2 = pack_bf16((v[j + 4] - mean) * rstd * g1.x + b1.x, (v[j + 5] - mean) * rstd * g1.y + b1.y);
@@ -175,25 +194,29 @@ __device__ __forceinline__ void layernorm_to_a(uint8_t* smem, const float (&v)[6
   }
 }
 
-// x[r, 64 hf + 32 sub ..] += acc + bias for 32 columns; the new values into v[32 sub ..]
-__device__ __forceinline__ void residual_add32(uint8_t* smem, int r, int hf, int sub, const float (&acc)[32],
-                                               const float4* __restrict__ bias, float (&v)[64]) {
+// x += acc + bias over the thread's 64 columns (TMEM accumulator at acc_col,
+// residual rows at T_X); the new values also into v.
+__device__ __forceinline__ void residual_add(uint32_t tmem, uint32_t lane_off, uint32_t acc_col, int hf,
+                                             const float4* bias, float (&v)[64]) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int u = 16 * hf + 8 * sub + q;
-    float4* p = reinterpret_cast<float4*>(smem + x_off(r, u));
-    float4 x = *p;
-    const float4 b = __ldg(bias + u);
-    x.x += acc[4 * q] + b.x;
-    x.y += acc[4 * q + 1] + b.y;
-    x.z += acc[4 * q + 2] + b.z;
-    x.w += acc[4 * q + 3] + b.w;
-    *p = x;
-    v[32 * sub + 4 * q] = x.x;
-    v[32 * sub + 4 * q + 1] = x.y;
-    v[32 * sub + 4 * q + 2] = x.z;
-    v[32 * sub + 4 * q + 3] = x.w;
+  for (int sub = 0; sub < 2; ++sub) {
+    const uint32_t col = (uint32_t)(64 * hf + 32 * sub);
+    float acc[32], x[32];
+    tmem_ld32(tmem + acc_col + col + lane_off, acc);
+    tmem_ld32(tmem + T_X + col + lane_off, x);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 b = bias[(col >> 2) + q];
+      x[4 * q] += acc[4 * q] + b.x;
+      x[4 * q + 1] += acc[4 * q + 1] + b.y;
+      x[4 * q + 2] += acc[4 * q + 2] + b.z;
+      x[4 * q + 3] += acc[4 * q + 3] + b.w;
+    }
+    tmem_st32(tmem + T_X + col + lane_off, x);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[32 * sub + j] = x[j];
   }
+  tmem_wait_st();
 }
 
 // Bounded wait (all lanes of the warp take the result of lane 0's view).
@@ -230,8 +253,9 @@ __device__ __forceinline__ bool latent_barrier(unsigned int* counter, unsigned i
 
 __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_constant__ RolloutSmallArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t w_full[2], w_empty[2], a_full, mma_done, drain_bar;
-  __shared__ __align__(8) uint64_t acc1_full[2], acc1_empty[2], h_full[2], h_empty[2];
+  __shared__ __align__(8) uint64_t w_full[NSLOT], w_empty[NSLOT], vec_full[2], vec_empty[2];
+  __shared__ __align__(8) uint64_t a_full, mma_done, drain_bar, qkv_ready;
+  __shared__ __align__(8) uint64_t acc1_full[2], acc1_empty[2], h_full[2], h_empty[2], kv_full[2], kv_empty[2];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
@@ -240,19 +264,40 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = blockIdx.x / a.T, tile = blockIdx.x % a.T;
   const int nb = a.n6[g] * a.L6 + a.n1[g] * a.L1;   // blocks of this latent's rollout (>= 1)
+  const int steps = 4 * a.kd;                         // attention steps per block: (head, key level)
+
+  // the patch: level d, latitudes h0 .. h0 + 7, longitudes w0 .. w0 + 15; its
+  // key levels kd0 .. kd0 + kd - 1 and slab latitudes S0 .. S0 + SR - 1
+  const int tpr = a.W / TW, tpl = (a.H / TH) * tpr;
+  const int d = tile / tpl, h0 = ((tile % tpl) / tpr) * TH, w0 = (tile % tpr) * TW;
+  const int rh = a.kh / 2;
+  const int S0 = clampi(h0 - rh, 0, a.H - a.kh);
+  const int SR = clampi(h0 + TH - 1 - rh, 0, a.H - a.kh) + a.kh - S0;
+  const int kd0 = clampi(d - a.kd / 2, 0, a.D - a.kd);
+  // K/V slab layout: 12 latitude rows x 20 longitudes of 64-byte key rows, one
+  // box; where the patch's longitude halo wraps (w0 = 0 or W - 16), two boxes
+  // side by side: columns 0-1 then 2-19, or 0-17 then 18-19
+  const int wrap = w0 == 0 ? -1 : (w0 + TW + 2 > a.W ? 1 : 0);
 
   if (threadIdx.x == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NSLOT; ++b) {
       mbar_init(&w_full[b], 1);
       mbar_init(&w_empty[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&vec_full[b], 1);
+      mbar_init(&vec_empty[b], 8);
       mbar_init(&acc1_full[b], 1);
       mbar_init(&acc1_empty[b], 8);
       mbar_init(&h_full[b], 8);
       mbar_init(&h_empty[b], 1);
+      mbar_init(&kv_full[b], 1);
+      mbar_init(&kv_empty[b], 8);
     }
     mbar_init(&a_full, 8);
     mbar_init(&mma_done, 1);
     mbar_init(&drain_bar, 1);
+    mbar_init(&qkv_ready, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -269,28 +314,42 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
 
   if (warp == LOAD_WARP) {
     if (lane == 0) {
-      // ------------------------------------------------------ weight stream
-      int seq = 0;
-      int last[2] = {-1, -1};   // parity of each slot's last copy (for the drain after a timeout)
+      // ---------------------------------------------- weights and vectors
+      int slot = 0, par = 0;                // ring position and its use parity
+      int last[NSLOT], last_vec[2] = {-1, -1};
+      for (int b = 0; b < NSLOT; ++b) last[b] = -1;
       bool ok = true;
       auto load = [&](const bf16* src) -> bool {
-        const int slot = seq & 1;
-        const uint32_t use = (uint32_t)(seq >> 1);
-        if (!mbar_wait(&w_empty[slot], (use & 1u) ^ 1u, &abort_flag)) return false;
+        if (!mbar_wait(&w_empty[slot], (uint32_t)par ^ 1u, &abort_flag)) return false;
         mbar_expect_tx(&w_full[slot], CHUNK);
         bulk_g2s(sbase + OFF_W + slot * CHUNK, src, CHUNK, &w_full[slot]);
-        last[slot] = (int)(use & 1u);
-        ++seq;
+        last[slot] = par;
+        if (++slot == NSLOT) {
+          slot = 0;
+          par ^= 1;
+        }
+        return true;
+      };
+      auto load_vec = [&](int j, const bf16* w) -> bool {
+        const int b = j & 1;
+        const uint32_t use = (uint32_t)(j >> 1) & 1u;
+        if (!mbar_wait(&vec_empty[b], use ^ 1u, &abort_flag)) return false;
+        mbar_expect_tx(&vec_full[b], VEC_BYTES);
+        bulk_g2s(sbase + OFF_VEC + b * VEC_BYTES, w + (size_t)W_VEC * (CHUNK / 2), VEC_BYTES, &vec_full[b]);
+        last_vec[b] = (int)use;
         return true;
       };
       constexpr int kOrder[9] = {W_O, W_1 + 0, W_1 + 1, W_2 + 0, W_1 + 2, W_2 + 1, W_1 + 3, W_2 + 2, W_2 + 3};
-      const bf16* w0 = block_of(a, g, 0)->w;
-      for (int c = 0; c < 3 && ok; ++c) ok = load(w0 + (size_t)(W_QKV + c) * (CHUNK / 2));
+      const bf16* w0p = block_weights(a, g, 0);
+      ok = load_vec(0, w0p);
+      for (int c = 0; c < 3 && ok; ++c) ok = load(w0p + (size_t)(W_QKV + c) * (CHUNK / 2));
       for (int i = 0; i < nb && ok; ++i) {
-        const bf16* w = block_of(a, g, i)->w;
+        const bf16* w = block_weights(a, g, i);
+#pragma unroll 1
         for (int q = 0; q < 9 && ok; ++q) ok = load(w + (size_t)kOrder[q] * (CHUNK / 2));
-        if (i + 1 < nb) {
-          const bf16* wn = block_of(a, g, i + 1)->w;
+        if (ok && i + 1 < nb) {
+          const bf16* wn = block_weights(a, g, i + 1);
+          ok = load_vec(i + 1, wn);
           for (int c = 0; c < 3 && ok; ++c) ok = load(wn + (size_t)(W_QKV + c) * (CHUNK / 2));
         }
       }
@@ -298,20 +357,74 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
         abort_flag = 1;
         atomicExch(a.status, (int)WM_ERR_TIMEOUT);
         volatile int never = 0;
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < NSLOT; ++b)
           if (last[b] >= 0) mbar_wait(&w_full[b], (uint32_t)last[b], &never);
+        for (int b = 0; b < 2; ++b)
+          if (last_vec[b] >= 0) mbar_wait(&vec_full[b], (uint32_t)last_vec[b], &never);
+      }
+    }
+  } else if (warp == KV_WARP) {
+    if (lane == 0) {
+      // ------------------------------------------------- K/V tensor copies
+      for (int k = 0; k < 3; ++k) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&a.tm_kv[k]) : "memory");
+      // boxes of 12 latitudes from S0 (rows past H read as zeros, rows past SR
+      // are not used) x 20 longitudes, K and V
+      const uint32_t kv_bytes = (uint32_t)(SR_MAX * SW * 64 * 2);
+      int kvs = 0, last[2] = {-1, -1};
+      bool ok = true;
+      for (int i = 0; i < nb && ok; ++i) {
+        // the latent's q, k, v of block i are complete
+        if (!mbar_wait(&qkv_ready, (uint32_t)i & 1u, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        // the q, k, v rows were written by generic stores (this and other CTAs);
+        // the tensor copies below read them through the async proxy
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        for (int s = 0; s < steps; ++s, ++kvs) {
+          const int b = kvs & 1;
+          const uint32_t use = (uint32_t)(kvs >> 1) & 1u;
+          if (!mbar_wait(&kv_empty[b], use ^ 1u, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          const int h = s / a.kd, lev = ((i & 1) * a.G + g) * a.D + kd0 + s % a.kd;
+          mbar_expect_tx(&kv_full[b], kv_bytes);
+          const uint32_t dst0 = sbase + OFF_H + b * KV_STAGE;
+#pragma unroll
+          for (int kv = 0; kv < 2; ++kv) {
+            const int ch = C + kv * C + h * DH;
+            const uint32_t dst = dst0 + kv * KV_SLAB;
+            if (wrap == 0) {
+              tma_load_4d(dst, &a.tm_kv[0], &kv_full[b], ch, w0 - 2, S0, lev);
+            } else if (wrap < 0) {
+              tma_load_4d(dst, &a.tm_kv[2], &kv_full[b], ch, a.W - 2, S0, lev);
+              tma_load_4d(dst + SR_MAX * 2 * 64, &a.tm_kv[1], &kv_full[b], ch, 0, S0, lev);
+            } else {
+              tma_load_4d(dst, &a.tm_kv[1], &kv_full[b], ch, a.W - 18, S0, lev);
+              tma_load_4d(dst + SR_MAX * 18 * 64, &a.tm_kv[2], &kv_full[b], ch, 0, S0, lev);
+            }
+          }
+          last[b] = (int)use;
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(a.status, (int)WM_ERR_TIMEOUT);
+        volatile int never = 0;
+        for (int b = 0; b < 2; ++b)
+          if (last[b] >= 0) mbar_wait(&kv_full[b], (uint32_t)last[b], &never);
       }
     }
   } else if (warp == MMA_WARP) {
     if (lane == 0) {
       // ------------------------------------------------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(128, 128);
-      int seq = 0, a_cnt = 0;
+      int slot = 0, par = 0, a_cnt = 0;
       bool ok = true;
       // one 128 x 128 x 128 product: A operand at a_addr, the next weight chunk of the ring
       auto gemm = [&](uint32_t col, uint32_t a_addr, bool acc_in) -> bool {
-        const int slot = seq & 1;
-        if (!mbar_wait(&w_full[slot], (uint32_t)(seq >> 1) & 1u, &abort_flag)) return false;
+        if (!mbar_wait(&w_full[slot], (uint32_t)par, &abort_flag)) return false;
         tc_fence_after();
         const uint32_t b_addr = sbase + OFF_W + slot * CHUNK;
 #pragma unroll
@@ -323,7 +436,10 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
                              (acc_in || s || k) ? 1u : 0u);
         }
         umma_commit(&w_empty[slot]);
-        ++seq;
+        if (++slot == NSLOT) {
+          slot = 0;
+          par ^= 1;
+        }
         return true;
       };
       auto wait_a = [&]() -> bool {
@@ -374,92 +490,93 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
       volatile int never = 0;
       mbar_wait(&drain_bar, 0u, &never);
     }
-  } else {
+  } else if (warp < 8) {
     // ------------------------------------------------------ compute warps
     const int r = 32 * (warp & 3) + lane, hf = warp >> 2;   // epilogue row and column half
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
-    const int tpr = a.W / TW, tpl = (a.H / TH) * tpr;
-    const int d = tile / tpl, h0 = ((tile % tpl) / tpr) * TH, w0 = (tile % tpr) * TW;
     const long N = (long)a.D * a.H * a.W;
-    const long tok_r = ((long)d * a.H + h0 + (r >> 4)) * a.W + w0 + (r & 15);
-    float* xg = a.x[g] + tok_r * C + 64 * hf;
+    const int tok_r = (d * a.H + h0 + (r >> 4)) * a.W + w0 + (r & 15);
+    float* xg = a.x[g] + (long)tok_r * C + 64 * hf;
     int md = 0;          // mma_done completions waited for
     bool ok = true;
     float v[64];
 
     // attention geometry of this warp: a 4 x 4 query group (rows g8, g8 + 8 of the m16 tile)
     const int gr = warp >> 2, gc = warp & 3, g8 = lane >> 2, t4 = lane & 3;
-    const int rh = a.kh / 2, rw = a.kw / 2;
-    const int S0 = clampi(h0 - rh, 0, a.H - a.kh);
-    const int SR = clampi(h0 + TH - 1 - rh, 0, a.H - a.kh) + a.kh - S0;
+    const int rw = a.kw / 2;
     const int R0 = min(clampi(h0 + 4 * gr - rh, 0, a.H - a.kh) - S0, SR - 8);
     const int qh0 = h0 + 4 * gr + (g8 >> 2), qh1 = qh0 + 2, qcl = g8 & 3;
     const uint32_t kmask = (1u << a.kh) - 1u;
     const uint32_t lat0 = kmask << (clampi(qh0 - rh, 0, a.H - a.kh) - S0 - R0);
     const uint32_t lat1 = kmask << (clampi(qh1 - rh, 0, a.H - a.kh) - S0 - R0);
     const bool lon0 = abs(2 * t4 - 2 - qcl) <= rw, lon1 = abs(2 * t4 + 1 - 2 - qcl) <= rw;
-    const int kd0 = clampi(d - a.kd / 2, 0, a.D - a.kd);
     const int tq0 = (d * a.H + qh0) * a.W + w0 + 4 * gc + qcl, tq1 = tq0 + 2 * a.W;
     const int ri0 = (4 * gr + (g8 >> 2)) * TW + 4 * gc + qcl, ri1 = ri0 + 2 * TW;
-    // ldmatrix row offsets within a stage (bytes): K rows per n8 block, V rows per (k16 step, matrix)
+    // byte offset in a K (or V) slab of 16-byte unit u of the key at slab row
+    // lr, column c; the 64-byte swizzle of the tensor copies moves unit u of
+    // the row at offset o to u ^ ((o >> 7) & 3)
+    auto kv_off = [&](int lr, int c, int u) -> uint32_t {
+      int o;
+      if (wrap == 0) o = (lr * SW + c) * 64;
+      else if (wrap < 0) o = c < 2 ? (lr * 2 + c) * 64 : SR_MAX * 2 * 64 + (lr * 18 + c - 2) * 64;
+      else o = c < 18 ? (lr * 18 + c) * 64 : SR_MAX * 18 * 64 + (lr * 2 + c - 18) * 64;
+      o += u * 16;
+      return (uint32_t)(o ^ (((o >> 7) & 3) << 4));
+    };
+    // ldmatrix row addresses: K rows per n8 block, V rows per (k16 step, matrix pair)
     uint32_t koff[8], voff[4][2];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int key = (R0 + b) * SW + 4 * gc + (lane & 7), u = lane >> 3;
-      koff[b] = (uint32_t)(key * 64 + ((u ^ ((key >> 1) & 3)) << 4));
-    }
+    for (int b = 0; b < 8; ++b) koff[b] = kv_off(R0 + b, 4 * gc + (lane & 7), lane >> 3);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int np = 0; np < 2; ++np) {
         const int mi = lane >> 3;
-        const int key = (R0 + 2 * q + (mi & 1)) * SW + 4 * gc + (lane & 7), u = 2 * np + (mi >> 1);
-        voff[q][np] = (uint32_t)(KV_SLAB + key * 64 + ((u ^ ((key >> 1) & 3)) << 4));
+        voff[q][np] = KV_SLAB + kv_off(R0 + 2 * q + (mi & 1), 4 * gc + (lane & 7), 2 * np + (mi >> 1));
       }
+    int kv_step = 0;   // K/V stages waited for so far
 
-    // K/V staging: this thread's fixed items (slab key k, K or V, 16-byte unit
-    // u); per step only the key level and the head move the source
-    // (item it = thread + 256 m: key k0 + 32 m, the same K/V and unit; the
-    // swizzle term (k >> 1) & 3 does not change with m)
-    const int items = SR * SW * 8;
-    int soff[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int it = threadIdx.x + 256 * m;
-      const int k = it >> 3, kv = (it >> 2) & 1, u = it & 3;
-      int lon = w0 - 2 + k % SW;
-      lon += lon < 0 ? a.W : 0;
-      lon -= lon >= a.W ? a.W : 0;
-      soff[m] = it < items ? ((S0 + k / SW) * a.W + lon) * QKV + C + kv * C + 8 * u : 0;
-    }
-    const int k0 = threadIdx.x >> 3, u0 = threadIdx.x & 3;
-    const uint32_t doff0 =
-        (uint32_t)(((threadIdx.x >> 2) & 1) * KV_SLAB + k0 * 64 + ((u0 ^ ((k0 >> 1) & 3)) << 4));
-    const long level_elems = (long)a.H * a.W * QKV;
-
-    // QKV epilogue: + bias, bf16 rows to the global qkv array of block buffer `buf`
-    auto qkv_epilogue = [&](const float4* __restrict__ bqkv, int buf) {
+    auto vec = [&](int j) -> const float4* { return reinterpret_cast<const float4*>(smem + OFF_VEC + (j & 1) * VEC_BYTES); };
+    // QKV epilogue: + bias, bf16. The 128 x 384 tile is staged in shared memory
+    // (chunk 0 in the A operand, chunks 1 and 2 in the GELU region, all free
+    // once the QKV MMAs are done) in the operand layout, then written to the
+    // global qkv array of block buffer `buf` in whole rows: the patch's 16
+    // tokens of a latitude are 12 KB of consecutive memory.
+    auto qkv_epilogue = [&](const float4* vb, int buf) {
       ok = warp_wait(&mma_done, (uint32_t)(md++) & 1u, &abort_flag) && ok;
       if (!ok) abort_flag = 1;
       tc_fence_after();
-      bf16* dst = a.qkv + (((long)buf * a.G + g) * N + tok_r) * QKV;
+      const float4* bq = vb + V_BQKV / 4;
 #pragma unroll 1
-      for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c) {
+        uint8_t* stg = smem + (c == 0 ? OFF_A : OFF_H + (c - 1) * CHUNK) + hf * SLICE + r * 128;
 #pragma unroll 1
         for (int sub = 0; sub < 2; ++sub) {
           const int col = 128 * c + 64 * hf + 32 * sub;
           float acc[32];
           tmem_ld32(tmem + T_ACC1 + (uint32_t)col + lane_off, acc);
-          uint4* o = reinterpret_cast<uint4*>(dst + col);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const float4 b0 = __ldg(bqkv + (col >> 2) + 2 * k), b1 = __ldg(bqkv + (col >> 2) + 2 * k + 1);
+            const float4 b0 = bq[(col >> 2) + 2 * k], b1 = bq[(col >> 2) + 2 * k + 1];
             const int j = 8 * k;
-            o[k] = make_uint4(pack_bf16(acc[j] + b0.x, acc[j + 1] + b0.y), pack_bf16(acc[j + 2] + b0.z, acc[j + 3] + b0.w),
-                              pack_bf16(acc[j + 4] + b1.x, acc[j + 5] + b1.y), pack_bf16(acc[j + 6] + b1.z, acc[j + 7] + b1.w));
+            *reinterpret_cast<uint4*>(stg + (((4 * sub + k) ^ (r & 7)) << 4)) =
+                make_uint4(pack_bf16(acc[j] + b0.x, acc[j + 1] + b0.y), pack_bf16(acc[j + 2] + b0.z, acc[j + 3] + b0.w),
+                           pack_bf16(acc[j + 4] + b1.x, acc[j + 5] + b1.y), pack_bf16(acc[j + 6] + b1.z, acc[j + 7] + b1.w));
           }
         }
+      }
       tc_fence_before();
+      bar_compute();
+      // 16-byte piece p (0 .. 47) of tile row rr, consecutive threads along a row
+      bf16* dst = a.qkv + ((long)buf * a.G + g) * N * QKV;
+#pragma unroll 4
+      for (int it = threadIdx.x; it < 128 * 48; it += 256) {
+        const int rr = it / 48, p = it - rr * 48;
+        const int c = p >> 4, sl = (p >> 3) & 1, u = p & 7;
+        const uint8_t* src = smem + (c == 0 ? OFF_A : OFF_H + (c - 1) * CHUNK) + sl * SLICE + rr * 128 + ((u ^ (rr & 7)) << 4);
+        const int tok = (d * a.H + h0 + (rr >> 4)) * a.W + w0 + (rr & 15);
+        *reinterpret_cast<uint4*>(dst + (long)tok * QKV + 8 * p) = *reinterpret_cast<const uint4*>(src);
+      }
     };
     auto a_ready = [&]() {
       fence_async_smem();   // generic-proxy stores, read by the tensor core next
@@ -467,44 +584,43 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
       if (lane == 0) mbar_arrive(&a_full);
     };
 
-    // ---- prologue: residual rows in, LayerNorm 1 of block 0, QKV, latent barrier
+    // ---- prologue: residual rows into TMEM, LayerNorm 1 of block 0, QKV, latent barrier
     {
       const float4* src = reinterpret_cast<const float4*>(xg);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const float4 x = src[q];
-        *reinterpret_cast<float4*>(smem + x_off(r, 16 * hf + q)) = x;
         v[4 * q] = x.x;
         v[4 * q + 1] = x.y;
         v[4 * q + 2] = x.z;
         v[4 * q + 3] = x.w;
       }
-      const Blk* b0 = block_of(a, g, 0);
-      layernorm_to_a(smem, v, r, hf, f4(b0->ln1_g), f4(b0->ln1_b), a.eps);
+#pragma unroll
+      for (int sub = 0; sub < 2; ++sub) {
+        float t[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) t[j] = v[32 * sub + j];
+        tmem_st32(tmem + T_X + (uint32_t)(64 * hf + 32 * sub) + lane_off, t);
+      }
+      tmem_wait_st();
+      ok = warp_wait(&vec_full[0], 0u, &abort_flag) && ok;
+      layernorm_to_a(smem, v, r, hf, vec(0) + V_LN1G / 4, vec(0) + V_LN1B / 4, a.eps);
       a_ready();
-      qkv_epilogue(f4(b0->bqkv), 0);
+      qkv_epilogue(vec(0), 0);
     }
     unsigned int epoch = 0;
     bool run = latent_barrier(a.bar + g, (++epoch) * (unsigned)a.T, warp, lane, &abort_flag) && !bar_compute_or(!ok);
+    if (run && threadIdx.x == 0) mbar_arrive(&qkv_ready);
 
     for (int i = 0; i < nb && run; ++i) {
-      const Blk* bk = block_of(a, g, i);
+      const float4* vb = vec(i);
       const bf16* qkv_cur = a.qkv + ((long)(i & 1) * a.G + g) * N * QKV;
       // ------------------------------------------------ neighborhood attention
       {
-        const int steps = 4 * a.kd;
-        auto stage = [&](int s) {
-          const bf16* base = qkv_cur + (kd0 + s % a.kd) * level_elems + (s / a.kd) * DH;
-          const uint32_t dst0 = sbase + OFF_H + (s & 1) * KV_STAGE;
-#pragma unroll
-          for (int m = 0; m < 8; ++m)
-            if ((int)threadIdx.x + 256 * m < items) cp_async16(dst0 + doff0 + 2048u * m, base + soff[m]);
-          cp_async_commit();
-        };
         // this lane's query rows of head h (A fragments of the two k16 steps)
         auto load_q = [&](int h, uint32_t (&q)[2][4]) {
-          const bf16* q0 = qkv_cur + tq0 * QKV + h * DH + 2 * t4;
-          const bf16* q1 = qkv_cur + tq1 * QKV + h * DH + 2 * t4;
+          const bf16* q0 = qkv_cur + (long)tq0 * QKV + h * DH + 2 * t4;
+          const bf16* q1 = qkv_cur + (long)tq1 * QKV + h * DH + 2 * t4;
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
             q[kk][0] = __ldcg(reinterpret_cast<const unsigned int*>(q0 + 16 * kk));
@@ -513,17 +629,15 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
             q[kk][3] = __ldcg(reinterpret_cast<const unsigned int*>(q1 + 16 * kk + 8));
           }
         };
-        stage(0);
         float o[4][4], l0 = 0.f, l1 = 0.f, m0 = -INFINITY, m1 = -INFINITY;
         uint32_t qa[2][4], qn[2][4];
         load_q(0, qn);
 #pragma unroll 1
         for (int s = 0; s < steps; ++s) {
           const int h = s / a.kd, lv = s % a.kd;
-          if (s + 1 < steps) stage(s + 1);
-          else cp_async_commit();
-          cp_async_wait1();
-          bar_compute();
+          ok = warp_wait(&kv_full[s & 1], (uint32_t)(kv_step >> 1) & 1u, &abort_flag) && ok;
+          ++kv_step;
+          if (!ok) abort_flag = 1;
           if (lv == 0) {
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk)
@@ -595,6 +709,9 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
               mma16816(o[2 * np], pa[q], v0, v1);
               mma16816(o[2 * np + 1], pa[q], v2, v3);
             }
+          // this warp is done with the stage
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&kv_empty[s & 1]);
           if (lv == a.kd - 1) {
             // head done: normalise, bf16 into the A operand (columns 32 h ..)
             float s0 = l0, s1 = l1;
@@ -610,31 +727,18 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
               *reinterpret_cast<uint32_t*>(smem + OFF_A + op_off(ri1, ch)) = pack_bf16(o[nb8][2] * i1, o[nb8][3] * i1);
             }
           }
-          bar_compute();   // the stage may be refilled
         }
-        cp_async_wait0();
       }
       a_ready();
       // ------------------------------------------------ output projection + residual, LayerNorm 2
       ok = warp_wait(&mma_done, (uint32_t)(md++) & 1u, &abort_flag) && ok;
       if (!ok) abort_flag = 1;
       tc_fence_after();
-      {
-        const float4* bo = f4(bk->bo);
-        const float4* g2 = f4(bk->ln2_g);
-        const float4* be2 = f4(bk->ln2_b);
-#pragma unroll
-        for (int sub = 0; sub < 2; ++sub) {
-          float acc[32];
-          tmem_ld32(tmem + T_PROJ + (uint32_t)(64 * hf + 32 * sub) + lane_off, acc);
-          residual_add32(smem, r, hf, sub, acc, bo, v);
-        }
-        tc_fence_before();
-        layernorm_to_a(smem, v, r, hf, g2, be2, a.eps);
-      }
+      residual_add(tmem, lane_off, T_PROJ, hf, vb + V_BO / 4, v);
+      tc_fence_before();
+      layernorm_to_a(smem, v, r, hf, vb + V_LN2G / 4, vb + V_LN2B / 4, a.eps);
       a_ready();
       // ------------------------------------------------ MLP: FC1 chunks -> GELU -> shared memory
-      const float4* b1v = f4(bk->b1);
 #pragma unroll 1
       for (int j = 0; j < 4; ++j) {
         const int b = j & 1;
@@ -652,14 +756,14 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc1_empty[b]);
           }
-          const float4* b1 = b1v + ((128 * j + c) >> 2);
+          const float4* b1 = vb + (V_B1 + 128 * j + c) / 4;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const float4 b = __ldg(b1 + q);
-            acc[4 * q] += b.x;
-            acc[4 * q + 1] += b.y;
-            acc[4 * q + 2] += b.z;
-            acc[4 * q + 3] += b.w;
+            const float4 bb = b1[q];
+            acc[4 * q] += bb.x;
+            acc[4 * q + 1] += bb.y;
+            acc[4 * q + 2] += bb.z;
+            acc[4 * q + 3] += bb.w;
           }
 #pragma unroll
           for (int jj = 0; jj < 32; jj += 2) gelu_erf2(acc[jj], acc[jj + 1]);
@@ -684,25 +788,22 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
       ok = warp_wait(&mma_done, (uint32_t)(md++) & 1u, &abort_flag) && ok;
       if (!ok) abort_flag = 1;
       tc_fence_after();
-      {
-        const float4* b2 = f4(bk->b2);
-#pragma unroll
-        for (int sub = 0; sub < 2; ++sub) {
-          float acc[32];
-          tmem_ld32(tmem + T_ACC2 + (uint32_t)(64 * hf + 32 * sub) + lane_off, acc);
-          residual_add32(smem, r, hf, sub, acc, b2, v);
-        }
-      }
+      residual_add(tmem, lane_off, T_ACC2, hf, vb + V_B2 / 4, v);
       tc_fence_before();
+      // block i's vectors are no longer needed: their slot may take block i + 2's
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&vec_empty[i & 1]);
       if (i + 1 < nb) {
         // ------------------------------------------------ next block: LayerNorm 1, QKV, latent barrier
-        const Blk* bn = block_of(a, g, i + 1);
-        const float4* bq = f4(bn->bqkv);
-        layernorm_to_a(smem, v, r, hf, f4(bn->ln1_g), f4(bn->ln1_b), a.eps);
+        ok = warp_wait(&vec_full[(i + 1) & 1], (uint32_t)((i + 1) >> 1) & 1u, &abort_flag) && ok;
+        if (!ok) abort_flag = 1;
+        const float4* vn = vec(i + 1);
+        layernorm_to_a(smem, v, r, hf, vn + V_LN1G / 4, vn + V_LN1B / 4, a.eps);
         a_ready();
-        qkv_epilogue(bq, (i + 1) & 1);
+        qkv_epilogue(vn, (i + 1) & 1);
         run = latent_barrier(a.bar + g, (++epoch) * (unsigned)a.T, warp, lane, &abort_flag);
         run = !bar_compute_or(!ok) && run;
+        if (run && threadIdx.x == 0) mbar_arrive(&qkv_ready);
       } else {
         run = !bar_compute_or(!ok);
         if (run) {

@@ -221,6 +221,12 @@ bool make_tmap_qkv_slab(CUtensorMap* map, const void* qkv, uint64_t C3, uint64_t
 // TMA descriptor of a row-major bf16 matrix [rows, cols] (cols contiguous),
 // box = box_rows x 64 columns, 128-byte swizzle.
 bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+// bf16 q, k, v viewed as [levels][H][W][C3]: box of 32 channels x box_w
+// longitudes x box_h latitudes x 1 level, 64-byte swizzle (16-byte unit u of
+// a 64-byte row at shared offset o lands at u ^ ((o >> 7) & 3)); rows past H
+// read as zeros.
+bool make_tmap_kv_slab(CUtensorMap* map, const void* qkv, uint64_t C3, uint64_t W, uint64_t H, uint64_t levels,
+                       uint32_t box_w, uint32_t box_h);
 
 // TMA descriptor of the GEMM output [rows, cols] (bf16 or fp32, row major),
 // box 32 x 32, 64-byte (bf16) / 128-byte (fp32) swizzle.
@@ -286,13 +292,16 @@ wm_status launch_mlp_small(const MlpArgs& a, cudaStream_t s);
 // Whole-rollout kernel for latents with C = 128 and 4 heads (k_rollout_small.cu):
 // one cooperative launch runs every block of every latent's greedy schedule.
 constexpr int kRolloutSmallMaxLatents = 8;
+constexpr size_t kRolloutBlockBytes = 12 * 32768 + 1664 * 4;   // one RolloutBlock's weights and vectors
 struct RolloutBlock {
   const __nv_bfloat16* w;   // 12 chunks of 128 x 128 bf16 in the 128B-swizzled K-major
-                            // layout: Wqkv rows 0-127, 128-255, 256-383; Wo; W1 rows
-                            // 0-127 .. 384-511; W2 columns 0-127 .. 384-511
-  const float *ln1_g, *ln1_b, *bqkv, *bo, *ln2_g, *ln2_b, *b1, *b2;
+                            // layout (Wqkv rows 0-127, 128-255, 256-383; Wo; W1 rows
+                            // 0-127 .. 384-511; W2 columns 0-127 .. 384-511), then the
+                            // block's vectors as fp32: bqkv[384] bo ln1_g ln1_b ln2_g
+                            // ln2_b [128 each] b1[512] b2[128]
 };
 struct RolloutSmallArgs {
+  CUtensorMap tm_kv[3];      // make_tmap_kv_slab over qkv ([2 G D][H][W][384]): 20, 18, 2 longitudes x 12 latitudes
   const RolloutBlock* blk;   // device array: the six-hour blocks, then the one-hour blocks
   int L6, L1;                // blocks per processor
   int G, T;                  // latents; CTAs (8 x 16-token patches) per latent
