@@ -12,8 +12,8 @@
 //               group and one head at a time and walks its 8 x 8 key
 //               rectangle per key level (K/V slabs of the patch's halo brought
 //               to shared memory by tensor copies from a producer warp, one
-//               box per slab and two where the longitude wraps, double
-//               buffered), FP32 online softmax; O goes to shared memory as the
+//               box per slab and two where the longitude wraps, three
+//               stages), FP32 online softmax; O goes to shared memory as the
 //               next GEMM's A operand
 //   proj        tcgen05.mma (M = N = 128, K = 128) into TMEM; x += acc + b_o;
 //               LayerNorm 2 of the new rows (two-pass, FP32) -> bf16 A operand
@@ -28,9 +28,9 @@
 // Roles (352 threads): warps 0-7 compute (attention, epilogues, LayerNorm),
 // warp 8 one thread issuing the tcgen05 MMAs, warp 9 one thread streaming the
 // block's weights (12 pre-swizzled 32 KB chunks per block, one bulk copy each,
-// through a three-slot ring) and its biases and LayerNorm vectors (one bulk
+// through a two-slot ring) and its biases and LayerNorm vectors (one bulk
 // copy into a two-slot buffer), warp 10 one thread issuing the K/V tensor
-// copies. Latents are independent: each has its own schedule (six-hour
+// copies into a three-stage ring. Latents are independent: each has its own schedule (six-hour
 // blocks, then one-hour blocks) and its own barrier, so latents with
 // different lead times share the launch.
 //
@@ -55,20 +55,24 @@ constexpr int SR_MAX = TH + 4;                 // slab rows (latitude windows of
 constexpr int THREADS = 352, MMA_WARP = 8, LOAD_WARP = 9, KV_WARP = 10;
 constexpr int CHUNK = 128 * 128 * 2;           // 128 x 128 bf16 operand: two 64-column 128B-swizzled slices
 constexpr int SLICE = CHUNK / 2;
-constexpr int NSLOT = 3;                       // weight ring slots
+constexpr int NSLOT = 2;                       // weight ring slots
+constexpr int NKV = 3;                         // K/V stages
 constexpr int VEC_FLOATS = 1664;               // a block's vectors (layout below)
 constexpr int VEC_BYTES = VEC_FLOATS * 4;
 constexpr int OFF_A = 0;                       // A operand: LN1(x), O or LN2(x)
 constexpr int OFF_W = OFF_A + CHUNK;           // weight ring
 constexpr int OFF_H = OFF_W + NSLOT * CHUNK;   // GELU chunks, 2 slots; the attention's K/V stages alias it
-constexpr int OFF_VEC = OFF_H + 2 * CHUNK;     // vectors of two blocks
-constexpr int SMEM_USED = OFF_VEC + 2 * VEC_BYTES;
-constexpr int SMEM = SMEM_USED + 1024;         // + alignment slack
 constexpr int KV_SLAB = SR_MAX * SW * DH * 2;  // one head's K (or V) rows of a key level
 constexpr int KV_STAGE = 2 * KV_SLAB;
+constexpr int OFF_KV2 = OFF_H + 2 * CHUNK;     // the third K/V stage (the first two alias the GELU region)
+constexpr int OFF_VEC = OFF_KV2 + KV_STAGE;    // vectors of two blocks
+constexpr int SMEM_USED = OFF_VEC + 2 * VEC_BYTES;
+constexpr int SMEM = SMEM_USED + 1024;         // + alignment slack
 constexpr int OFF_RED = OFF_H + 2 * KV_STAGE;  // LayerNorm row partials [2 passes][2 halves][128]
 static_assert(OFF_RED + 4 * 128 * 4 <= OFF_H + 2 * CHUNK, "LayerNorm exchange must fit in the GELU region");
-static_assert(OFF_H % 1024 == 0 && KV_SLAB % 512 == 0, "swizzled operands need aligned bases");
+static_assert(OFF_H % 1024 == 0 && OFF_KV2 % 512 == 0 && KV_SLAB % 512 == 0, "swizzled operands need aligned bases");
+static_assert(SMEM <= 232448, "shared memory per CTA");
+__device__ __forceinline__ uint32_t kv_stage_off(int b) { return (uint32_t)(b < 2 ? OFF_H + b * KV_STAGE : OFF_KV2); }
 // TMEM columns: FC1 accumulators (and the projection's) at 0 and 128, FC2's at
 // 256; QKV chunks at 0, 128, 256; the fp32 residual rows at 384
 constexpr uint32_t T_ACC1 = 0, T_PROJ = 0, T_ACC2 = 256, T_X = 384;
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t w_full[NSLOT], w_empty[NSLOT], vec_full[2], vec_empty[2];
   __shared__ __align__(8) uint64_t a_full, mma_done, drain_bar, qkv_ready;
-  __shared__ __align__(8) uint64_t acc1_full[2], acc1_empty[2], h_full[2], h_empty[2], kv_full[2], kv_empty[2];
+  __shared__ __align__(8) uint64_t acc1_full[2], acc1_empty[2], h_full[2], h_empty[2], kv_full[NKV], kv_empty[NKV];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
@@ -291,6 +295,8 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
       mbar_init(&acc1_empty[b], 8);
       mbar_init(&h_full[b], 8);
       mbar_init(&h_empty[b], 1);
+    }
+    for (int b = 0; b < NKV; ++b) {
       mbar_init(&kv_full[b], 1);
       mbar_init(&kv_empty[b], 8);
     }
@@ -370,7 +376,8 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
       // boxes of 12 latitudes from S0 (rows past H read as zeros, rows past SR
       // are not used) x 20 longitudes, K and V
       const uint32_t kv_bytes = (uint32_t)(SR_MAX * SW * 64 * 2);
-      int kvs = 0, last[2] = {-1, -1};
+      int kst = 0, kpar = 0, last[NKV];   // ring position and its use parity
+      for (int b = 0; b < NKV; ++b) last[b] = -1;
       bool ok = true;
       for (int i = 0; i < nb && ok; ++i) {
         // the latent's q, k, v of block i are complete
@@ -381,16 +388,16 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
         // the q, k, v rows were written by generic stores (this and other CTAs);
         // the tensor copies below read them through the async proxy
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        for (int s = 0; s < steps; ++s, ++kvs) {
-          const int b = kvs & 1;
-          const uint32_t use = (uint32_t)(kvs >> 1) & 1u;
+        for (int s = 0; s < steps; ++s) {
+          const int b = kst;
+          const uint32_t use = (uint32_t)kpar;
           if (!mbar_wait(&kv_empty[b], use ^ 1u, &abort_flag)) {
             ok = false;
             break;
           }
           const int h = s / a.kd, lev = ((i & 1) * a.G + g) * a.D + kd0 + s % a.kd;
           mbar_expect_tx(&kv_full[b], kv_bytes);
-          const uint32_t dst0 = sbase + OFF_H + b * KV_STAGE;
+          const uint32_t dst0 = sbase + kv_stage_off(b);
 #pragma unroll
           for (int kv = 0; kv < 2; ++kv) {
             const int ch = C + kv * C + h * DH;
@@ -406,13 +413,17 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
             }
           }
           last[b] = (int)use;
+          if (++kst == NKV) {
+            kst = 0;
+            kpar ^= 1;
+          }
         }
       }
       if (!ok) {
         abort_flag = 1;
         atomicExch(a.status, (int)WM_ERR_TIMEOUT);
         volatile int never = 0;
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < NKV; ++b)
           if (last[b] >= 0) mbar_wait(&kv_full[b], (uint32_t)last[b], &never);
       }
     }
@@ -534,7 +545,7 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
         const int mi = lane >> 3;
         voff[q][np] = KV_SLAB + kv_off(R0 + 2 * q + (mi & 1), 4 * gc + (lane & 7), 2 * np + (mi >> 1));
       }
-    int kv_step = 0;   // K/V stages waited for so far
+    int kst = 0, kpar = 0;   // K/V ring position and its use parity
 
     auto vec = [&](int j) -> const float4* { return reinterpret_cast<const float4*>(smem + OFF_VEC + (j & 1) * VEC_BYTES); };
     // QKV epilogue: + bias, bf16. The 128 x 384 tile is staged in shared memory
@@ -635,8 +646,7 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
 #pragma unroll 1
         for (int s = 0; s < steps; ++s) {
           const int h = s / a.kd, lv = s % a.kd;
-          ok = warp_wait(&kv_full[s & 1], (uint32_t)(kv_step >> 1) & 1u, &abort_flag) && ok;
-          ++kv_step;
+          ok = warp_wait(&kv_full[kst], (uint32_t)kpar, &abort_flag) && ok;
           if (!ok) abort_flag = 1;
           if (lv == 0) {
 #pragma unroll
@@ -649,7 +659,7 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
             l0 = l1 = 0.f;
             m0 = m1 = -INFINITY;
           }
-          const uint32_t kb = sbase + OFF_H + (s & 1) * KV_STAGE;
+          const uint32_t kb = sbase + kv_stage_off(kst);
           // S = Q K^T over the 8 x 8 key rectangle (8 n8 blocks, one per rectangle row)
           float sc[8][4];
 #pragma unroll
@@ -711,7 +721,11 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
             }
           // this warp is done with the stage
           __syncwarp();
-          if (lane == 0) mbar_arrive(&kv_empty[s & 1]);
+          if (lane == 0) mbar_arrive(&kv_empty[kst]);
+          if (++kst == NKV) {
+            kst = 0;
+            kpar ^= 1;
+          }
           if (lv == a.kd - 1) {
             // head done: normalise, bf16 into the A operand (columns 32 h ..)
             float s0 = l0, s1 = l1;
