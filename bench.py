@@ -599,34 +599,51 @@ def fields_bench(wm, torch, dev, ctx, shape, lead=336, reps=2):
 
 
 def small_rollout(wm, torch, dev, reps=10):
+    """The 14-day rollout of the small latent: BF16 through the whole-rollout
+    kernel (one launch) at batch 1 and 4, the same with the per-kernel path
+    (one launch per GEMM / attention, captured as a graph), and FP32."""
     s = synth.SMALL
     p6, p1 = synth.processor_weights(s, seed=0)
-    ctx = wm.wm_create_from_host(wm.make_config(s, wm.WM_PREC_BF16), synth.pack_weights(p6, p1))
-    x0 = torch.from_numpy(synth.latent(s, 1, seed=1)).to(dev)
-    res = {"workload": "latent 4x24x48x128, window 3x5x5, P6 8 blocks + P1 4 blocks, greedy schedule"}
+    ctx = wm.wm_create_from_host(wm.make_config(s, wm.WM_PREC_BF16, 4), synth.pack_weights(p6, p1))
+    x1 = torch.from_numpy(synth.latent(s, 1, seed=1)).to(dev)
+    x4 = torch.from_numpy(synth.latent(s, 4, seed=1)).to(dev)
+    res = {"workload": "latent 4x24x48x128, window 3x5x5, P6 8 blocks + P1 4 blocks, greedy schedule; "
+                       "bf16: one whole-rollout launch (a CTA per 8x16 patch), bf16_per_kernel: one graph"}
+
+    def timed(x0, T):
+        x = x0.clone()
+        for _ in range(3):                      # capture / first launch + warm-up
+            x.copy_(x0)
+            wm.wm_latent_rollout(ctx, x, T)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            x.copy_(x0)
+            wm.wm_latent_rollout(ctx, x, T)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, x
+
     try:
         finals = {}
-        for prec, name in ((wm.WM_PREC_BF16, "bf16"), (wm.WM_PREC_FP32, "fp32")):
+        for prec, name, fused in ((wm.WM_PREC_BF16, "bf16", 1), (wm.WM_PREC_BF16, "bf16_per_kernel", 0),
+                                  (wm.WM_PREC_FP32, "fp32", 1)):
             wm.wm_set_precision(ctx, prec)
+            wm.wm_set_fused_rollout(fused)
             for T in (336, 337):
-                x = x0.clone()
-                for _ in range(3):                      # capture + warm-up replays
-                    x.copy_(x0)
-                    wm.wm_latent_rollout(ctx, x, T)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(reps):
-                    x.copy_(x0)
-                    wm.wm_latent_rollout(ctx, x, T)
-                e1.record()
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / reps
+                ms, x = timed(x1, T)
                 res[f"{name}_T{T}_forecasts_per_s"] = 1e3 / ms
                 finals[(name, T)] = x.clone()
+            if name != "fp32":
+                ms, _ = timed(x4, 336)
+                res[f"{name}_batch4_T336_forecasts_per_s"] = 4e3 / ms
         for T in (336, 337):
             res[f"bf16_vs_fp32_final_rel_l2_T{T}"] = wm.wm_rel_l2(finals[("bf16", T)], finals[("fp32", T)])
+            res[f"bf16_vs_bf16_per_kernel_final_rel_l2_T{T}"] = wm.wm_rel_l2(finals[("bf16", T)],
+                                                                              finals[("bf16_per_kernel", T)])
     finally:
+        wm.wm_set_fused_rollout(1)
         wm.wm_destroy(ctx)
     return res
 
@@ -641,7 +658,9 @@ def batch_bench(wm, torch, dev, reps=3):
     x0 = [torch.from_numpy(synth.latent(s, 1, seed=1 + i)).to(dev) for i in range(len(leads))]
     ctx = wm.wm_create_from_host(wm.make_config(s, wm.WM_PREC_BF16, max_batch=len(leads)),
                                  synth.pack_weights(p6, p1))
-    res = {"workload": "8 latents 4x24x48x128, leads {1,6,7,24,72,120,240,336} h, 1080 blocks, one graph"}
+    res = {"workload": "8 latents 4x24x48x128, leads {1,6,7,24,72,120,240,336} h, 1080 blocks; "
+                       "bf16: two whole-rollout launches of four latents (longest leads first), "
+                       "fp8mlp / fp32: one graph of batched steps"}
     outs = {}
     try:
         for prec, name in ((wm.WM_PREC_BF16_FP8MLP, "fp8mlp"), (wm.WM_PREC_BF16, "bf16"), (wm.WM_PREC_FP32, "fp32")):
@@ -703,7 +722,8 @@ def hourly_ensemble_bench(wm, torch, dev, full_members=8, reps=2):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        res["ensemble_small_14d"] = {"workload": "64 members 4x24x48x128, 336 h each, one graph",
+        res["ensemble_small_14d"] = {"workload": "64 members 4x24x48x128, 336 h each, "
+                                                 "16 whole-rollout launches of 4 members",
                                      "member_forecasts_per_s": 64e3 / ms}
     finally:
         wm.wm_destroy(ctx)
