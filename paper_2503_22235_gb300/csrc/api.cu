@@ -791,6 +791,27 @@ wm_status rollout_small(wm_ctx* ctx, float* const* x, const int* n6, const int* 
 }  // namespace
 
 namespace wm {
+bool processor_step_inplace_ok(wm_ctx* ctx, int n) {
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  return n >= 1 && rollout_small_group(ctx, n) >= 1;
+}
+
+// One processor step on n latents at arbitrary device addresses (the
+// server's slots), read and written in place by whole-rollout launches of as
+// many latents as the device holds at once.
+wm_status processor_step_inplace(wm_ctx* ctx, float* const* xs, int n, int which, cudaStream_t s) {
+  if (which != WM_P6 && which != WM_P1) return fail(WM_ERR_INVALID_ARG, "which must be WM_P6 or WM_P1");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  const int G = rollout_small_group(ctx, n);
+  if (G < 1) return fail(WM_ERR_INVALID_ARG, "the whole-rollout kernel does not take this step");
+  for (int i0 = 0; i0 < n; i0 += G) {
+    const int g = std::min(G, n - i0);
+    std::vector<int> a6(g, which == WM_P6 ? 1 : 0), a1(g, which == WM_P1 ? 1 : 0);
+    WM_TRY(rollout_small(ctx, xs + i0, a6.data(), a1.data(), g, s));
+  }
+  return WM_OK;
+}
+
 // One processor step on `batch` contiguous latents, replayed from a CUDA
 // graph captured once per (latent buffer, batch, processor, precision): the
 // server's ticks launch one graph instead of every kernel of the step.

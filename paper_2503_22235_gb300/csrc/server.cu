@@ -88,15 +88,23 @@ wm_status run_tick(wm_server* s, const std::vector<uint64_t>& ids, const std::ve
         s->max_step_batch = std::max(s->max_step_batch, g);
         if (g >= 2) ++s->multi_request_steps;
       }
-      // gather into the staging batch, one graph-replayed step, scatter back
-      for (int j = 0; j < g; ++j)
-        WM_CUDA(cudaMemcpyAsync(s->stage + (size_t)j * lat, s->slab + (size_t)due[b0 + j] * lat, lat * 4,
-                                cudaMemcpyDeviceToDevice, s->stream));
-      wm_status st = wm::processor_step_graphed(s->ctx, s->stage, g, w, s->stream);
-      if (st != WM_OK) return st;
-      for (int j = 0; j < g; ++j)
-        WM_CUDA(cudaMemcpyAsync(s->slab + (size_t)due[b0 + j] * lat, s->stage + (size_t)j * lat, lat * 4,
-                                cudaMemcpyDeviceToDevice, s->stream));
+      if (wm::processor_step_inplace_ok(s->ctx, g)) {
+        // narrow latent: one whole-rollout launch reads and writes the slots in place
+        std::vector<float*> xs(g);
+        for (int j = 0; j < g; ++j) xs[j] = s->slab + (size_t)due[b0 + j] * lat;
+        wm_status st = wm::processor_step_inplace(s->ctx, xs.data(), g, w, s->stream);
+        if (st != WM_OK) return st;
+      } else {
+        // gather into the staging batch, one graph-replayed step, scatter back
+        for (int j = 0; j < g; ++j)
+          WM_CUDA(cudaMemcpyAsync(s->stage + (size_t)j * lat, s->slab + (size_t)due[b0 + j] * lat, lat * 4,
+                                  cudaMemcpyDeviceToDevice, s->stream));
+        wm_status st = wm::processor_step_graphed(s->ctx, s->stage, g, w, s->stream);
+        if (st != WM_OK) return st;
+        for (int j = 0; j < g; ++j)
+          WM_CUDA(cudaMemcpyAsync(s->slab + (size_t)due[b0 + j] * lat, s->stage + (size_t)j * lat, lat * 4,
+                                  cudaMemcpyDeviceToDevice, s->stream));
+      }
       ++s->batched_steps;
     }
   }

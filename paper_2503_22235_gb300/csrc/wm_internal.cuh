@@ -20,6 +20,10 @@ const wm_config* ctx_config(const wm_ctx* ctx);
 // One processor step on `batch` contiguous latents, replayed from a CUDA graph
 // captured per (latent buffer, batch, processor, precision).
 wm_status processor_step_graphed(wm_ctx* ctx, float* x, int batch, int which, cudaStream_t s);
+// The same for n latents at arbitrary device addresses, in place, when the
+// whole-rollout kernel takes the step (processor_step_inplace_ok).
+bool processor_step_inplace_ok(wm_ctx* ctx, int n);
+wm_status processor_step_inplace(wm_ctx* ctx, float* const* xs, int n, int which, cudaStream_t s);
 
 // ------------------------------------------------------------ errors ----
 void set_error(const std::string& msg);
