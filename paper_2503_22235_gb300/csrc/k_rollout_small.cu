@@ -396,13 +396,20 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
             break;
           }
           const int h = s / a.kd, lev = ((i & 1) * a.G + g) * a.D + kd0 + s % a.kd;
+          // debug builds: the boxes start inside the q, k, v array (a failed
+          // check still issues the copies from coordinate 0, so the stage completes)
+          const bool coords = WM_DCHECK(S0 >= 0 && S0 < a.H && lev >= 0 && lev < 2 * a.G * a.D &&
+                                            (wrap != 0 || (w0 - 2 >= 0 && w0 - 2 + SW <= a.W)),
+                                        a.status);
           mbar_expect_tx(&kv_full[b], kv_bytes);
           const uint32_t dst0 = sbase + kv_stage_off(b);
 #pragma unroll
           for (int kv = 0; kv < 2; ++kv) {
             const int ch = C + kv * C + h * DH;
             const uint32_t dst = dst0 + kv * KV_SLAB;
-            if (wrap == 0) {
+            if (!coords) {
+              tma_load_4d(dst, &a.tm_kv[0], &kv_full[b], ch, 0, 0, 0);
+            } else if (wrap == 0) {
               tma_load_4d(dst, &a.tm_kv[0], &kv_full[b], ch, w0 - 2, S0, lev);
             } else if (wrap < 0) {
               tma_load_4d(dst, &a.tm_kv[2], &kv_full[b], ch, a.W - 2, S0, lev);
@@ -515,11 +522,19 @@ __global__ void __launch_bounds__(THREADS, 1) rollout_small_kernel(const __grid_
     // attention geometry of this warp: a 4 x 4 query group (rows g8, g8 + 8 of the m16 tile)
     const int gr = warp >> 2, gc = warp & 3, g8 = lane >> 2, t4 = lane & 3;
     const int rw = a.kw / 2;
-    const int R0 = min(clampi(h0 + 4 * gr - rh, 0, a.H - a.kh) - S0, SR - 8);
+    int R0 = min(clampi(h0 + 4 * gr - rh, 0, a.H - a.kh) - S0, SR - 8);
     const int qh0 = h0 + 4 * gr + (g8 >> 2), qh1 = qh0 + 2, qcl = g8 & 3;
     const uint32_t kmask = (1u << a.kh) - 1u;
-    const uint32_t lat0 = kmask << (clampi(qh0 - rh, 0, a.H - a.kh) - S0 - R0);
-    const uint32_t lat1 = kmask << (clampi(qh1 - rh, 0, a.H - a.kh) - S0 - R0);
+    int sh0 = clampi(qh0 - rh, 0, a.H - a.kh) - S0 - R0, sh1 = clampi(qh1 - rh, 0, a.H - a.kh) - S0 - R0;
+    // debug builds: the warp's 8-row key rectangle lies in the slab and holds
+    // both query rows' latitude windows; on failure the warp reads rows 0-7
+    if (!(WM_DCHECK(SR >= 8 && SR <= SR_MAX && R0 >= 0 && R0 + 8 <= SR, a.status) &&
+          WM_DCHECK(sh0 >= 0 && sh0 + a.kh <= 8 && sh1 >= 0 && sh1 + a.kh <= 8, a.status))) {
+      R0 = 0;
+      sh0 = sh1 = 0;
+    }
+    const uint32_t lat0 = kmask << sh0;
+    const uint32_t lat1 = kmask << sh1;
     const bool lon0 = abs(2 * t4 - 2 - qcl) <= rw, lon1 = abs(2 * t4 + 1 - 2 - qcl) <= rw;
     const int tq0 = (d * a.H + qh0) * a.W + w0 + 4 * gc + qcl, tq1 = tq0 + 2 * a.W;
     const int ri0 = (4 * gr + (g8 >> 2)) * TW + 4 * gc + qcl, ri1 = ri0 + 2 * TW;

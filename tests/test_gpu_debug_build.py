@@ -2,11 +2,13 @@
 i.e. device-side checks of the attention windows, slab geometry and tail
 tiles that record WM_ERR_BOUNDS and skip the access) on the hot path: no
 check fails on any attention family and kernel kind, on the FP32 attention,
-or on blocks at the small and the full-size latent. Every attention output
-(each family and kernel kind named explicitly, and the FP32 kernel) and the
-FP32 block equal the release build's bit for bit (the checks change no
-arithmetic); the BF16 blocks, whose attention family the autotuner picks
-per process by timing, agree within 2e-3.
+on blocks at the small and the full-size latent, or on whole-rollout
+launches (two latents, 7 h, on the small latent and on a 2 x 8 x 32 grid
+with a 1 x 5 x 3 window). Every attention output (each family and kernel
+kind named explicitly, and the FP32 kernel), the FP32 block and the
+whole-rollout results equal the release build's bit for bit (the checks
+change no arithmetic); the BF16 blocks, whose attention family the
+autotuner picks per process by timing, agree within 2e-3.
 
 The debug library runs in a child process (WM_LIBRARY=debug makes the
 binding load it); this process runs the same cases on the release library.
@@ -76,6 +78,17 @@ def run_cases(out_path):
         finally:
             wm.wm_destroy(ctx)
     wm.wm_gemm_tile_override(wm.GEMM_TILES_TUNED)
+    grids = (dataclasses.replace(synth.SMALL, blocks_p6=2, blocks_p1=1),
+             dataclasses.replace(synth.SMALL, D=2, H=8, W=32, kd=1, kh=5, kw=3, blocks_p6=2, blocks_p1=1))
+    for gi, shape in enumerate(grids):
+        p6, p1 = synth.processor_weights(shape, seed=0, stress=True)
+        ctx = wm.wm_create_from_host(wm.make_config(shape, wm.WM_PREC_BF16, 2), synth.pack_weights(p6, p1))
+        try:
+            x = torch.from_numpy(synth.latent(shape, 2, seed=2)).to(dev)
+            wm.wm_latent_rollout(ctx, x, 7)          # one whole-rollout launch of two latents
+            res[f"exact_rollout{gi}"] = x.cpu().numpy()
+        finally:
+            wm.wm_destroy(ctx)
     wm.wm_device_status()   # raises WmError(WM_ERR_BOUNDS) if a debug check failed
     np.savez(out_path, **res)
 
