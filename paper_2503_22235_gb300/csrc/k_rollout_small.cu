@@ -30,9 +30,9 @@
 // block's weights (12 pre-swizzled 32 KB chunks per block, one bulk copy each,
 // through a two-slot ring) and its biases and LayerNorm vectors (one bulk
 // copy into a two-slot buffer), warp 10 one thread issuing the K/V tensor
-// copies into a three-stage ring. Latents are independent: each has its own schedule (six-hour
-// blocks, then one-hour blocks) and its own barrier, so latents with
-// different lead times share the launch.
+// copies into a three-stage ring. Latents are independent: each has its own
+// schedule (six-hour blocks, then one-hour blocks) and its own barrier, so
+// latents with different lead times share the launch.
 //
 // Every mbarrier wait and the latent barrier are bounded in time; on a
 // timeout the CTA records WM_ERR_TIMEOUT, the compute warps leave together
@@ -61,7 +61,7 @@ constexpr int VEC_FLOATS = 1664;               // a block's vectors (layout belo
 constexpr int VEC_BYTES = VEC_FLOATS * 4;
 constexpr int OFF_A = 0;                       // A operand: LN1(x), O or LN2(x)
 constexpr int OFF_W = OFF_A + CHUNK;           // weight ring
-constexpr int OFF_H = OFF_W + NSLOT * CHUNK;   // GELU chunks, 2 slots; the attention's K/V stages alias it
+constexpr int OFF_H = OFF_W + NSLOT * CHUNK;   // GELU chunks, 2 slots; K/V stages 0 and 1 alias it
 constexpr int KV_SLAB = SR_MAX * SW * DH * 2;  // one head's K (or V) rows of a key level
 constexpr int KV_STAGE = 2 * KV_SLAB;
 constexpr int OFF_KV2 = OFF_H + 2 * CHUNK;     // the third K/V stage (the first two alias the GELU region)
